@@ -1,0 +1,326 @@
+"""Pins of the CPU oracle against facts fixed by mathematics, not by the oracle.
+
+Each test would fail for a plausible mistake in the oracle: a wrong node set,
+a dropped quadrature weight, a transposed basis table, a missing Jacobian
+factor, a wrong sign in the forcing, a wrong index in Algorithm 5.
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from oracle import cg, fastdiag, fem
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+# ---------------------------------------------------------------- 1D rules
+
+
+def test_gauss_lobatto_nodes_closed_forms():
+    for row in _read_golden("gauss_lobatto_nodes.txt"):
+        p = int(row[0])
+        xi = np.array([eval(t, {"sqrt": math.sqrt}) for t in row[1:]])
+        np.testing.assert_allclose(fem.gauss_lobatto_nodes(p), 0.5 * (xi + 1.0), atol=2e-15)
+
+
+def test_gauss_rule_exactness_degree():
+    # n-point Gauss is exact up to degree 2n-1 and not for degree 2n
+    for n in range(1, 10):
+        x, w = fem.gauss_rule(n)
+        for k in range(2 * n):
+            assert abs(w @ x ** k - 1.0 / (k + 1)) < 1e-14
+        assert abs(w @ x ** (2 * n) - 1.0 / (2 * n + 1)) > 1e-12
+    x, w = fem.gauss_rule(3)
+    np.testing.assert_allclose(x, [0.5 - math.sqrt(15) / 10, 0.5, 0.5 + math.sqrt(15) / 10], atol=1e-15)
+    np.testing.assert_allclose(w, [5 / 18, 8 / 18, 5 / 18], atol=1e-15)
+
+
+def test_lagrange_tables_reproduce_polynomials():
+    rng = np.random.default_rng(1)
+    for p in range(1, 9):
+        nodes = fem.gauss_lobatto_nodes(p)
+        x = rng.random(7)
+        V = fem.lagrange_values(nodes, x)
+        D = fem.lagrange_derivatives(nodes, x)
+        np.testing.assert_allclose(fem.lagrange_values(nodes, nodes), np.eye(p + 1), atol=1e-13)
+        for m in range(p + 1):
+            np.testing.assert_allclose(V @ nodes ** m, x ** m, atol=1e-12)
+            deriv = m * x ** (m - 1) if m > 0 else np.zeros_like(x)
+            np.testing.assert_allclose(D @ nodes ** m, deriv, atol=1e-10)
+
+
+def test_1d_matrices_exact_q1_q2():
+    for row in _read_golden("q1_q2_1d_matrices.txt"):
+        name, p = row[0], int(row[1])
+        exact = np.array([float(Fraction(t)) for t in row[2:]]).reshape(p + 1, p + 1)
+        K, M = fem.element_matrices_1d(p)
+        np.testing.assert_allclose(K if name == "K" else M, exact, atol=1e-14)
+
+
+def test_1d_matrices_match_symbolic_integration():
+    sympy = pytest.importorskip("sympy")
+    X = sympy.Symbol("x")
+    for p in (3, 4, 5):
+        xi = sorted(sympy.Poly(sympy.diff(sympy.legendre(p, X), X), X).nroots(n=40))
+        nodes = [sympy.Integer(0)] + [(t + 1) / 2 for t in xi] + [sympy.Integer(1)]
+        L = []
+        for j in range(p + 1):
+            e = sympy.Integer(1)
+            for k in range(p + 1):
+                if k != j:
+                    e *= (X - nodes[k]) / (nodes[j] - nodes[k])
+            L.append(sympy.expand(e))
+        K_ex = np.array([[float(sympy.integrate(sympy.diff(L[i], X) * sympy.diff(L[j], X), (X, 0, 1)))
+                          for j in range(p + 1)] for i in range(p + 1)])
+        M_ex = np.array([[float(sympy.integrate(L[i] * L[j], (X, 0, 1))) for j in range(p + 1)]
+                         for i in range(p + 1)])
+        K, M = fem.element_matrices_1d(p)
+        np.testing.assert_allclose(K, K_ex, atol=1e-12 * np.abs(K_ex).max())
+        np.testing.assert_allclose(M, M_ex, atol=1e-13)
+
+
+# ---------------------------------------------------------------- operator
+
+
+def _kronecker_operator(p, cells, K1, M1):
+    """Independent construction A = sum of Kronecker products of 1D assembled
+    matrices (x fastest), Dirichlet identity rows."""
+    mats = []
+    for d in range(3):
+        n = p * cells[d] + 1
+        h = 1.0 / cells[d]
+        Kg = np.zeros((n, n))
+        Mg = np.zeros((n, n))
+        for c in range(cells[d]):
+            s = slice(p * c, p * c + p + 1)
+            Kg[s, s] += K1 / h
+            Mg[s, s] += M1 * h
+        mats.append((sp.csr_matrix(Kg), sp.csr_matrix(Mg)))
+    (Kx, Mx), (Ky, My), (Kz, Mz) = mats
+    A = sp.kron(Kz, sp.kron(My, Mx)) + sp.kron(Mz, sp.kron(Ky, Mx)) + sp.kron(Mz, sp.kron(My, Kx))
+    prob = fem.Problem(p, cells)
+    bnd = fem.boundary_mask(prob)
+    keep = sp.diags((~bnd).astype(float))
+    return (keep @ A @ keep + sp.diags(bnd.astype(float))).tocsr()
+
+
+def test_assembled_equals_kronecker_q2_exact_1d():
+    rows = {(r[0], int(r[1])): np.array([float(Fraction(t)) for t in r[2:]]) for r in _read_golden("q1_q2_1d_matrices.txt")}
+    K1, M1 = rows[("K", 2)].reshape(3, 3), rows[("M", 2)].reshape(3, 3)
+    cells = (3, 2, 4)
+    A = fem.assemble(fem.Problem(2, cells))
+    B = _kronecker_operator(2, cells, K1, M1)
+    assert abs(A - B).max() < 1e-13 * abs(B).max()
+
+
+def test_assembled_equals_kronecker_higher_degree():
+    for p, cells in ((4, (2, 3, 2)), (6, (2, 2, 1))):
+        K1, M1 = fem.element_matrices_1d(p)
+        A = fem.assemble(fem.Problem(p, cells))
+        B = _kronecker_operator(p, cells, K1, M1)
+        assert abs(A - B).max() < 1e-13 * abs(B).max()
+
+
+def test_q1_27_point_stencil():
+    vals = {r[0]: float(Fraction(r[1])) for r in _read_golden("q1_stencil.txt")}
+    N = 4
+    prob = fem.Problem(1, (N, N, N))
+    A = fem.assemble(prob)
+    h = 1.0 / N
+    nx = N + 1
+    c = 2 + nx * (2 + nx * 2)
+    row = A.getrow(c).toarray().ravel()
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                nnz = abs(dx) + abs(dy) + abs(dz)
+                cls = ["centre", "face", "edge", "corner"][nnz]
+                assert abs(row[c + dx + nx * (dy + nx * dz)] - vals[cls] * h) < 1e-14
+
+
+@pytest.mark.parametrize("amp,coef", [(0.0, fem.COEF_CONSTANT), (0.05, fem.COEF_SIN_X), (0.08, fem.COEF_CONSTANT)])
+def test_symmetric_positive_definite(amp, coef):
+    prob = fem.Problem(3, (2, 3, 2), amp, coef)
+    A = fem.assemble(prob).toarray()
+    assert np.abs(A - A.T).max() < 1e-14 * np.abs(A).max()
+    np.linalg.cholesky(A)
+    assert np.linalg.eigvalsh(A).min() > 0
+
+
+@pytest.mark.parametrize("amp,coef", [(0.0, fem.COEF_CONSTANT), (0.05, fem.COEF_SIN_X), (0.08, fem.COEF_SIN_X)])
+def test_neumann_constant_null_space(amp, coef):
+    prob = fem.Problem(4, (2, 2, 3), amp, coef)
+    A = fem.assemble(prob, dirichlet=False)
+    r = A @ np.ones(prob.n_dofs)
+    assert np.abs(r).max() < 1e-14 * abs(A).max() * 10
+
+
+def test_deformed_jacobian_matches_finite_differences():
+    prob = fem.Problem(3, (2, 2, 2), 0.07)
+    x, J, detJ, _ = fem.quadrature_geometry(prob, np.array([0, 5]))
+    # perturb the reference coordinate of one point through a shifted rule is not
+    # available, so difference the physical map directly: x(X) = X + A s(X)(1,1,1)
+    h = 0.5
+    g, _ = fem.gauss_rule(4)
+    for e, (cx, cy, cz) in enumerate([(0, 0, 0), (1, 0, 1)]):
+        for q in (0, 17, 40):
+            qa, qb, qc = q % 4, (q // 4) % 4, q // 16
+            xh = np.array([g[qa], g[qb], g[qc]])
+            c = np.array([cx, cy, cz])
+
+            def phys(xhat):
+                X = h * (c + xhat)
+                s = np.sin(2 * np.pi * X[0]) * np.sin(2 * np.pi * X[1]) * np.sin(2 * np.pi * X[2])
+                return X + 0.07 * s
+
+            eps = 1e-6
+            Jfd = np.stack([(phys(xh + eps * np.eye(3)[d]) - phys(xh - eps * np.eye(3)[d])) / (2 * eps)
+                            for d in range(3)], axis=1)
+            np.testing.assert_allclose(J[e, q], Jfd, atol=1e-8)
+            np.testing.assert_allclose(x[e, q], phys(xh), atol=1e-15)
+            assert detJ[e, q] > 0
+
+
+def test_forcing_matches_finite_difference_operator():
+    rng = np.random.default_rng(3)
+    for coef in (fem.COEF_CONSTANT, fem.COEF_SIN_X):
+        prob = fem.Problem(2, (2, 2, 2), 0.0, coef)
+        pts = 0.1 + 0.8 * rng.random((5, 3))
+        eps = 1e-4
+
+        def a(x):
+            return fem.coefficient(prob, x)
+
+        for x in pts:
+            div = 0.0
+            for d in range(3):
+                e = eps * np.eye(3)[d]
+                fp = a(x + e / 2) * (fem.manufactured_solution(x + e) - fem.manufactured_solution(x)) / eps
+                fm = a(x - e / 2) * (fem.manufactured_solution(x) - fem.manufactured_solution(x - e)) / eps
+                div += (fp - fm) / eps
+            assert abs(-div - fem.manufactured_forcing(prob, x)) < 1e-5 * 30
+
+
+@pytest.mark.parametrize("p,amp,coef", [(2, 0.0, fem.COEF_CONSTANT), (3, 0.0, fem.COEF_SIN_X),
+                                        (2, 0.05, fem.COEF_SIN_X), (2, 0.08, fem.COEF_CONSTANT)])
+def test_l2_convergence_rate(p, amp, coef):
+    # the sine deformation has unit wavelength, so its Jacobian varies on a
+    # scale of 1/(2 pi); rates on deformed meshes are read between N = 4 and 8
+    errs = []
+    Ns = (2, 4, 8) if p == 2 else (2, 4, 6)
+    for N in Ns:
+        prob = fem.Problem(p, (N, N, N), amp, coef)
+        A = fem.assemble(prob)
+        u = spla.spsolve(A.tocsc(), fem.rhs(prob))
+        errs.append(fem.l2_error(prob, u))
+    rate = math.log(errs[-2] / errs[-1]) / math.log(Ns[-1] / Ns[-2])
+    assert rate > p + 1 - 0.35, (errs, rate)
+
+
+def test_apply_rows_matches_assembled_matrix():
+    rng = np.random.default_rng(5)
+    for prob in (fem.Problem(2, (3, 2, 3)), fem.Problem(3, (2, 2, 2), 0.05, fem.COEF_SIN_X)):
+        A = fem.assemble(prob)
+        u = rng.standard_normal(prob.n_dofs)
+        rows = rng.choice(prob.n_dofs, 40, replace=False)
+        np.testing.assert_allclose(fem.apply_rows(prob, u, rows), (A @ u)[rows], atol=1e-13 * np.abs(A @ u).max())
+        np.testing.assert_allclose(fem.diagonal_rows(prob, rows), A.diagonal()[rows], atol=1e-14)
+
+
+# ---------------------------------------------------------------- solvers
+
+
+def _exact_q2_system(cells):
+    rows = {(r[0], int(r[1])): [Fraction(t) for t in r[2:]] for r in _read_golden("q1_q2_1d_matrices.txt")}
+    K1 = np.array(rows[("K", 2)], dtype=object).reshape(3, 3)
+    M1 = np.array(rows[("M", 2)], dtype=object).reshape(3, 3)
+    mats = []
+    for d in range(3):
+        n = 2 * cells[d] + 1
+        h = Fraction(1, cells[d])
+        Kg = np.zeros((n, n), dtype=object)
+        Mg = np.zeros((n, n), dtype=object)
+        Kg[:] = Fraction(0)
+        Mg[:] = Fraction(0)
+        for c in range(cells[d]):
+            for i in range(3):
+                for j in range(3):
+                    Kg[2 * c + i, 2 * c + j] += K1[i, j] / h
+                    Mg[2 * c + i, 2 * c + j] += M1[i, j] * h
+        mats.append((Kg[1:-1, 1:-1], Mg[1:-1, 1:-1]))
+    (Kx, Mx), (Ky, My), (Kz, Mz) = mats
+    A = np.kron(Kz, np.kron(My, Mx)) + np.kron(Mz, np.kron(Ky, Mx)) + np.kron(Mz, np.kron(My, Kx))
+    return A
+
+
+def test_algorithm5_equals_algorithm1_exact_rationals():
+    A = _exact_q2_system((2, 2, 2))  # 27 interior unknowns
+    n = A.shape[0]
+    b = np.array([Fraction((7 * i) % 5 - 2) for i in range(n)], dtype=object)
+    inv_diag = np.array([1 / A[i, i] for i in range(n)], dtype=object)
+
+    def apply_A(x):
+        return A.dot(x)
+
+    rtol = Fraction(1, 10 ** 8)
+    r1 = cg.pcg_algorithm1(apply_A, b, inv_diag, rtol, 100)
+    r5 = cg.pcg_algorithm5(apply_A, b, inv_diag, rtol, 100)
+    assert r1.iterations == r5.iterations
+    assert r1.alphas == r5.alphas
+    assert r1.betas == r5.betas
+    assert r1.residual_sq_history == r5.residual_sq_history
+    assert list(r1.x) == list(r5.x)
+    # CG terminates in at most n steps in exact arithmetic with the exact solution
+    assert r1.iterations <= n
+
+
+def test_algorithm5_odd_and_even_finalisation_exact():
+    A = _exact_q2_system((2, 2, 2))
+    n = A.shape[0]
+    b = np.array([Fraction((3 * i) % 7 - 3) for i in range(n)], dtype=object)
+    inv_diag = np.array([1 / A[i, i] for i in range(n)], dtype=object)
+    for maxit in (1, 2, 3, 4, 5, 6):
+        r1 = cg.pcg_algorithm1(lambda x: A.dot(x), b, inv_diag, Fraction(0), maxit)
+        r5 = cg.pcg_algorithm5(lambda x: A.dot(x), b, inv_diag, Fraction(0), maxit)
+        assert r1.iterations == r5.iterations == maxit
+        assert list(r1.x) == list(r5.x)
+
+
+def test_cg_fp64_converges_to_direct_solution():
+    prob = fem.Problem(2, (8, 8, 8))
+    A = fem.assemble(prob)
+    b = fem.rhs(prob)
+    inv_diag = 1.0 / A.diagonal()
+    x_direct = spla.spsolve(A.tocsc(), b)
+    r1 = cg.pcg_algorithm1(lambda x: A @ x, b, inv_diag, 1e-10, 1000)
+    r5 = cg.pcg_algorithm5(lambda x: A @ x, b, inv_diag, 1e-10, 1000)
+    assert r1.converged and r5.converged
+    assert abs(r1.iterations - r5.iterations) <= 1
+    assert np.linalg.norm(b - A @ r1.x) < 1e-10 * np.linalg.norm(b)
+    assert np.abs(r1.x - x_direct).max() < 1e-8 * np.abs(x_direct).max()
+    assert np.abs(r5.x - r1.x).max() < 1e-9 * np.abs(r1.x).max()
+
+
+def test_fast_diagonalisation_matches_direct_solve():
+    rng = np.random.default_rng(11)
+    for p, cells in ((2, (3, 4, 2)), (4, (2, 2, 3))):
+        prob = fem.Problem(p, cells)
+        A = fem.assemble(prob)
+        b = rng.standard_normal(prob.n_dofs)
+        x = fastdiag.solve(prob, b)
+        np.testing.assert_allclose(A @ x, b, atol=1e-11 * np.abs(b).max())
