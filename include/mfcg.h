@@ -1,0 +1,167 @@
+/*
+ * mfcg.h -- C ABI of the fused matrix-free Jacobi-CG library for GB300 (sm_103a).
+ *
+ * The library solves A u = b for the continuous Q_p finite-element
+ * discretisation of -div(a grad u) = f on the unit cube with homogeneous
+ * Dirichlet data (Sec. 2, Eqs. 1-3), where the action of A is evaluated
+ * matrix-free as a sum of cell contributions (Eq. 4) with the cell integrals
+ * of Eq. 5 computed by sum factorisation on the tensor-product Gauss rule with
+ * p+1 points per direction, and the solver is the preconditioned CG with
+ * merged vector operations (Algorithm 5) whose vector updates and seven inner
+ * products run inside the operator pass (Sec. 5).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Vectors are arrays of n doubles, n = (p*Nx+1)(p*Ny+1)(p*Nz+1), one per mesh
+ *    node including the Dirichlet nodes, in the library's tile-blocked DoF
+ *    ordering (the nodes of each tile of cells are contiguous; see
+ *    mfcg_to_lexicographic for the conversion).  Dirichlet nodes stay in the
+ *    system as identity rows (Sec. 5.3): (A u)_i = u_i there.
+ *  - Unless the name ends in _host, pointers are DEVICE pointers on the device
+ *    that was current at mfcg_setup; the caller owns them and keeps them alive
+ *    until the call's work has finished on the problem's stream.
+ *  - All device work is enqueued on the stream given to mfcg_setup.  Calls that
+ *    return results to the host (cg_solve, n_dofs) synchronise that stream.
+ *  - Every function returns an mfcg_status code; no exception or abort crosses
+ *    the ABI.  After MFCG_CUDA_ERROR the problem must be destroyed.
+ */
+#ifndef MFCG_H
+#define MFCG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum mfcg_status {
+  MFCG_OK = 0,
+  MFCG_INVALID_ARG = 1,          /* null pointer, bad size, bad enum value          */
+  MFCG_UNSUPPORTED_DEGREE = 2,   /* degree outside 1..8                              */
+  MFCG_OUT_OF_MEMORY = 3,        /* a device allocation failed                       */
+  MFCG_CUDA_ERROR = 4,           /* a CUDA runtime call failed                        */
+  MFCG_NOT_CONVERGED = 5,        /* maxit reached before the tolerance               */
+  MFCG_BREAKDOWN = 6,            /* p^T A p <= 0, r^T M^-1 r <= 0 or a non-finite sum */
+  MFCG_DEVICE_TIMEOUT = 7        /* a bounded device-side wait gave up               */
+} mfcg_status;
+
+/* Mesh of Nx x Ny x Nz box cells on [0,1]^3.  amplitude A deforms the mesh by
+ * x = X + A sin(2 pi X) sin(2 pi Y) sin(2 pi Z) on every component (A = 0 is
+ * the Cartesian mesh); |A| < 0.1 keeps the map invertible. */
+typedef struct mfcg_mesh {
+  int32_t nx, ny, nz;
+  double amplitude;
+} mfcg_mesh;
+
+typedef enum mfcg_geometry_kind {
+  MFCG_GEOM_AFFINE = 0,     /* constant Jacobian per cell (Cartesian box cells), Sec. 2.2 "affine" variant */
+  MFCG_GEOM_DEFORMED = 1    /* per-quadrature-point inverse Jacobian and JxW stored in FP64, Sec. 2.2
+                               "inverse Jacobian load" variant                                             */
+} mfcg_geometry_kind;
+
+typedef enum mfcg_coefficient_kind {
+  MFCG_COEF_CONSTANT = 0,   /* a(x) = 1                                  */
+  MFCG_COEF_SIN_X = 1       /* a(x) = 1 + 0.5 sin(pi x), x physical     */
+} mfcg_coefficient_kind;
+
+typedef struct mfcg_geometry {
+  int32_t kind;             /* mfcg_geometry_kind   */
+  int32_t coefficient;      /* mfcg_coefficient_kind */
+} mfcg_geometry;
+
+typedef enum mfcg_mode {
+  MFCG_MODE_FUSED = 0,      /* Algorithm 5 with pre/post inside the operator pass (Sec. 5)        */
+  MFCG_MODE_UNFUSED = 1     /* Algorithm 1 with a separate operator, axpy, Jacobi and dot kernel   */
+} mfcg_mode;
+
+typedef struct mfcg_options {
+  int32_t mode;             /* mfcg_mode                                                            */
+  int32_t graph_iterations; /* CG iterations per captured CUDA graph (even; 0 = 16)                   */
+  int32_t instrument;       /* 1: launch without graphs and time every operator-pass kernel with
+                               CUDA events (mfcg_solve_info.main_kernel_ms); 0: graphs, no timing      */
+  int32_t tile[3];          /* cells per tile and direction; 0 = chosen from the degree               */
+  int32_t reserved[2];      /* must be zero                                                          */
+} mfcg_options;
+
+typedef struct mfcg_solve_info {
+  int32_t iterations;         /* number of products A p performed                                  */
+  int32_t converged;          /* 1 if ||r|| < rtol ||b|| was detected                               */
+  int32_t status;             /* same value as the return code                                     */
+  int32_t main_kernel_launches; /* operator-pass kernels timed (instrument = 1), else 0              */
+  double residual_sq_est;     /* last ||r_{k+1}||^2: Eq. 8 expansion (fused) or explicit (unfused)   */
+  double rhs_norm_sq;         /* ||b||^2                                                           */
+  double main_kernel_ms;      /* summed CUDA-event time of the operator-pass kernels (instrument = 1) */
+  int64_t kernel_launches;    /* kernels this call enqueued, graph replays included                */
+} mfcg_solve_info;
+
+typedef struct mfcg_problem mfcg_problem;
+
+/* mfcg_setup -- Sec. 2 (Eqs. 2-5) and Sec. 2.1: builds the 1D Gauss-Lobatto
+ * basis of degree `degree`, the (degree+1)-point Gauss rule, the tile-blocked
+ * DoF numbering (Sec. 5.3) and, for MFCG_GEOM_DEFORMED, the per-point metric
+ * data; allocates every internal device buffer.
+ *   mesh, geom    in: problem description (copied).
+ *   opt           in: may be NULL for defaults.
+ *   cuda_stream   in: cudaStream_t (NULL = legacy default stream) used by every call.
+ *   out           out: new handle; release with mfcg_destroy.
+ * Errors: INVALID_ARG (cells < 1, |amplitude| >= 0.1, affine kind with A != 0 or
+ * a != 1, bad enums), UNSUPPORTED_DEGREE, OUT_OF_MEMORY, CUDA_ERROR. */
+int mfcg_setup(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, const mfcg_options* opt,
+               void* cuda_stream, mfcg_problem** out);
+
+/* mfcg_n_dofs -- number n of unknowns, all mesh nodes including Dirichlet ones
+ * (Sec. 2: n counts the unique coefficients of the expansion). */
+int mfcg_n_dofs(const mfcg_problem* prob, int64_t* n);
+
+/* mfcg_apply_operator -- dst = A src (Eq. 4 with the cell operator of Eq. 5),
+ * Dirichlet rows identity.  src, dst: device, n doubles, must not overlap.
+ * Asynchronous on the problem's stream. */
+int mfcg_apply_operator(mfcg_problem* prob, const double* src, double* dst);
+
+/* mfcg_diagonal -- diag(A) of the same operator (exact diagonal with the same
+ * Gauss rule; 1 on Dirichlet nodes), the point-Jacobi preconditioner M of
+ * Sec. 3.  diag: device, n doubles.  Asynchronous. */
+int mfcg_diagonal(mfcg_problem* prob, double* diag);
+
+/* mfcg_rhs -- right-hand side b_i = int f phi_i for the manufactured solution
+ * u = sin(pi x) sin(pi y) sin(pi z) (f = -div(a grad u)), same Gauss rule,
+ * 0 on Dirichlet nodes.  b: device, n doubles.  Asynchronous. */
+int mfcg_rhs(mfcg_problem* prob, double* b);
+
+/* mfcg_cg_solve -- Jacobi-preconditioned CG from the initial guess in x
+ * (Algorithm 5 in FUSED mode, Algorithm 1 in UNFUSED mode) until
+ * ||r_k|| < rtol ||b|| (unpreconditioned residual, Sec. 3.1) or maxit products
+ * A p.  rtol == 0 runs exactly maxit iterations and returns MFCG_OK.
+ *   b   in : device, n doubles, must be zero on Dirichlet nodes (INVALID_ARG is
+ *            not checked on the device; a nonzero value there is solved as an
+ *            identity row).
+ *   x   in/out: device, n doubles; initial guess on entry (all-zero skips A x0),
+ *            solution on return.
+ *   info out: may be NULL.
+ * Synchronises the stream.  Returns OK, NOT_CONVERGED, BREAKDOWN or CUDA_ERROR. */
+int mfcg_cg_solve(mfcg_problem* prob, const double* b, double* x, double rtol, int maxit,
+                  mfcg_solve_info* info);
+
+/* mfcg_cg_solve_host -- the same solve with HOST arrays (pinned memory gives
+ * asynchronous copies): b is copied to a library-owned device buffer, x is
+ * copied in and the solution copied back before return. */
+int mfcg_cg_solve_host(mfcg_problem* prob, const double* b_host, double* x_host, double rtol, int maxit,
+                       mfcg_solve_info* info);
+
+/* mfcg_to_lexicographic / mfcg_from_lexicographic -- reorder a device vector
+ * between the library's tile-blocked order and the lexicographic node order
+ * g = i + (p Nx + 1)(j + (p Ny + 1) k).  in, out: device, n doubles, no overlap. */
+int mfcg_to_lexicographic(mfcg_problem* prob, const double* in, double* out);
+int mfcg_from_lexicographic(mfcg_problem* prob, const double* in, double* out);
+
+/* mfcg_destroy -- frees every buffer the library owns; NULL is accepted. */
+int mfcg_destroy(mfcg_problem* prob);
+
+/* mfcg_status_string -- static description of a status code. */
+const char* mfcg_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MFCG_H */

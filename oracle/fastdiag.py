@@ -65,3 +65,41 @@ def solve(prob: fem.Problem, b: np.ndarray) -> np.ndarray:
     U = np.einsum("kc,cba->kba", Sz, U, optimize=True)
     x[1:-1, 1:-1, 1:-1] = U
     return x.reshape(-1)
+
+
+def _sparse_1d(p: int, n_cells: int):
+    h = 1.0 / n_cells
+    Kg, Mg = assembled_1d(p, n_cells)
+    import scipy.sparse as sp
+    return sp.csr_matrix(Kg / h), sp.csr_matrix(Mg * h)
+
+
+def apply(prob: fem.Problem, u: np.ndarray) -> np.ndarray:
+    """A u for the Cartesian Dirichlet problem from the Kronecker-sum form
+    A = K_z (x) M_y (x) M_x + M_z (x) K_y (x) M_x + M_z (x) M_y (x) K_x on the
+    interior nodes (boundary columns zero), identity rows on the boundary.
+    Cost O(n p) with sparse 1D factors, usable at any mesh size."""
+    if not fem.cartesian_cells_identical(prob):
+        raise ValueError("the Kronecker form needs a Cartesian mesh with a = 1")
+    nx, ny, nz = prob.nodes_per_dim
+    Kx, Mx = _sparse_1d(prob.p, prob.cells[0])
+    Ky, My = _sparse_1d(prob.p, prob.cells[1])
+    Kz, Mz = _sparse_1d(prob.p, prob.cells[2])
+    U = u.reshape(nz, ny, nx).copy()
+    bnd = fem.boundary_mask(prob).reshape(nz, ny, nx)
+    U[bnd] = 0.0
+
+    def along(mat, X, axis):
+        Xm = np.moveaxis(X, axis, 0)
+        shp = Xm.shape
+        Y = (mat @ Xm.reshape(shp[0], -1)).reshape(shp)
+        return np.moveaxis(Y, 0, axis)
+
+    Mx_u = along(Mx, U, 2)
+    Kx_u = along(Kx, U, 2)
+    MyMx = along(My, Mx_u, 1)
+    out = along(Kz, MyMx, 0)
+    out += along(Mz, along(Ky, Mx_u, 1) + along(My, Kx_u, 1), 0)
+    out[bnd] = u.reshape(nz, ny, nx)[bnd]
+    return out.reshape(-1)
+

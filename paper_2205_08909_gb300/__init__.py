@@ -1,0 +1,148 @@
+"""Fused matrix-free Jacobi-CG for GB300 (sm_103a).
+
+The hot path of Kronbichler, Sashko and Munch (arXiv 2205.08909): a CG
+iteration for the continuous Q_p Laplacian in which the sum-factorised
+matrix-free operator evaluation (Eqs. 4-5) is fused with the vector updates
+and the seven inner products of the merged PCG algorithm (Algorithm 5).  The
+compute runs in the CUDA library libmfcg.so behind the C ABI of
+include/mfcg.h; this package is a thin torch binding (device memory, streams).
+
+    import torch, paper_2205_08909_gb300 as mfcg
+    prob = mfcg.Problem(degree=4, cells=(64, 64, 64))
+    b = prob.rhs()
+    x, info = prob.cg_solve(b, rtol=1e-10)
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _binding
+from ._binding import MfcgError, SolveInfo  # noqa: F401
+
+__all__ = ["Problem", "MfcgError", "SolveInfo"]
+
+
+def _ptr(t: torch.Tensor) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Problem:
+    """One Q_p Poisson problem on the unit cube, set up on the current CUDA device.
+
+    degree: 1..8; cells: (Nx, Ny, Nz); amplitude: sine deformation of the mesh
+    (needs geometry="deformed"); coefficient: "constant" (a = 1) or "sin_x"
+    (a = 1 + 0.5 sin(pi x)); mode: "fused" (Algorithm 5 inside the operator
+    pass) or "unfused" (Algorithm 1, one kernel per vector operation).
+    Vectors are float64 CUDA tensors in the library's tile-blocked order.
+    """
+
+    def __init__(self, degree: int, cells, amplitude: float = 0.0, geometry: str = "affine",
+                 coefficient: str = "constant", mode: str = "fused", graph_iterations: int = 0,
+                 instrument: bool = False, tile=None, stream: torch.cuda.Stream | None = None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("paper_2205_08909_gb300 needs a CUDA device (no CPU fallback)")
+        self._lib = _binding.load()
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        cells = tuple(int(c) for c in (cells if hasattr(cells, "__len__") else (cells,) * 3))
+        self.degree, self.cells = int(degree), cells
+        mesh = _binding.Mesh(cells[0], cells[1], cells[2], float(amplitude))
+        geom = _binding.Geometry(_binding.GEOM[geometry], _binding.COEF[coefficient])
+        opt = _binding.Options()
+        opt.mode = _binding.MODE[mode]
+        opt.graph_iterations = int(graph_iterations)
+        opt.instrument = 1 if instrument else 0
+        if tile is not None:
+            for d in range(3):
+                opt.tile[d] = int(tile[d])
+        handle = ctypes.c_void_p()
+        _binding.check("mfcg_setup", self._lib.mfcg_setup(ctypes.byref(mesh), self.degree, ctypes.byref(geom),
+                                                           ctypes.byref(opt), ctypes.c_void_p(self.stream.cuda_stream),
+                                                           ctypes.byref(handle)))
+        self._h = handle
+        n = ctypes.c_int64()
+        _binding.check("mfcg_n_dofs", self._lib.mfcg_n_dofs(self._h, ctypes.byref(n)))
+        self.n_dofs = int(n.value)
+
+    # ---------------------------------------------------------------- helpers
+    def _vec(self, t: torch.Tensor, name: str) -> torch.Tensor:
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or t.device != self.device \
+                or t.numel() != self.n_dofs or not t.is_contiguous():
+            raise ValueError(f"{name}: expected a contiguous float64 tensor of {self.n_dofs} entries on {self.device}")
+        return t
+
+    def empty(self) -> torch.Tensor:
+        return torch.empty(self.n_dofs, dtype=torch.float64, device=self.device)
+
+    # ---------------------------------------------------------------- API
+    def apply_operator(self, src: torch.Tensor, dst: torch.Tensor | None = None) -> torch.Tensor:
+        dst = self.empty() if dst is None else dst
+        _binding.check("mfcg_apply_operator", self._lib.mfcg_apply_operator(
+            self._h, _ptr(self._vec(src, "src")), _ptr(self._vec(dst, "dst"))))
+        return dst
+
+    def diagonal(self, out: torch.Tensor | None = None) -> torch.Tensor:
+        out = self.empty() if out is None else out
+        _binding.check("mfcg_diagonal", self._lib.mfcg_diagonal(self._h, _ptr(self._vec(out, "diag"))))
+        return out
+
+    def rhs(self, out: torch.Tensor | None = None) -> torch.Tensor:
+        out = self.empty() if out is None else out
+        _binding.check("mfcg_rhs", self._lib.mfcg_rhs(self._h, _ptr(self._vec(out, "b"))))
+        return out
+
+    def cg_solve(self, b: torch.Tensor, x: torch.Tensor | None = None, rtol: float = 1e-10, maxit: int = 100000,
+                 allow_not_converged: bool = False):
+        """Solves A x = b; x (if given) is the initial guess and is overwritten.
+        Returns (x, info dict)."""
+        if x is None:
+            x = torch.zeros(self.n_dofs, dtype=torch.float64, device=self.device)
+        info = SolveInfo()
+        allowed = (_binding.OK, _binding.NOT_CONVERGED) if allow_not_converged else (_binding.OK,)
+        st = self._lib.mfcg_cg_solve(self._h, _ptr(self._vec(b, "b")), _ptr(self._vec(x, "x")), float(rtol),
+                                     int(maxit), ctypes.byref(info))
+        _binding.check("mfcg_cg_solve", st, allowed)
+        return x, info.as_dict()
+
+    def cg_solve_host(self, b: torch.Tensor, x: torch.Tensor, rtol: float = 1e-10, maxit: int = 100000,
+                      allow_not_converged: bool = False):
+        """The same solve with CPU float64 tensors (pinned for asynchronous copies)."""
+        for t, name in ((b, "b"), (x, "x")):
+            if t.device.type != "cpu" or t.dtype != torch.float64 or t.numel() != self.n_dofs or not t.is_contiguous():
+                raise ValueError(f"{name}: expected a contiguous CPU float64 tensor of {self.n_dofs} entries")
+        info = SolveInfo()
+        allowed = (_binding.OK, _binding.NOT_CONVERGED) if allow_not_converged else (_binding.OK,)
+        st = self._lib.mfcg_cg_solve_host(self._h, _ptr(b), _ptr(x), float(rtol), int(maxit), ctypes.byref(info))
+        _binding.check("mfcg_cg_solve_host", st, allowed)
+        return x, info.as_dict()
+
+    def to_lexicographic(self, v: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        out = self.empty() if out is None else out
+        _binding.check("mfcg_to_lexicographic", self._lib.mfcg_to_lexicographic(
+            self._h, _ptr(self._vec(v, "in")), _ptr(self._vec(out, "out"))))
+        return out
+
+    def from_lexicographic(self, v: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        out = self.empty() if out is None else out
+        _binding.check("mfcg_from_lexicographic", self._lib.mfcg_from_lexicographic(
+            self._h, _ptr(self._vec(v, "in")), _ptr(self._vec(out, "out"))))
+        return out
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            self._lib.mfcg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

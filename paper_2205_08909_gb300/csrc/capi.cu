@@ -1,0 +1,501 @@
+// C ABI of the library (include/mfcg.h): problem setup, operator, diagonal,
+// right-hand side, the fused (Algorithm 5) and unfused (Algorithm 1) CG
+// drivers and the reordering helpers.
+//
+// Execution model: every call runs on a private non-blocking stream that is
+// ordered after the caller's stream on entry and before it on exit (events),
+// so CUDA graphs can be captured even when the caller uses the legacy stream.
+// The CG iterations are captured once per problem as a graph of G iterations
+// (an even number: odd and even iterations use swapped ping-pong buffers);
+// the host replays it and reads the device-side convergence flag only once per
+// graph, one graph behind, so there is no per-iteration host synchronisation.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "mfcg_internal.h"
+
+namespace mfcg {
+void build_coeffs(int p, const double h[3], double amplitude, int coef, OperatorCoeffs& c);
+int vec_grid(int64_t n);
+}  // namespace mfcg
+
+using namespace mfcg;
+
+struct mfcg_problem {
+  int device = 0;
+  cudaStream_t user = nullptr;
+  cudaStream_t exec = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  int degree = 0;
+  mfcg_mesh mesh{};
+  mfcg_geometry geom{};
+  mfcg_options opt{};
+  TileGeom g{};
+  OperatorCoeffs c{};
+  int geom_kind = GEOM_AFFINE;
+  double* r[2] = {nullptr, nullptr};
+  double* p[2] = {nullptr, nullptr};
+  double* v[2] = {nullptr, nullptr};
+  double* x = nullptr;
+  double* z = nullptr;
+  double* work = nullptr;
+  double* bdev = nullptr;   // host-array solves: b
+  double* xdev = nullptr;   // host-array solves: x
+  double* diag = nullptr;
+  double* diag_inv = nullptr;
+  double* shell = nullptr;
+  double* partial = nullptr;
+  double* geo = nullptr;
+  CGState* state = nullptr;
+  CGState* h_state = nullptr;  // pinned, two slots
+  int64_t tail_nodes = 0;
+  int64_t fam[3] = {0, 0, 0};
+  int tail_ctas = 1;
+  int graph_iters = 16;
+  cudaGraphExec_t graph_fused = nullptr;
+  cudaGraphExec_t graph_unfused = nullptr;
+  int64_t launches = 0;
+};
+
+namespace {
+
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return MFCG_CUDA_ERROR; \
+  } while (0)
+
+int alloc(double** p, int64_t n) {
+  if (cudaMalloc(p, (size_t)std::max<int64_t>(n, 1) * sizeof(double)) != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return MFCG_OUT_OF_MEMORY;
+  }
+  return MFCG_OK;
+}
+
+// default tile edge (cells) per degree: node bricks of about 17^3
+int default_tile(int p, int geom) {
+  static const int affine[9] = {0, 16, 8, 5, 4, 3, 3, 2, 2};
+  static const int deformed[9] = {0, 8, 4, 4, 3, 2, 2, 2, 2};
+  return geom == GEOM_AFFINE ? affine[p] : deformed[p];
+}
+
+TileArgs base_args(const mfcg_problem* P) {
+  TileArgs a{};
+  a.g = P->g;
+  a.shell = P->shell;
+  a.partial = P->partial;
+  a.geo = P->geo;
+  a.state = P->state;
+  a.tail_nodes = P->tail_nodes;
+  for (int d = 0; d < 3; ++d) a.fam[d] = P->fam[d];
+  a.geom = P->geom_kind;
+  a.tail_ctas = P->tail_ctas;
+  return a;
+}
+
+// operator-like pass (tile kernel + tail): src -> dst in mode
+int run_pass(mfcg_problem* P, int mode, const double* src, double* dst) {
+  TileArgs a = base_args(P);
+  a.in0 = src;
+  a.out0 = dst;
+  CK(launch_tile(P->degree, mode, a, P->c, P->exec));
+  CK(launch_tail(P->degree, mode, a, P->exec));
+  P->launches += 2;
+  return MFCG_OK;
+}
+
+// one fused CG iteration of the given parity (odd: buffers 0 -> 1)
+int enqueue_fused_iteration(mfcg_problem* P, int odd, cudaEvent_t t0, cudaEvent_t t1) {
+  const int o = odd ? 0 : 1, n = odd ? 1 : 0;
+  TileArgs a = base_args(P);
+  a.in0 = P->r[o];
+  a.in1 = P->v[o];
+  a.in2 = P->p[o];
+  a.diag_inv = P->diag_inv;
+  a.out0 = P->r[n];
+  a.out1 = P->v[n];
+  a.out2 = P->p[n];
+  a.x = P->x;
+  if (t0) CK(cudaEventRecord(t0, P->exec));
+  CK(launch_tile(P->degree, MODE_CG, a, P->c, P->exec));
+  if (t1) CK(cudaEventRecord(t1, P->exec));
+  CK(launch_tail(P->degree, MODE_CG, a, P->exec));
+  return MFCG_OK;
+}
+
+UnfusedArgs unfused_args(mfcg_problem* P) {
+  UnfusedArgs u{};
+  u.n = P->g.n_dofs;
+  u.diag_inv = P->diag_inv;
+  u.x = P->x;
+  u.r = P->r[0];
+  u.p = P->p[0];
+  u.v = P->v[0];
+  u.z = P->z;
+  u.partial = P->partial;
+  u.state = P->state;
+  return u;
+}
+
+int enqueue_unfused_iteration(mfcg_problem* P, cudaEvent_t t0, cudaEvent_t t1) {
+  UnfusedArgs u = unfused_args(P);
+  if (t0) CK(cudaEventRecord(t0, P->exec));
+  // v = A p
+  TileArgs a = base_args(P);
+  a.in0 = u.p;
+  a.out0 = u.v;
+  CK(launch_tile(P->degree, MODE_OPERATOR, a, P->c, P->exec));
+  if (t1) CK(cudaEventRecord(t1, P->exec));
+  CK(launch_tail(P->degree, MODE_OPERATOR, a, P->exec));
+  CK(launch_unfused_dot(0, u, P->exec));   // alpha = e / p.v
+  CK(launch_unfused_axpy(0, u, P->exec));  // x += alpha p
+  CK(launch_unfused_axpy(1, u, P->exec));  // r -= alpha v
+  CK(launch_unfused_dot(1, u, P->exec));   // gamma = r.r, convergence
+  CK(launch_unfused_axpy(2, u, P->exec));  // z = M^-1 r
+  CK(launch_unfused_dot(2, u, P->exec));   // beta = r.z / e
+  CK(launch_unfused_axpy(3, u, P->exec));  // p = z + beta p
+  return MFCG_OK;
+}
+
+constexpr int kFusedLaunchesPerIter = 2;
+constexpr int kUnfusedLaunchesPerIter = 9;
+
+int capture_graph(mfcg_problem* P, int fused, cudaGraphExec_t* out) {
+  cudaGraph_t graph;
+  CK(cudaStreamBeginCapture(P->exec, cudaStreamCaptureModeThreadLocal));
+  int st = MFCG_OK;
+  for (int it = 0; it < P->graph_iters && st == MFCG_OK; ++it)
+    st = fused ? enqueue_fused_iteration(P, (it & 1) == 0, nullptr, nullptr)
+               : enqueue_unfused_iteration(P, nullptr, nullptr);
+  cudaError_t e = cudaStreamEndCapture(P->exec, &graph);
+  if (st != MFCG_OK || e != cudaSuccess) return MFCG_CUDA_ERROR;
+  e = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  return e == cudaSuccess ? MFCG_OK : MFCG_CUDA_ERROR;
+}
+
+int enter(mfcg_problem* P) {
+  CK(cudaSetDevice(P->device));
+  CK(cudaEventRecord(P->ev_in, P->user));
+  CK(cudaStreamWaitEvent(P->exec, P->ev_in, 0));
+  return MFCG_OK;
+}
+
+int leave(mfcg_problem* P) {
+  CK(cudaEventRecord(P->ev_out, P->exec));
+  CK(cudaStreamWaitEvent(P->user, P->ev_out, 0));
+  return MFCG_OK;
+}
+
+int solve_impl(mfcg_problem* P, const double* b, double* x_user, double rtol, int maxit, mfcg_solve_info* info) {
+  const int64_t n = P->g.n_dofs;
+  const int fused = P->opt.mode == MFCG_MODE_FUSED;
+  const int64_t launches0 = P->launches;
+  int st;
+  // x0 into the internal solution buffer, r0 = b - A x0
+  CK(cudaMemcpyAsync(P->x, x_user, n * sizeof(double), cudaMemcpyDeviceToDevice, P->exec));
+  if ((st = run_pass(P, MODE_OPERATOR, P->x, P->work)) != MFCG_OK) return st;
+  CK(launch_residual(b, P->work, P->r[0], n, P->exec));
+  CK(launch_fill(P->p[0], 0.0, n, P->exec));
+  CK(launch_fill(P->v[0], 0.0, n, P->exec));
+  const int fixed = rtol == 0.0;
+  CK(launch_cg_init(P->state, b, P->r[0], n, rtol, maxit, fixed, P->partial, 0, P->exec));
+  P->launches += 4;
+  if (!fused) {
+    UnfusedArgs u = unfused_args(P);
+    CK(launch_unfused_dot(3, u, P->exec));  // z0 = M^-1 r0, p0 = z0, e0 = r0.z0
+    P->launches += 1;
+  }
+  const int per_iter = fused ? kFusedLaunchesPerIter : kUnfusedLaunchesPerIter;
+  double main_ms = 0.0;
+  int main_launches = 0;
+  if (P->opt.instrument) {
+    // direct launches with an event pair around every operator-pass kernel
+    std::vector<cudaEvent_t> ev;
+    int done_it = 0;
+    while (done_it < maxit) {
+      const int chunk = std::min(64, maxit - done_it);
+      ev.resize(2 * chunk);
+      for (auto& e : ev) CK(cudaEventCreate(&e));
+      for (int i = 0; i < chunk; ++i) {
+        const int k = done_it + i + 1;
+        st = fused ? enqueue_fused_iteration(P, k & 1, ev[2 * i], ev[2 * i + 1])
+                   : enqueue_unfused_iteration(P, ev[2 * i], ev[2 * i + 1]);
+        if (st != MFCG_OK) return st;
+      }
+      P->launches += (int64_t)chunk * per_iter;
+      CK(cudaMemcpyAsync(P->h_state, P->state, sizeof(CGState), cudaMemcpyDeviceToHost, P->exec));
+      CK(cudaStreamSynchronize(P->exec));
+      const int ran = std::min(chunk, std::max(0, P->h_state->iterations - done_it));
+      for (int i = 0; i < ran; ++i) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]));
+        main_ms += ms;
+        ++main_launches;
+      }
+      for (auto& e : ev) cudaEventDestroy(e);
+      done_it += chunk;
+      if (P->h_state->done) break;
+    }
+  } else {
+    cudaGraphExec_t* gexec = fused ? &P->graph_fused : &P->graph_unfused;
+    if (!*gexec && (st = capture_graph(P, fused, gexec)) != MFCG_OK) return st;
+    const int G = P->graph_iters;
+    const int n_graphs = (maxit + G - 1) / G;
+    // keep one graph in flight ahead of the flag we read
+    cudaEvent_t evs[2];
+    CK(cudaEventCreateWithFlags(&evs[0], cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&evs[1], cudaEventDisableTiming));
+    int launched = 0, checked = 0;
+    bool finished = false;
+    while (!finished) {
+      while (launched < n_graphs && launched < checked + 2) {
+        CK(cudaGraphLaunch(*gexec, P->exec));
+        CK(cudaMemcpyAsync(P->h_state + (launched & 1), P->state, sizeof(CGState), cudaMemcpyDeviceToHost, P->exec));
+        CK(cudaEventRecord(evs[launched & 1], P->exec));
+        P->launches += (int64_t)G * per_iter;
+        ++launched;
+      }
+      if (checked >= launched) break;
+      CK(cudaEventSynchronize(evs[checked & 1]));
+      if (P->h_state[checked & 1].done) finished = true;
+      ++checked;
+      if (checked >= n_graphs) finished = true;
+    }
+    CK(cudaStreamSynchronize(P->exec));
+    cudaEventDestroy(evs[0]);
+    cudaEventDestroy(evs[1]);
+  }
+  if (fused) {
+    CK(launch_finalize_fused(P->g, P->state, P->x, P->p[0], P->p[1], P->r[0], P->r[1], P->diag_inv, P->exec));
+    P->launches += 1;
+  }
+  CK(cudaMemcpyAsync(x_user, P->x, n * sizeof(double), cudaMemcpyDeviceToDevice, P->exec));
+  CK(cudaMemcpyAsync(P->h_state, P->state, sizeof(CGState), cudaMemcpyDeviceToHost, P->exec));
+  CK(cudaStreamSynchronize(P->exec));
+  const CGState& S = *P->h_state;
+  int status = MFCG_OK;
+  if (S.done == 3) status = MFCG_BREAKDOWN;
+  else if (S.done != 1 && !fixed) status = MFCG_NOT_CONVERGED;
+  if (info) {
+    info->iterations = S.iterations;
+    info->converged = S.done == 1;
+    info->status = status;
+    info->main_kernel_launches = main_launches;
+    info->residual_sq_est = S.gamma_next;
+    info->rhs_norm_sq = S.sums[7];
+    info->main_kernel_ms = main_ms;
+    info->kernel_launches = P->launches - launches0;
+  }
+  return status;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mfcg_status_string(int status) {
+  switch (status) {
+    case MFCG_OK: return "ok";
+    case MFCG_INVALID_ARG: return "invalid argument";
+    case MFCG_UNSUPPORTED_DEGREE: return "unsupported polynomial degree (1..8)";
+    case MFCG_OUT_OF_MEMORY: return "device allocation failed";
+    case MFCG_CUDA_ERROR: return "CUDA runtime error";
+    case MFCG_NOT_CONVERGED: return "maximum number of iterations reached";
+    case MFCG_BREAKDOWN: return "CG breakdown (non-positive or non-finite inner product)";
+    case MFCG_DEVICE_TIMEOUT: return "bounded device wait expired";
+    default: return "unknown status";
+  }
+}
+
+int mfcg_destroy(mfcg_problem* P) {
+  if (!P) return MFCG_OK;
+  cudaSetDevice(P->device);
+  if (P->exec) cudaStreamSynchronize(P->exec);
+  if (P->graph_fused) cudaGraphExecDestroy(P->graph_fused);
+  if (P->graph_unfused) cudaGraphExecDestroy(P->graph_unfused);
+  double* bufs[] = {P->r[0], P->r[1], P->p[0], P->p[1], P->v[0], P->v[1], P->x, P->z, P->work,
+                    P->bdev, P->xdev, P->diag, P->diag_inv, P->shell, P->partial, P->geo};
+  for (double* b : bufs)
+    if (b) cudaFree(b);
+  if (P->state) cudaFree(P->state);
+  if (P->h_state) cudaFreeHost(P->h_state);
+  if (P->ev_in) cudaEventDestroy(P->ev_in);
+  if (P->ev_out) cudaEventDestroy(P->ev_out);
+  if (P->exec) cudaStreamDestroy(P->exec);
+  delete P;
+  return MFCG_OK;
+}
+
+int mfcg_setup(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, const mfcg_options* opt,
+               void* cuda_stream, mfcg_problem** out) {
+  if (!mesh || !geom || !out) return MFCG_INVALID_ARG;
+  *out = nullptr;
+  if (degree < 1 || degree > kMaxDegree) return MFCG_UNSUPPORTED_DEGREE;
+  if (mesh->nx < 1 || mesh->ny < 1 || mesh->nz < 1) return MFCG_INVALID_ARG;
+  if (!(std::fabs(mesh->amplitude) < 0.1)) return MFCG_INVALID_ARG;
+  if (geom->kind != MFCG_GEOM_AFFINE && geom->kind != MFCG_GEOM_DEFORMED) return MFCG_INVALID_ARG;
+  if (geom->coefficient != MFCG_COEF_CONSTANT && geom->coefficient != MFCG_COEF_SIN_X) return MFCG_INVALID_ARG;
+  if (geom->kind == MFCG_GEOM_AFFINE && (mesh->amplitude != 0.0 || geom->coefficient != MFCG_COEF_CONSTANT))
+    return MFCG_INVALID_ARG;
+  mfcg_options o{};
+  if (opt) o = *opt;
+  if (o.mode != MFCG_MODE_FUSED && o.mode != MFCG_MODE_UNFUSED) return MFCG_INVALID_ARG;
+  if (o.graph_iterations < 0 || (o.graph_iterations & 1)) return MFCG_INVALID_ARG;
+  for (int d = 0; d < 3; ++d)
+    if (o.tile[d] < 0) return MFCG_INVALID_ARG;
+  const int64_t nn[3] = {(int64_t)degree * mesh->nx + 1, (int64_t)degree * mesh->ny + 1, (int64_t)degree * mesh->nz + 1};
+  if (nn[0] > (1 << 20) || nn[1] > (1 << 20) || nn[2] > (1 << 20)) return MFCG_INVALID_ARG;
+
+  mfcg_problem* P = new (std::nothrow) mfcg_problem();
+  if (!P) return MFCG_OUT_OF_MEMORY;
+  int st = MFCG_OK;
+  auto fail = [&](int code) {
+    mfcg_destroy(P);
+    return code;
+  };
+  if (cudaGetDevice(&P->device) != cudaSuccess) return fail(MFCG_CUDA_ERROR);
+  P->user = (cudaStream_t)cuda_stream;
+  P->degree = degree;
+  P->mesh = *mesh;
+  P->geom = *geom;
+  P->opt = o;
+  P->geom_kind = geom->kind == MFCG_GEOM_AFFINE ? GEOM_AFFINE : GEOM_DEFORMED;
+  P->graph_iters = o.graph_iterations ? o.graph_iterations : 16;
+  if (cudaStreamCreateWithFlags(&P->exec, cudaStreamNonBlocking) != cudaSuccess) return fail(MFCG_CUDA_ERROR);
+  if (cudaEventCreateWithFlags(&P->ev_in, cudaEventDisableTiming) != cudaSuccess) return fail(MFCG_CUDA_ERROR);
+  if (cudaEventCreateWithFlags(&P->ev_out, cudaEventDisableTiming) != cudaSuccess) return fail(MFCG_CUDA_ERROR);
+
+  TileGeom& g = P->g;
+  const int N[3] = {mesh->nx, mesh->ny, mesh->nz};
+  int T[3];
+  for (int d = 0; d < 3; ++d) {
+    T[d] = o.tile[d] ? o.tile[d] : default_tile(degree, P->geom_kind);
+    if (degree == 1 && T[d] < 2) T[d] = 2;
+  }
+  init_tile_geom(degree, N, T, g, P->fam);
+  const size_t smem = tile_smem_bytes(degree, P->geom_kind, g) + 8 * (kThreads / 32) * sizeof(double);
+  int max_smem = 0;
+  cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device);
+  if (smem > (size_t)max_smem) return fail(MFCG_INVALID_ARG);
+  if (prepare_tile(degree, P->geom_kind, tile_smem_bytes(degree, P->geom_kind, g)) != cudaSuccess)
+    return fail(MFCG_CUDA_ERROR);
+
+  P->tail_nodes = P->fam[0] + P->fam[1] + P->fam[2];
+  P->tail_ctas = (int)std::min<int64_t>(std::max<int64_t>((P->tail_nodes + kThreads - 1) / kThreads, 1), 152 * 8);
+
+  const double h[3] = {1.0 / N[0], 1.0 / N[1], 1.0 / N[2]};
+  build_coeffs(degree, h, mesh->amplitude, geom->coefficient, P->c);
+
+  const int64_t n = g.n_dofs;
+  for (int i = 0; i < 2 && st == MFCG_OK; ++i) {
+    if ((st = alloc(&P->r[i], n)) != MFCG_OK) break;
+    if ((st = alloc(&P->p[i], n)) != MFCG_OK) break;
+    st = alloc(&P->v[i], n);
+  }
+  if (st == MFCG_OK) st = alloc(&P->x, n);
+  if (st == MFCG_OK && o.mode == MFCG_MODE_UNFUSED) st = alloc(&P->z, n);
+  if (st == MFCG_OK) st = alloc(&P->work, n);
+  if (st == MFCG_OK) st = alloc(&P->diag, n);
+  if (st == MFCG_OK) st = alloc(&P->diag_inv, n);
+  if (st == MFCG_OK) st = alloc(&P->shell, g.n_tiles * g.face_stride);
+  const int64_t nparts = std::max<int64_t>(g.n_tiles + P->tail_ctas, 152 * 8);
+  if (st == MFCG_OK) st = alloc(&P->partial, nparts * 8);
+  if (st == MFCG_OK && P->geom_kind == GEOM_DEFORMED)
+    st = alloc(&P->geo, (int64_t)N[0] * N[1] * N[2] * 10 * (degree + 1) * (degree + 1) * (degree + 1));
+  if (st != MFCG_OK) return fail(st);
+  if (cudaMalloc(&P->state, sizeof(CGState)) != cudaSuccess) return fail(MFCG_OUT_OF_MEMORY);
+  if (cudaMallocHost(&P->h_state, 2 * sizeof(CGState)) != cudaSuccess) return fail(MFCG_OUT_OF_MEMORY);
+  if (cudaMemsetAsync(P->state, 0, sizeof(CGState), P->exec) != cudaSuccess) return fail(MFCG_CUDA_ERROR);
+  if (enter(P) != MFCG_OK) return fail(MFCG_CUDA_ERROR);
+  if (P->geom_kind == GEOM_DEFORMED && launch_geometry(g, P->c, P->geo, P->exec) != cudaSuccess)
+    return fail(MFCG_CUDA_ERROR);
+  // Jacobi preconditioner: exact diagonal and its inverse
+  if ((st = run_pass(P, MODE_DIAG, nullptr, P->diag)) != MFCG_OK) return fail(st);
+  if (launch_invert(P->diag, P->diag_inv, n, P->exec) != cudaSuccess) return fail(MFCG_CUDA_ERROR);
+  if (cudaStreamSynchronize(P->exec) != cudaSuccess) return fail(MFCG_CUDA_ERROR);
+  if (leave(P) != MFCG_OK) return fail(MFCG_CUDA_ERROR);
+  *out = P;
+  return MFCG_OK;
+}
+
+int mfcg_n_dofs(const mfcg_problem* P, int64_t* n) {
+  if (!P || !n) return MFCG_INVALID_ARG;
+  *n = P->g.n_dofs;
+  return MFCG_OK;
+}
+
+int mfcg_apply_operator(mfcg_problem* P, const double* src, double* dst) {
+  if (!P || !src || !dst || src == dst) return MFCG_INVALID_ARG;
+  int st;
+  if ((st = enter(P)) != MFCG_OK) return st;
+  if ((st = run_pass(P, MODE_OPERATOR, src, dst)) != MFCG_OK) return st;
+  return leave(P);
+}
+
+int mfcg_diagonal(mfcg_problem* P, double* diag) {
+  if (!P || !diag) return MFCG_INVALID_ARG;
+  int st;
+  if ((st = enter(P)) != MFCG_OK) return st;
+  CK(cudaMemcpyAsync(diag, P->diag, P->g.n_dofs * sizeof(double), cudaMemcpyDeviceToDevice, P->exec));
+  return leave(P);
+}
+
+int mfcg_rhs(mfcg_problem* P, double* b) {
+  if (!P || !b) return MFCG_INVALID_ARG;
+  int st;
+  if ((st = enter(P)) != MFCG_OK) return st;
+  if ((st = run_pass(P, MODE_RHS, nullptr, b)) != MFCG_OK) return st;
+  return leave(P);
+}
+
+int mfcg_cg_solve(mfcg_problem* P, const double* b, double* x, double rtol, int maxit, mfcg_solve_info* info) {
+  if (!P || !b || !x || b == x || maxit < 0 || !(rtol >= 0.0)) return MFCG_INVALID_ARG;
+  int st;
+  if ((st = enter(P)) != MFCG_OK) return st;
+  st = solve_impl(P, b, x, rtol, maxit, info);
+  const int st2 = leave(P);
+  return st != MFCG_OK ? st : st2;
+}
+
+int mfcg_cg_solve_host(mfcg_problem* P, const double* b_host, double* x_host, double rtol, int maxit,
+                       mfcg_solve_info* info) {
+  if (!P || !b_host || !x_host || maxit < 0 || !(rtol >= 0.0)) return MFCG_INVALID_ARG;
+  const int64_t n = P->g.n_dofs;
+  int st;
+  if ((st = enter(P)) != MFCG_OK) return st;
+  if (!P->bdev && (st = alloc(&P->bdev, n)) != MFCG_OK) return st;
+  if (!P->xdev && (st = alloc(&P->xdev, n)) != MFCG_OK) return st;
+  CK(cudaMemcpyAsync(P->bdev, b_host, n * sizeof(double), cudaMemcpyHostToDevice, P->exec));
+  CK(cudaMemcpyAsync(P->xdev, x_host, n * sizeof(double), cudaMemcpyHostToDevice, P->exec));
+  st = solve_impl(P, P->bdev, P->xdev, rtol, maxit, info);
+  if (st != MFCG_OK && st != MFCG_NOT_CONVERGED && st != MFCG_BREAKDOWN) return st;
+  CK(cudaMemcpyAsync(x_host, P->xdev, n * sizeof(double), cudaMemcpyDeviceToHost, P->exec));
+  CK(cudaStreamSynchronize(P->exec));
+  const int st2 = leave(P);
+  return st != MFCG_OK ? st : st2;
+}
+
+int mfcg_to_lexicographic(mfcg_problem* P, const double* in, double* out) {
+  if (!P || !in || !out || in == out) return MFCG_INVALID_ARG;
+  int st;
+  if ((st = enter(P)) != MFCG_OK) return st;
+  CK(launch_reorder(P->g, in, out, 1, P->exec));
+  return leave(P);
+}
+
+int mfcg_from_lexicographic(mfcg_problem* P, const double* in, double* out) {
+  if (!P || !in || !out || in == out) return MFCG_INVALID_ARG;
+  int st;
+  if ((st = enter(P)) != MFCG_OK) return st;
+  CK(launch_reorder(P->g, in, out, 0, P->exec));
+  return leave(P);
+}
+
+}  // extern "C"

@@ -1,0 +1,267 @@
+// Internal declarations of the mfcg library: tile geometry, DoF numbering,
+// kernel argument blocks and launch entry points.  Nothing here is part of the
+// C ABI (include/mfcg.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mfcg.h"
+
+namespace mfcg {
+
+constexpr int kMaxDegree = 8;
+constexpr int kThreads = 256;  // threads per CTA of every tile kernel
+
+// ------------------------------------------------------------------------------------
+// Tile geometry and the tile-blocked numbering of unknowns (Sec. 5.3).
+//
+// Cells are grouped into tiles of T[0] x T[1] x T[2] cells (ragged at the high
+// end).  Every mesh node is owned by exactly one tile: along each direction
+// the node index i (0..p*N) belongs to tile min(i / (p*T), nt-1), so a tile
+// owns the nodes [p*T*t, p*T*(t+1)) and the last tile also owns the final
+// node plane.  The unknowns of a tile are numbered contiguously (tiles in
+// lexicographic order, x fastest; inside a tile lexicographic), which is the
+// GPU form of "unknowns touched by a single cell batch are numbered together".
+// ------------------------------------------------------------------------------------
+struct TileGeom {
+  int p;
+  int N[3];         // cells per direction
+  int T[3];         // cells per tile per direction
+  int nt[3];        // tiles per direction
+  int nn[3];        // nodes per direction, p*N+1
+  int own_last[3];  // nodes owned by the last tile per direction
+  int face_stride;  // doubles per tile in the shell (face partial) buffer
+  int64_t n_tiles;
+  int64_t n_dofs;
+};
+
+__host__ __device__ inline int tile_of(const TileGeom& g, int d, int i) {
+  int t = i / (g.p * g.T[d]);
+  return t < g.nt[d] - 1 ? t : g.nt[d] - 1;
+}
+
+__host__ __device__ inline int owned_count(const TileGeom& g, int d, int t) {
+  return t == g.nt[d] - 1 ? g.own_last[d] : g.p * g.T[d];
+}
+
+// position of node (i,j,k) in the tile-blocked vector
+__host__ __device__ inline int64_t node_index(const TileGeom& g, int i, int j, int k) {
+  const int tx = tile_of(g, 0, i), ty = tile_of(g, 1, j), tz = tile_of(g, 2, k);
+  const int ox = owned_count(g, 0, tx), oy = owned_count(g, 1, ty), oz = owned_count(g, 2, tz);
+  const int pTx = g.p * g.T[0], pTy = g.p * g.T[1], pTz = g.p * g.T[2];
+  const int li = i - pTx * tx, lj = j - pTy * ty, lk = k - pTz * tz;
+  const int64_t base = (int64_t)g.nn[0] * g.nn[1] * pTz * tz + (int64_t)g.nn[0] * pTy * ty * oz +
+                       (int64_t)pTx * tx * oy * oz;
+  return base + li + (int64_t)ox * (lj + (int64_t)oy * lk);
+}
+
+__host__ __device__ inline bool is_dirichlet(const TileGeom& g, int i, int j, int k) {
+  return i == 0 || j == 0 || k == 0 || i == g.nn[0] - 1 || j == g.nn[1] - 1 || k == g.nn[2] - 1;
+}
+
+// Shell buffer: every tile stores the partial operator result of its boundary
+// nodes that are shared with a neighbouring tile, face by face (x-, x+, y-, y+,
+// z-, z+); a node on several faces of the tile is stored on the first of them
+// in that order.  Slot of tile-local node (li,lj,lk) with brick extents
+// bx,by,bz (= p*cells+1 of this tile) and maximal extents Bx,By,Bz.
+__host__ __device__ inline int shell_slot(const TileGeom& g, int li, int lj, int lk, int bx, int by, int bz) {
+  const int Bx = g.p * g.T[0] + 1, By = g.p * g.T[1] + 1, Bz = g.p * g.T[2] + 1;
+  const int FX = By * Bz, FY = Bx * Bz, FZ = Bx * By;
+  if (li == 0) return lj + By * lk;
+  if (li == bx - 1) return FX + lj + By * lk;
+  if (lj == 0) return 2 * FX + li + Bx * lk;
+  if (lj == by - 1) return 2 * FX + FY + li + Bx * lk;
+  if (lk == 0) return 2 * FX + 2 * FY + li + Bx * lj;
+  return 2 * FX + 2 * FY + FZ + li + Bx * lj;
+}
+
+// ------------------------------------------------------------------------------------
+// Enumeration of the shared-face nodes finalised by the tail kernel: interior
+// (non-Dirichlet) nodes lying on at least one tile boundary plane, split into
+// three families (on an x plane; on a y plane but no x plane; on a z plane
+// only), each a product set that is decoded arithmetically.
+// ------------------------------------------------------------------------------------
+// rank r of an interior node index that is not a tile boundary plane -> index
+__host__ __device__ inline int skip_planes(int r, int pT) { return r + 1 + r / (pT - 1); }
+
+__host__ __device__ inline void decode_tail_node(const TileGeom& g, const int64_t (&fam)[3], int64_t t, int& i, int& j, int& k) {
+  const int pTx = g.p * g.T[0], pTy = g.p * g.T[1], pTz = g.p * g.T[2];
+  const int niy = g.nn[1] - 2, niz = g.nn[2] - 2;
+  const int nbx = g.nt[0] - 1, nby = g.nt[1] - 1;
+  if (t < fam[0]) {  // i on an x plane, j, k interior
+    const int64_t per = (int64_t)niy * niz;
+    const int b = (int)(t / per);
+    const int64_t rem = t - b * per;
+    i = pTx * (b + 1);
+    j = 1 + (int)(rem % niy);
+    k = 1 + (int)(rem / niy);
+    return;
+  }
+  t -= fam[0];
+  const int nxr = g.nn[0] - 2 - nbx;  // interior x indices off the x planes
+  if (t < fam[1]) {  // j on a y plane
+    const int64_t per = (int64_t)nxr * niz;
+    const int b = (int)(t / per);
+    const int64_t rem = t - b * per;
+    j = pTy * (b + 1);
+    i = skip_planes((int)(rem % nxr), pTx);
+    k = 1 + (int)(rem / nxr);
+    return;
+  }
+  t -= fam[1];
+  const int nyr = g.nn[1] - 2 - nby;
+  const int64_t per = (int64_t)nxr * nyr;
+  const int b = (int)(t / per);
+  const int64_t rem = t - b * per;
+  k = pTz * (b + 1);
+  i = skip_planes((int)(rem % nxr), pTx);
+  j = skip_planes((int)(rem / nxr), pTy);
+}
+
+// tiles containing node index i along direction d: up to two (tile, local index) pairs
+__host__ __device__ inline int contributors(const TileGeom& g, int d, int i, int (&t)[2], int (&l)[2]) {
+  const int pT = g.p * g.T[d];
+  if (i % pT == 0 && i > 0 && i < g.nn[d] - 1) {
+    t[0] = i / pT - 1;
+    l[0] = pT;
+    t[1] = i / pT;
+    l[1] = 0;
+    return 2;
+  }
+  t[0] = tile_of(g, d, i);
+  l[0] = i - pT * t[0];
+  return 1;
+}
+
+__host__ __device__ inline int brick_extent(const TileGeom& g, int d, int t) {
+  const int cells = g.N[d] - t * g.T[d];
+  return g.p * (g.T[d] < cells ? g.T[d] : cells) + 1;
+}
+
+// Tile geometry for degree p, cells N and tile edges T (each clamped to N),
+// and the sizes of the three tail-node families.
+inline void init_tile_geom(int p, const int N[3], const int T[3], TileGeom& g, int64_t (&fam)[3]) {
+  g.p = p;
+  for (int d = 0; d < 3; ++d) {
+    g.N[d] = N[d];
+    g.T[d] = T[d] < N[d] ? T[d] : N[d];
+    g.nt[d] = (N[d] + g.T[d] - 1) / g.T[d];
+    g.nn[d] = p * N[d] + 1;
+    g.own_last[d] = g.nn[d] - p * g.T[d] * (g.nt[d] - 1);
+  }
+  const int Bx = p * g.T[0] + 1, By = p * g.T[1] + 1, Bz = p * g.T[2] + 1;
+  g.face_stride = 2 * (By * Bz + Bx * Bz + Bx * By);
+  g.n_tiles = (int64_t)g.nt[0] * g.nt[1] * g.nt[2];
+  g.n_dofs = (int64_t)g.nn[0] * g.nn[1] * g.nn[2];
+  const int64_t nbx = g.nt[0] - 1, nby = g.nt[1] - 1, nbz = g.nt[2] - 1;
+  const int64_t nix = g.nn[0] - 2, niy = g.nn[1] - 2, niz = g.nn[2] - 2;
+  fam[0] = fam[1] = fam[2] = 0;
+  if (nix > 0 && niy > 0 && niz > 0) {
+    fam[0] = nbx * niy * niz;
+    fam[1] = nby * (nix - nbx) * niz;
+    fam[2] = nbz * (nix - nbx) * (niy - nby);
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Device-resident CG scalars (Algorithm 5 / Algorithm 1); no host round trip
+// per iteration.
+// ------------------------------------------------------------------------------------
+struct CGState {
+  double alpha_prev, beta_prev;    // alpha_{k-1}, beta_{k-1}
+  double alpha_prev2, beta_prev2;  // alpha_{k-2}, beta_{k-2}
+  double alpha_cur;                // alpha_k of the last finished iteration
+  double gamma_next;               // ||r_{k+1}||^2 (Eq. 8 expansion or explicit)
+  double eps_sq;                   // (rtol ||b||)^2
+  double e_cur;                    // r^T z of Algorithm 1 (unfused path)
+  double sums[8];                  // last reduced sums
+  int k;                           // iteration to run next (1-based)
+  int done;                        // 0 running, 1 converged, 2 maxit, 3 breakdown
+  int maxit;
+  int iterations;                  // finished iterations
+  unsigned int ticket;             // last-CTA election counter
+  int x_every_iter;                // 1 once beta_{k-2} underflows: x updated every iteration
+  int fixed;                       // 1: ignore the tolerance, run maxit iterations
+  int pad;
+};
+
+enum TileMode { MODE_OPERATOR = 0, MODE_CG = 1, MODE_RHS = 2, MODE_DIAG = 3 };
+
+enum GeomKind { GEOM_AFFINE = 0, GEOM_DEFORMED = 1 };
+
+struct OperatorCoeffs {
+  // 1D matrices, row-major (P+1)x(P+1): for the affine Kronecker form the mass
+  // matrix M and the per-direction scaled stiffness matrices K_d; for the
+  // deformed form the interpolation S (Gauss points x GL nodes) and the Gauss
+  // collocation derivative Dc.
+  double M[(kMaxDegree + 1) * (kMaxDegree + 1)];
+  double K[3][(kMaxDegree + 1) * (kMaxDegree + 1)];
+  double S[(kMaxDegree + 1) * (kMaxDegree + 1)];
+  double Dc[(kMaxDegree + 1) * (kMaxDegree + 1)];
+  // products of 1D tables used by the exact diagonal: SS = S.*S, DS = D.*S,
+  // DD = D.*D with D[q][a] = L_a'(g_q) (Gauss points x GL nodes)
+  double T2[3][(kMaxDegree + 1) * (kMaxDegree + 1)];
+  double w[kMaxDegree + 1];  // Gauss weights on [0,1]
+  double g[kMaxDegree + 1];  // Gauss points on [0,1]
+  double h[3];               // cell sizes
+  double amplitude;
+  int coef;
+};
+
+struct TileArgs {
+  TileGeom g;
+  // operator mode: in0 = src, out0 = dst
+  // CG mode: in0 = r_old, in1 = v_old, in2 = p_old, diag_inv; out0 = r_new, out1 = v_new, out2 = p_new, x
+  const double* in0;
+  const double* in1;
+  const double* in2;
+  const double* diag_inv;
+  double* out0;
+  double* out1;
+  double* out2;
+  double* x;
+  double* shell;
+  double* partial;       // [n_tiles][8] (main) and [tail CTAs][8] (tail)
+  const double* geo;     // deformed: [cell][10][nq] = J^{-1} row-major, JxW*a
+  CGState* state;
+  int64_t tail_nodes;    // number of shared-face nodes handled by the tail kernel
+  int64_t fam[3];        // tail enumeration: nodes in the x / y / z boundary-plane families
+  int geom;              // GeomKind
+  int tail_ctas;
+};
+
+// launchers (one set per degree, see tile_kernels.cuh)
+cudaError_t launch_tile(int degree, int mode, const TileArgs& a, const OperatorCoeffs& c, cudaStream_t s);
+cudaError_t launch_tail(int degree, int mode, const TileArgs& a, cudaStream_t s);
+size_t tile_smem_bytes(int degree, int geom, const TileGeom& g);
+cudaError_t prepare_tile(int degree, int geom, size_t smem);
+
+// BLAS-1 / reduction / utility kernels (cg_kernels.cu)
+cudaError_t launch_fill(double* v, double value, int64_t n, cudaStream_t s);
+cudaError_t launch_invert(const double* in, double* out, int64_t n, cudaStream_t s);
+cudaError_t launch_reorder(const TileGeom& g, const double* in, double* out, int to_lex, cudaStream_t s);
+cudaError_t launch_geometry(const TileGeom& g, const OperatorCoeffs& c, double* geo, cudaStream_t s);
+
+// CG drivers (cg_kernels.cu)
+struct UnfusedArgs {
+  int64_t n;
+  const double* diag_inv;
+  double* x;
+  double* r;
+  double* p;
+  double* v;
+  double* z;
+  double* partial;
+  int n_ctas;
+  CGState* state;
+};
+cudaError_t launch_unfused_dot(int which, const UnfusedArgs& a, cudaStream_t s);
+cudaError_t launch_unfused_axpy(int which, const UnfusedArgs& a, cudaStream_t s);
+cudaError_t launch_cg_init(CGState* st, const double* b, const double* r0, int64_t n, double rtol, int maxit,
+                           int fixed, double* partial, int n_ctas, cudaStream_t s);
+cudaError_t launch_residual(const double* b, const double* ax, double* r, int64_t n, cudaStream_t s);
+cudaError_t launch_finalize_fused(const TileGeom& g, CGState* st, double* x, const double* p0, const double* p1,
+                                  const double* r0, const double* r1, const double* diag_inv, cudaStream_t s);
+
+}  // namespace mfcg

@@ -1,0 +1,699 @@
+// Tile kernels of the fused matrix-free CG: one CTA per tile of cells.
+//
+//   phase 1 ("pre", Algorithm 5):  r_k = r_{k-1} - alpha_{k-1} v_{k-1},
+//            p_k = D^{-1} r_k + beta_{k-1} p_{k-1} on every node of the tile
+//            (recomputed from the previous buffers for nodes shared with a
+//            neighbour tile, stored by the owner only), the delayed x update
+//            on odd k > 1, and p_k staged in shared memory;
+//   phase 2 (Eq. 4 / Eq. 5): sum-factorised cell integrals of all cells of the
+//            tile, accumulated into a shared-memory node brick, cells of one
+//            colour (parity of the cell index) at a time so that no two
+//            concurrent cells share a node;
+//   phase 3 ("post"): nodes whose last contribution came from this tile are
+//            final: v_k is stored and the seven sums of Algorithm 5 are
+//            accumulated; nodes on faces shared with another tile store their
+//            partial sum in the shell buffer.
+// The tail kernel adds the shell partials of the shared-face nodes in a fixed
+// order, finishes their post operation and, in its last CTA, reduces all
+// per-CTA sums in a fixed order and computes alpha_k, the Eq. 8 residual
+// estimate, the convergence flag and beta_k (Eq. 7) on the device.
+#pragma once
+
+#include "mfcg_internal.h"
+
+namespace mfcg {
+
+// ------------------------------------------------------------------------------------
+// 1D contractions on a pencil of N1 = P+1 values held in registers
+// ------------------------------------------------------------------------------------
+template <int N1>
+__device__ __forceinline__ void matvec(const double* __restrict__ A, const double (&x)[N1], double (&y)[N1]) {
+#pragma unroll
+  for (int i = 0; i < N1; ++i) {
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < N1; ++j) s = fma(A[i * N1 + j], x[j], s);
+    y[i] = s;
+  }
+}
+
+template <int N1>
+__device__ __forceinline__ void matvec_t(const double* __restrict__ A, const double (&x)[N1], double (&y)[N1]) {
+#pragma unroll
+  for (int i = 0; i < N1; ++i) {
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < N1; ++j) s = fma(A[j * N1 + i], x[j], s);
+    y[i] = s;
+  }
+}
+
+// position of element (a,b,c) of a cell array (x fastest)
+template <int N1>
+__device__ __forceinline__ int cidx(int a, int b, int c) {
+  return a + N1 * (b + N1 * c);
+}
+
+// pencil along direction `dir` with transverse indices (e1, e2): element s of the pencil
+template <int N1>
+__device__ __forceinline__ int pencil_idx(int dir, int e1, int e2, int s) {
+  return dir == 0 ? cidx<N1>(s, e1, e2) : (dir == 1 ? cidx<N1>(e1, s, e2) : cidx<N1>(e1, e2, s));
+}
+
+// In-place application of a 1D matrix (or its transpose) along `dir` to the
+// cell arrays arr + ci*stride, ci < nc.  Ends with a barrier.
+template <int P, bool TRANS>
+__device__ __forceinline__ void sweep_inplace(double* arr, int stride, int nc, int dir, const double* __restrict__ A) {
+  constexpr int N1 = P + 1, N2 = N1 * N1;
+  for (int t = threadIdx.x; t < nc * N2; t += kThreads) {
+    const int ci = t / N2, e = t - ci * N2, e1 = e % N1, e2 = e / N1;
+    double* a = arr + ci * stride;
+    double x[N1], y[N1];
+#pragma unroll
+    for (int s = 0; s < N1; ++s) x[s] = a[pencil_idx<N1>(dir, e1, e2, s)];
+    if (TRANS) matvec_t<N1>(A, x, y); else matvec<N1>(A, x, y);
+#pragma unroll
+    for (int s = 0; s < N1; ++s) a[pencil_idx<N1>(dir, e1, e2, s)] = y[s];
+  }
+  __syncthreads();
+}
+
+// out (+)= A^(T) in along `dir`, separate arrays.  Ends with a barrier.
+template <int P, bool TRANS, bool ACCUM>
+__device__ __forceinline__ void sweep_copy(const double* in, double* out, int stride, int nc, int dir,
+                                           const double* __restrict__ A) {
+  constexpr int N1 = P + 1, N2 = N1 * N1;
+  for (int t = threadIdx.x; t < nc * N2; t += kThreads) {
+    const int ci = t / N2, e = t - ci * N2, e1 = e % N1, e2 = e / N1;
+    const double* a = in + ci * stride;
+    double* o = out + ci * stride;
+    double x[N1], y[N1];
+#pragma unroll
+    for (int s = 0; s < N1; ++s) x[s] = a[pencil_idx<N1>(dir, e1, e2, s)];
+    if (TRANS) matvec_t<N1>(A, x, y); else matvec<N1>(A, x, y);
+#pragma unroll
+    for (int s = 0; s < N1; ++s) {
+      const int id = pencil_idx<N1>(dir, e1, e2, s);
+      o[id] = ACCUM ? o[id] + y[s] : y[s];
+    }
+  }
+  __syncthreads();
+}
+
+struct ColorCells {
+  int mx, my, mz, px, py, pz;
+  __device__ int count() const { return mx * my * mz; }
+  // tile-local cell coordinates of the ci-th cell of this colour
+  __device__ void cell(int ci, int& cx, int& cy, int& cz) const {
+    cx = px + 2 * (ci % mx);
+    cy = py + 2 * ((ci / mx) % my);
+    cz = pz + 2 * (ci / (mx * my));
+  }
+};
+
+// ------------------------------------------------------------------------------------
+// Cell operators.  U: p_k (Dirichlet-masked) on the node brick (bx x by x bz),
+// V: accumulated result on the same brick, S: per-cell scratch.
+// ------------------------------------------------------------------------------------
+
+// Affine box cells: the cell matrix of Eq. 5 is the Kronecker sum
+// K_x (x) M (x) M + M (x) K_y (x) M + M (x) M (x) K_z (K_d scaled by the cell
+// sizes), applied in seven 1D sweeps with shared intermediates.
+template <int P>
+__device__ void cell_op_affine(const OperatorCoeffs& c, const double* U, double* V, double* S, int bx, int by,
+                               const ColorCells& cc) {
+  constexpr int N1 = P + 1, N2 = N1 * N1, N3 = N2 * N1;
+  const int nc = cc.count();
+  // z direction: s1 = M_z u, s2 = K_z u
+  for (int t = threadIdx.x; t < nc * N2; t += kThreads) {
+    const int ci = t / N2, e = t - ci * N2, a = e % N1, b = e / N1;
+    int cx, cy, cz;
+    cc.cell(ci, cx, cy, cz);
+    const double* u0 = U + (P * cx + a) + bx * ((P * cy + b) + by * (P * cz));
+    double x[N1], y1[N1], y2[N1];
+#pragma unroll
+    for (int s = 0; s < N1; ++s) x[s] = u0[s * bx * by];
+    matvec<N1>(c.M, x, y1);
+    matvec<N1>(c.K[2], x, y2);
+    double* s1 = S + ci * 2 * N3;
+    double* s2 = s1 + N3;
+#pragma unroll
+    for (int s = 0; s < N1; ++s) {
+      s1[cidx<N1>(a, b, s)] = y1[s];
+      s2[cidx<N1>(a, b, s)] = y2[s];
+    }
+  }
+  __syncthreads();
+  // y direction: s1 <- M_y s1, s2 <- K_y s1 + M_y s2
+  for (int t = threadIdx.x; t < nc * N2; t += kThreads) {
+    const int ci = t / N2, e = t - ci * N2, a = e % N1, cz = e / N1;
+    double* s1 = S + ci * 2 * N3;
+    double* s2 = s1 + N3;
+    double m[N1], k[N1], y1[N1], y2[N1], y3[N1];
+#pragma unroll
+    for (int s = 0; s < N1; ++s) {
+      m[s] = s1[cidx<N1>(a, s, cz)];
+      k[s] = s2[cidx<N1>(a, s, cz)];
+    }
+    matvec<N1>(c.M, m, y1);
+    matvec<N1>(c.K[1], m, y2);
+    matvec<N1>(c.M, k, y3);
+#pragma unroll
+    for (int s = 0; s < N1; ++s) {
+      s1[cidx<N1>(a, s, cz)] = y1[s];
+      s2[cidx<N1>(a, s, cz)] = y2[s] + y3[s];
+    }
+  }
+  __syncthreads();
+  // x direction: out = K_x s1 + M_x s2, added into V
+  for (int t = threadIdx.x; t < nc * N2; t += kThreads) {
+    const int ci = t / N2, e = t - ci * N2, b = e % N1, cz = e / N1;
+    int cx, cy, czz;
+    cc.cell(ci, cx, cy, czz);
+    const double* s1 = S + ci * 2 * N3;
+    const double* s2 = s1 + N3;
+    double m[N1], k[N1];
+#pragma unroll
+    for (int s = 0; s < N1; ++s) {
+      m[s] = s1[cidx<N1>(s, b, cz)];
+      k[s] = s2[cidx<N1>(s, b, cz)];
+    }
+    double* v0 = V + (P * cx) + bx * ((P * cy + b) + by * (P * czz + cz));
+#pragma unroll
+    for (int i = 0; i < N1; ++i) {
+      double s = 0.0;
+#pragma unroll
+      for (int j = 0; j < N1; ++j) s = fma(c.K[0][i * N1 + j], m[j], s);
+#pragma unroll
+      for (int j = 0; j < N1; ++j) s = fma(c.M[i * N1 + j], k[j], s);
+      v0[i] += s;
+    }
+  }
+  __syncthreads();
+}
+
+// Deformed cells ("inverse Jacobian load" variant of Sec. 2.2): values at the
+// Gauss points by three sweeps with the interpolation matrix S, reference
+// gradients by three sweeps with the Gauss collocation derivative Dc, the
+// per-point metric J^{-1} (JxW a) J^{-T}, and the transposed sweeps back.
+template <int P>
+__device__ void cell_op_deformed(const OperatorCoeffs& c, const double* U, double* V, double* S, int bx, int by,
+                                 const ColorCells& cc, const double* __restrict__ geo, int64_t cell_base_x,
+                                 int64_t cell_base_y, int64_t cell_base_z, const TileGeom& g) {
+  constexpr int N1 = P + 1, N2 = N1 * N1, N3 = N2 * N1;
+  const int nc = cc.count();
+  const int stride = 4 * N3;
+  // gather u into s0
+  for (int t = threadIdx.x; t < nc * N3; t += kThreads) {
+    const int ci = t / N3, e = t - ci * N3, a = e % N1, b = (e / N1) % N1, cz = e / N2;
+    int cx, cy, czz;
+    cc.cell(ci, cx, cy, czz);
+    S[ci * stride + e] = U[(P * cx + a) + bx * ((P * cy + b) + by * (P * czz + cz))];
+  }
+  __syncthreads();
+  sweep_inplace<P, false>(S, stride, nc, 0, c.S);
+  sweep_inplace<P, false>(S, stride, nc, 1, c.S);
+  sweep_inplace<P, false>(S, stride, nc, 2, c.S);
+  // reference gradients at the Gauss points (single pass over all three directions)
+  for (int t = threadIdx.x; t < nc * N2 * 3; t += kThreads) {
+    const int dir = t / (nc * N2);
+    const int tt = t - dir * nc * N2;
+    const int ci = tt / N2, e = tt - ci * N2, e1 = e % N1, e2 = e / N1;
+    const double* a = S + ci * stride;
+    double* o = S + ci * stride + (1 + dir) * N3;
+    double x[N1], y[N1];
+#pragma unroll
+    for (int s = 0; s < N1; ++s) x[s] = a[pencil_idx<N1>(dir, e1, e2, s)];
+    matvec<N1>(c.Dc, x, y);
+#pragma unroll
+    for (int s = 0; s < N1; ++s) o[pencil_idx<N1>(dir, e1, e2, s)] = y[s];
+  }
+  __syncthreads();
+  // metric at each point: flux = J^{-1} (JxW a) J^{-T} grad_ref
+  for (int t = threadIdx.x; t < nc * N3; t += kThreads) {
+    const int ci = t / N3, q = t - ci * N3;
+    int cx, cy, cz;
+    cc.cell(ci, cx, cy, cz);
+    const int64_t cell = (cell_base_x + cx) + (int64_t)g.N[0] * ((cell_base_y + cy) + (int64_t)g.N[1] * (cell_base_z + cz));
+    const double* gq = geo + cell * 10 * N3 + q;
+    double Ji[9];
+#pragma unroll
+    for (int m = 0; m < 9; ++m) Ji[m] = __ldg(gq + m * N3);
+    const double jxw = __ldg(gq + 9 * N3);
+    double* s = S + ci * stride;
+    const double g0 = s[N3 + q], g1 = s[2 * N3 + q], g2 = s[3 * N3 + q];
+    // physical gradient (J^{-T} g)_m = sum_n Ji[n][m] g_n, scaled by JxW a
+    const double f0 = jxw * fma(Ji[0], g0, fma(Ji[3], g1, Ji[6] * g2));
+    const double f1 = jxw * fma(Ji[1], g0, fma(Ji[4], g1, Ji[7] * g2));
+    const double f2 = jxw * fma(Ji[2], g0, fma(Ji[5], g1, Ji[8] * g2));
+    s[N3 + q] = fma(Ji[0], f0, fma(Ji[1], f1, Ji[2] * f2));
+    s[2 * N3 + q] = fma(Ji[3], f0, fma(Ji[4], f1, Ji[5] * f2));
+    s[3 * N3 + q] = fma(Ji[6], f0, fma(Ji[7], f1, Ji[8] * f2));
+  }
+  __syncthreads();
+  // transposed derivative sweeps, summed into s0
+  sweep_copy<P, true, false>(S + N3, S, stride, nc, 0, c.Dc);
+  sweep_copy<P, true, true>(S + 2 * N3, S, stride, nc, 1, c.Dc);
+  sweep_copy<P, true, true>(S + 3 * N3, S, stride, nc, 2, c.Dc);
+  sweep_inplace<P, true>(S, stride, nc, 0, c.S);
+  sweep_inplace<P, true>(S, stride, nc, 1, c.S);
+  // last sweep writes straight into the node brick
+  for (int t = threadIdx.x; t < nc * N2; t += kThreads) {
+    const int ci = t / N2, e = t - ci * N2, a = e % N1, b = e / N1;
+    int cx, cy, cz;
+    cc.cell(ci, cx, cy, cz);
+    const double* s0 = S + ci * stride;
+    double x[N1], y[N1];
+#pragma unroll
+    for (int s = 0; s < N1; ++s) x[s] = s0[cidx<N1>(a, b, s)];
+    matvec_t<N1>(c.S, x, y);
+    double* v0 = V + (P * cx + a) + bx * ((P * cy + b) + by * (P * cz));
+#pragma unroll
+    for (int s = 0; s < N1; ++s) v0[s * bx * by] += y[s];
+  }
+  __syncthreads();
+}
+
+// Right-hand side b_e = sum_q w_q det J_q f(x_q) phi(xhat_q): forcing at the
+// Gauss points, then three transposed interpolation sweeps.
+__device__ inline double manufactured_forcing(double x, double y, double z, int coef) {
+  const double pi = 3.14159265358979323846;
+  const double u = sin(pi * x) * sin(pi * y) * sin(pi * z);
+  if (coef == MFCG_COEF_CONSTANT) return 3.0 * pi * pi * u;
+  const double a = 1.0 + 0.5 * sin(pi * x);
+  const double cx = cos(pi * x);
+  return a * 3.0 * pi * pi * u - 0.5 * pi * pi * cx * cx * sin(pi * y) * sin(pi * z);
+}
+
+template <int P>
+__device__ void cell_rhs(const OperatorCoeffs& c, double* V, double* S, int bx, int by, const ColorCells& cc,
+                         int cx0, int cy0, int cz0, int stride) {
+  constexpr int N1 = P + 1, N2 = N1 * N1, N3 = N2 * N1;
+  const int nc = cc.count();
+  const double twopi = 6.28318530717958647692;
+  for (int t = threadIdx.x; t < nc * N3; t += kThreads) {
+    const int ci = t / N3, q = t - ci * N3, qa = q % N1, qb = (q / N1) % N1, qc = q / N2;
+    int cx, cy, cz;
+    cc.cell(ci, cx, cy, cz);
+    const double X = c.h[0] * (cx0 + cx + c.g[qa]);
+    const double Y = c.h[1] * (cy0 + cy + c.g[qb]);
+    const double Z = c.h[2] * (cz0 + cz + c.g[qc]);
+    const double sx = sin(twopi * X), sy = sin(twopi * Y), sz = sin(twopi * Z);
+    const double A = c.amplitude;
+    const double s = sx * sy * sz;
+    const double dsum = twopi * (cos(twopi * X) * sy * sz + sx * cos(twopi * Y) * sz + sx * sy * cos(twopi * Z));
+    const double detJ = c.h[0] * c.h[1] * c.h[2] * (1.0 + A * dsum);
+    const double f = manufactured_forcing(X + A * s, Y + A * s, Z + A * s, c.coef);
+    S[ci * stride + q] = c.w[qa] * c.w[qb] * c.w[qc] * detJ * f;
+  }
+  __syncthreads();
+  sweep_inplace<P, true>(S, stride, nc, 0, c.S);
+  sweep_inplace<P, true>(S, stride, nc, 1, c.S);
+  sweep_inplace<P, true>(S, stride, nc, 2, c.S);
+  for (int t = threadIdx.x; t < nc * N3; t += kThreads) {
+    const int ci = t / N3, e = t - ci * N3, a = e % N1, b = (e / N1) % N1, cz = e / N2;
+    int cx, cy, czz;
+    cc.cell(ci, cx, cy, czz);
+    V[(P * cx + a) + bx * ((P * cy + b) + by * (P * czz + cz))] += S[ci * stride + e];
+  }
+  __syncthreads();
+}
+
+// Exact diagonal of the cell matrix of Eq. 5 with the same Gauss rule:
+// diag_e(i) = sum_q sum_{d,d'} G_d(q,i) C_q^{dd'} G_{d'}(q,i), C_q = JxW a J^{-1} J^{-T},
+// where G_d(q,i) is a product of 1D tables; each (d,d') term is a 3D
+// contraction of C^{dd'} with the element-wise products SS, DS or DD of the 1D
+// tables along each direction, i.e. three transposed sweeps.
+template <int P, int GEOM>
+__device__ void cell_diag(const OperatorCoeffs& c, double* V, double* S, int bx, int by, const ColorCells& cc,
+                          const double* __restrict__ geo, int cx0, int cy0, int cz0, const TileGeom& g, int stride) {
+  constexpr int N1 = P + 1, N2 = N1 * N1, N3 = N2 * N1;
+  const int nc = cc.count();
+  for (int t = threadIdx.x; t < nc * N3; t += kThreads) {
+    const int ci = t / N3, e = t - ci * N3;
+    S[ci * stride + N3 + e] = 0.0;
+  }
+  const int combos[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+  const int ncombo = GEOM == GEOM_AFFINE ? 3 : 6;
+  for (int cb = 0; cb < ncombo; ++cb) {
+    const int d0 = combos[cb][0], d1 = combos[cb][1];
+    const double factor = d0 == d1 ? 1.0 : 2.0;
+    for (int t = threadIdx.x; t < nc * N3; t += kThreads) {
+      const int ci = t / N3, q = t - ci * N3;
+      double C;
+      if (GEOM == GEOM_AFFINE) {
+        const int qa = q % N1, qb = (q / N1) % N1, qc = q / N2;
+        C = c.w[qa] * c.w[qb] * c.w[qc] * c.h[0] * c.h[1] * c.h[2] / (c.h[d0] * c.h[d0]);
+      } else {
+        int cx, cy, cz;
+        cc.cell(ci, cx, cy, cz);
+        const int64_t cell = (cx0 + cx) + (int64_t)g.N[0] * ((cy0 + cy) + (int64_t)g.N[1] * (cz0 + cz));
+        const double* gq = geo + cell * 10 * N3 + q;
+        double s = 0.0;
+#pragma unroll
+        for (int m = 0; m < 3; ++m) s = fma(__ldg(gq + (3 * d0 + m) * N3), __ldg(gq + (3 * d1 + m) * N3), s);
+        C = __ldg(gq + 9 * N3) * s;
+      }
+      S[ci * stride + q] = factor * C;
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int dim = 0; dim < 3; ++dim) {
+      const int nd = (dim == d0) + (dim == d1);
+      sweep_inplace<P, true>(S, stride, nc, dim, c.T2[nd]);
+    }
+    for (int t = threadIdx.x; t < nc * N3; t += kThreads) {
+      const int ci = t / N3, e = t - ci * N3;
+      S[ci * stride + N3 + e] += S[ci * stride + e];
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < nc * N3; t += kThreads) {
+    const int ci = t / N3, e = t - ci * N3, a = e % N1, b = (e / N1) % N1, cz = e / N2;
+    int cx, cy, czz;
+    cc.cell(ci, cx, cy, czz);
+    V[(P * cx + a) + bx * ((P * cy + b) + by * (P * czz + cz))] += S[ci * stride + N3 + e];
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------------------------------
+// Block reduction of NV doubles in a fixed order (warp shuffles, then warps in order)
+// ------------------------------------------------------------------------------------
+template <int NV>
+__device__ __forceinline__ void block_reduce(double (&v)[NV], double* red) {
+#pragma unroll
+  for (int m = 0; m < NV; ++m) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[m] += __shfl_down_sync(0xffffffffu, v[m], o);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+#pragma unroll
+    for (int m = 0; m < NV; ++m) red[warp * NV + m] = v[m];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int m = 0; m < NV; ++m) {
+      double s = 0.0;
+      for (int w = 0; w < kThreads / 32; ++w) s += red[w * NV + m];
+      v[m] = s;
+    }
+  }
+  __syncthreads();
+}
+
+// accumulate the seven sums of Algorithm 5 for one finalised node
+__device__ __forceinline__ void post_sums(double (&sm)[7], double r, double p, double v, double dinv) {
+  const double z = dinv * r;      // M^{-1} r
+  const double zv = dinv * v;     // M^{-1} v
+  sm[0] = fma(r, r, sm[0]);       // gamma = r.r
+  sm[1] = fma(p, v, sm[1]);       // a = p.v
+  sm[2] = fma(r, v, sm[2]);       // b = r.v
+  sm[3] = fma(v, v, sm[3]);       // c = v.v
+  sm[4] = fma(r, z, sm[4]);       // d = r.M^-1 r
+  sm[5] = fma(r, zv, sm[5]);      // e = r.M^-1 v
+  sm[6] = fma(v, zv, sm[6]);      // f = v.M^-1 v
+}
+
+// ------------------------------------------------------------------------------------
+// The tile kernel
+// ------------------------------------------------------------------------------------
+template <int P, int MODE, int GEOM>
+__global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a, const OperatorCoeffs c) {
+  extern __shared__ double smem[];
+  __shared__ double red[8 * (kThreads / 32)];
+  constexpr int N1 = P + 1, N3 = N1 * N1 * N1;
+  const TileGeom& g = a.g;
+
+  double alpha_prev = 0.0, beta_prev = 0.0, xa = 0.0, xr = 0.0;
+  bool xupd = false;
+  if (MODE == MODE_CG) {
+    const CGState* st = a.state;
+    if (st->done) return;
+    alpha_prev = st->alpha_prev;
+    beta_prev = st->beta_prev;
+    const int k = st->k;
+    xupd = (k > 1) && (k & 1);
+    xa = alpha_prev;
+    xr = xupd ? st->alpha_prev2 / st->beta_prev2 : 0.0;
+  }
+
+  const int64_t tile = blockIdx.x;
+  const int tx = (int)(tile % g.nt[0]);
+  const int ty = (int)((tile / g.nt[0]) % g.nt[1]);
+  const int tz = (int)(tile / ((int64_t)g.nt[0] * g.nt[1]));
+  const int cx0 = tx * g.T[0], cy0 = ty * g.T[1], cz0 = tz * g.T[2];
+  const int ncx = min(g.T[0], g.N[0] - cx0), ncy = min(g.T[1], g.N[1] - cy0), ncz = min(g.T[2], g.N[2] - cz0);
+  const int bx = P * ncx + 1, by = P * ncy + 1, bz = P * ncz + 1;
+  const int bsize = bx * by * bz;
+  const int Bmax = (P * g.T[0] + 1) * (P * g.T[1] + 1) * (P * g.T[2] + 1);
+  const int gi0 = P * cx0, gj0 = P * cy0, gk0 = P * cz0;
+  const int pTx = P * g.T[0], pTy = P * g.T[1], pTz = P * g.T[2];
+  const bool lastx = tx == g.nt[0] - 1, lasty = ty == g.nt[1] - 1, lastz = tz == g.nt[2] - 1;
+
+  double* U = smem;
+  double* V = smem + Bmax;
+  double* S = smem + 2 * Bmax;
+
+  // ---------------- phase 1: pre ----------------
+  for (int n = threadIdx.x; n < bsize; n += kThreads) {
+    const int li = n % bx, lj = (n / bx) % by, lk = n / (bx * by);
+    const int i = gi0 + li, j = gj0 + lj, k = gk0 + lk;
+    if (MODE == MODE_OPERATOR) {
+      const bool dir = is_dirichlet(g, i, j, k);
+      U[n] = dir ? 0.0 : a.in0[node_index(g, i, j, k)];
+    } else if (MODE == MODE_CG) {
+      const bool dir = is_dirichlet(g, i, j, k);
+      const int64_t gi = node_index(g, i, j, k);
+      const double r_o = a.in0[gi], v_o = a.in1[gi], p_o = a.in2[gi], dinv = a.diag_inv[gi];
+      const double rk = fma(-alpha_prev, v_o, r_o);
+      const double pk = fma(beta_prev, p_o, dinv * rk);
+      U[n] = dir ? 0.0 : pk;
+      const bool owned = (li < pTx || lastx) && (lj < pTy || lasty) && (lk < pTz || lastz);
+      if (owned) {
+        a.out0[gi] = rk;
+        a.out2[gi] = pk;
+        if (xupd) a.x[gi] += fma(xa, p_o, xr * (p_o - dinv * r_o));
+      }
+    }
+    V[n] = 0.0;
+  }
+  __syncthreads();
+
+  // ---------------- phase 2: cell integrals, one colour at a time ----------------
+  for (int color = 0; color < 8; ++color) {
+    ColorCells cc;
+    cc.px = color & 1;
+    cc.py = (color >> 1) & 1;
+    cc.pz = color >> 2;
+    cc.mx = (ncx - cc.px + 1) / 2;
+    cc.my = (ncy - cc.py + 1) / 2;
+    cc.mz = (ncz - cc.pz + 1) / 2;
+    if (cc.count() == 0) continue;
+    if (MODE == MODE_RHS) {
+      cell_rhs<P>(c, V, S, bx, by, cc, cx0, cy0, cz0, (GEOM == GEOM_AFFINE ? 2 : 4) * N3);
+    } else if (MODE == MODE_DIAG) {
+      cell_diag<P, GEOM>(c, V, S, bx, by, cc, a.geo, cx0, cy0, cz0, g, (GEOM == GEOM_AFFINE ? 2 : 4) * N3);
+    } else if (GEOM == GEOM_AFFINE) {
+      cell_op_affine<P>(c, U, V, S, bx, by, cc);
+    } else {
+      cell_op_deformed<P>(c, U, V, S, bx, by, cc, a.geo, cx0, cy0, cz0, g);
+    }
+  }
+
+  // ---------------- phase 3: post ----------------
+  double sm[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int n = threadIdx.x; n < bsize; n += kThreads) {
+    const int li = n % bx, lj = (n / bx) % by, lk = n / (bx * by);
+    const int i = gi0 + li, j = gj0 + lj, k = gk0 + lk;
+    const bool dir = is_dirichlet(g, i, j, k);
+    const bool shared = !dir && ((li == 0 && tx > 0) || (li == bx - 1 && !lastx) || (lj == 0 && ty > 0) ||
+                                 (lj == by - 1 && !lasty) || (lk == 0 && tz > 0) || (lk == bz - 1 && !lastz));
+    if (shared) {
+      a.shell[tile * g.face_stride + shell_slot(g, li, lj, lk, bx, by, bz)] = V[n];
+      continue;
+    }
+    const bool owned = (li < pTx || lastx) && (lj < pTy || lasty) && (lk < pTz || lastz);
+    if (!owned) continue;
+    const int64_t gi = node_index(g, i, j, k);
+    if (MODE == MODE_OPERATOR) {
+      a.out0[gi] = dir ? a.in0[gi] : V[n];
+    } else if (MODE == MODE_RHS) {
+      a.out0[gi] = dir ? 0.0 : V[n];
+    } else if (MODE == MODE_DIAG) {
+      a.out0[gi] = dir ? 1.0 : V[n];
+    } else {
+      const double pk = dir ? a.out2[gi] : U[n];
+      const double v = dir ? pk : V[n];
+      const double rk = a.out0[gi];
+      a.out1[gi] = v;
+      post_sums(sm, rk, pk, v, a.diag_inv[gi]);
+    }
+  }
+  if (MODE == MODE_CG) {
+    block_reduce<7>(sm, red);
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int m = 0; m < 7; ++m) a.partial[tile * 8 + m] = sm[m];
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Tail: shared-face nodes and the scalar step of Algorithm 5
+// ------------------------------------------------------------------------------------
+
+template <int MODE>
+__device__ void cg_scalar_step(CGState* st, const double (&s)[7]) {
+  const double gam = s[0], av = s[1], bv = s[2], cv = s[3], dv = s[4], ev = s[5], fv = s[6];
+  const int k = st->k;
+  for (int m = 0; m < 7; ++m) st->sums[m] = s[m];
+  st->iterations = k;
+  bool finite = true;
+  for (int m = 0; m < 7; ++m) finite = finite && isfinite(s[m]);
+  if (!finite || !(av > 0.0) || !(dv > 0.0)) {
+    st->done = 3;
+    return;
+  }
+  const double alpha = dv / av;                                   // alpha_k = d_k / a_k
+  double gn = fma(alpha * alpha, cv, fma(-2.0 * alpha, bv, gam)); // Eq. 8: ||r_{k+1}||^2
+  if (gn < 0.0) gn = 0.0;
+  st->alpha_cur = alpha;
+  st->gamma_next = gn;
+  if (!st->fixed && gn < st->eps_sq) {
+    st->done = 1;
+    return;
+  }
+  if (k >= st->maxit) {
+    st->done = 2;
+    return;
+  }
+  const double beta = fma(alpha * alpha, fv, fma(-2.0 * alpha, ev, dv)) / dv;  // Eq. 7
+  if ((k + 1) % 2 == 1 && !(st->beta_prev != 0.0)) {
+    // the delayed update of the next (odd) iteration divides by beta_{k-1}
+    st->done = 3;
+    return;
+  }
+  st->alpha_prev2 = st->alpha_prev;
+  st->beta_prev2 = st->beta_prev;
+  st->alpha_prev = alpha;
+  st->beta_prev = beta;
+  st->k = k + 1;
+}
+
+template <int P, int MODE>
+__global__ void __launch_bounds__(kThreads) tail_kernel(const TileArgs a) {
+  __shared__ double red[8 * (kThreads / 32)];
+  __shared__ int is_last;
+  const TileGeom& g = a.g;
+  if (MODE == MODE_CG && a.state->done) return;
+  double sm[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x; t < a.tail_nodes; t += (int64_t)gridDim.x * kThreads) {
+    int i, j, k;
+    decode_tail_node(g, a.fam, t, i, j, k);
+    int txs[2], lis[2], tys[2], ljs[2], tzs[2], lks[2];
+    const int nx = contributors(g, 0, i, txs, lis);
+    const int ny = contributors(g, 1, j, tys, ljs);
+    const int nz = contributors(g, 2, k, tzs, lks);
+    double v = 0.0;
+    for (int cz = 0; cz < nz; ++cz)
+      for (int cy = 0; cy < ny; ++cy)
+        for (int cx = 0; cx < nx; ++cx) {
+          const int64_t tl = txs[cx] + (int64_t)g.nt[0] * (tys[cy] + (int64_t)g.nt[1] * tzs[cz]);
+          const int bx = brick_extent(g, 0, txs[cx]), by = brick_extent(g, 1, tys[cy]),
+                    bz = brick_extent(g, 2, tzs[cz]);
+          v += a.shell[tl * g.face_stride + shell_slot(g, lis[cx], ljs[cy], lks[cz], bx, by, bz)];
+        }
+    const int64_t gi = node_index(g, i, j, k);
+    if (MODE == MODE_CG) {
+      const double rk = a.out0[gi], pk = a.out2[gi];
+      a.out1[gi] = v;
+      post_sums(sm, rk, pk, v, a.diag_inv[gi]);
+    } else {
+      a.out0[gi] = v;
+    }
+  }
+  if (MODE != MODE_CG) return;
+  block_reduce<7>(sm, red);
+  double* tail_partial = a.partial + a.g.n_tiles * 8;
+  if (threadIdx.x == 0) {
+    for (int m = 0; m < 7; ++m) tail_partial[blockIdx.x * 8 + m] = sm[m];
+    __threadfence();
+    const unsigned prev = atomicAdd(&a.state->ticket, 1u);
+    is_last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  // last CTA: fixed-order reduction of all per-CTA sums
+  const int64_t nparts = a.g.n_tiles + gridDim.x;
+  double s[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int64_t t = threadIdx.x; t < nparts; t += kThreads) {
+#pragma unroll
+    for (int m = 0; m < 7; ++m) s[m] += __ldcg(a.partial + t * 8 + m);
+  }
+  block_reduce<7>(s, red);
+  if (threadIdx.x == 0) {
+    cg_scalar_step<MODE>(a.state, s);
+    a.state->ticket = 0u;
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// launch helpers
+// ------------------------------------------------------------------------------------
+inline size_t tile_smem_doubles(int P, int geom, const TileGeom& g) {
+  const size_t Bmax = (size_t)(P * g.T[0] + 1) * (P * g.T[1] + 1) * (P * g.T[2] + 1);
+  const size_t cpc = (size_t)((g.T[0] + 1) / 2) * ((g.T[1] + 1) / 2) * ((g.T[2] + 1) / 2);
+  const size_t n3 = (size_t)(P + 1) * (P + 1) * (P + 1);
+  return 2 * Bmax + cpc * (geom == GEOM_AFFINE ? 2 : 4) * n3;
+}
+
+template <int P>
+using TileFn = void (*)(const TileArgs, const OperatorCoeffs);
+
+template <int P, int GEOM>
+TileFn<P> tile_fn_g(int mode) {
+  switch (mode) {
+    case MODE_CG: return tile_kernel<P, MODE_CG, GEOM>;
+    case MODE_OPERATOR: return tile_kernel<P, MODE_OPERATOR, GEOM>;
+    case MODE_RHS: return tile_kernel<P, MODE_RHS, GEOM>;
+    default: return tile_kernel<P, MODE_DIAG, GEOM>;
+  }
+}
+
+template <int P>
+TileFn<P> tile_fn(int mode, int geom) {
+  return geom == GEOM_AFFINE ? tile_fn_g<P, GEOM_AFFINE>(mode) : tile_fn_g<P, GEOM_DEFORMED>(mode);
+}
+
+// once per problem (outside any stream capture): allow the dynamic shared memory
+template <int P>
+cudaError_t prepare_tile_p(int geom, size_t smem) {
+  for (int mode = 0; mode < 4; ++mode) {
+    cudaError_t e = cudaFuncSetAttribute(tile_fn<P>(mode, geom), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+template <int P>
+cudaError_t launch_tile_p(int mode, const TileArgs& a, const OperatorCoeffs& c, cudaStream_t s) {
+  const size_t smem = tile_smem_doubles(P, a.geom, a.g) * sizeof(double);
+  tile_fn<P>(mode, a.geom)<<<(unsigned)a.g.n_tiles, kThreads, smem, s>>>(a, c);
+  return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t launch_tail_p(int mode, const TileArgs& a, cudaStream_t s) {
+  const unsigned grid = (unsigned)(a.tail_ctas > 0 ? a.tail_ctas : 1);
+  if (mode == MODE_CG)
+    tail_kernel<P, MODE_CG><<<grid, kThreads, 0, s>>>(a);
+  else
+    tail_kernel<P, MODE_OPERATOR><<<grid, kThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace mfcg

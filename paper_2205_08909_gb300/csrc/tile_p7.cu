@@ -1,0 +1,11 @@
+// Instantiation of the tile kernels for degree 7 (one translation unit per
+// degree keeps the parallel build short).
+#include "tile_kernels.cuh"
+
+namespace mfcg {
+cudaError_t launch_tile_deg7(int mode, const TileArgs& a, const OperatorCoeffs& c, cudaStream_t s) {
+  return launch_tile_p<7>(mode, a, c, s);
+}
+cudaError_t launch_tail_deg7(int mode, const TileArgs& a, cudaStream_t s) { return launch_tail_p<7>(mode, a, s); }
+cudaError_t prepare_tile_deg7(int geom, size_t smem) { return prepare_tile_p<7>(geom, smem); }
+}  // namespace mfcg

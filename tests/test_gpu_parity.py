@@ -1,0 +1,248 @@
+"""GPU parity of the CUDA path against the CPU oracle, through the C ABI.
+
+Tolerances (stated by the workload definition): operator application in FP64
+max_i |d_i| / max_i |ref_i| <= 1e-13; converged solution at rtol 1e-10 within
+1e-9 (max norm, relative) of the oracle's Algorithm 1 and iteration counts
+within +-1.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import cg as ocg
+from oracle import fastdiag, fem
+from paper_2205_08909_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+OP_TOL = 1e-13
+SOL_TOL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def mfcg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2205_08909_gb300 import build
+
+    build.build()
+    import paper_2205_08909_gb300 as m
+
+    return m
+
+
+def _oracle_problem(p, cells, amp=0.0, coef="constant"):
+    return fem.Problem(p, tuple(cells), amp, fem.COEF_SIN_X if coef == "sin_x" else fem.COEF_CONSTANT)
+
+
+def _gpu_problem(mfcg, p, cells, amp=0.0, coef="constant", **kw):
+    geometry = "deformed" if (amp != 0.0 or coef != "constant") else "affine"
+    return mfcg.Problem(p, cells, amplitude=amp, geometry=geometry, coefficient=coef, **kw)
+
+
+def _to_dev(prob, lex):
+    return prob.from_lexicographic(torch.from_numpy(np.ascontiguousarray(lex)).cuda())
+
+
+def _to_host(prob, v):
+    return prob.to_lexicographic(v).cpu().numpy()
+
+
+def _rel(a, ref):
+    return np.abs(a - ref).max() / max(np.abs(ref).max(), 1e-300)
+
+
+OPERATOR_CASES = [
+    (2, (8, 8, 8), 0.0, "constant", None),
+    (4, (9, 5, 6), 0.0, "constant", None),
+    (1, (7, 6, 5), 0.0, "constant", (2, 3, 2)),
+    (3, (5, 4, 7), 0.0, "constant", (2, 2, 3)),
+    (5, (3, 4, 3), 0.0, "constant", None),
+    (6, (4, 3, 3), 0.0, "constant", None),
+    (7, (2, 3, 2), 0.0, "constant", (1, 2, 1)),
+    (8, (2, 2, 3), 0.0, "constant", (1, 1, 2)),
+    (2, (1, 1, 1), 0.0, "constant", None),
+    (3, (1, 2, 1), 0.0, "constant", None),
+    (2, (5, 4, 6), 0.05, "sin_x", None),
+    (4, (3, 4, 3), 0.08, "constant", None),
+    (6, (3, 3, 2), 0.05, "sin_x", None),
+    (3, (4, 3, 5), 0.0, "sin_x", (2, 2, 2)),
+]
+
+
+@pytest.mark.parametrize("p,cells,amp,coef,tile", OPERATOR_CASES)
+def test_operator_diagonal_rhs_match_oracle(mfcg, p, cells, amp, coef, tile):
+    op = _oracle_problem(p, cells, amp, coef)
+    A = fem.assemble(op)
+    prob = _gpu_problem(mfcg, p, cells, amp, coef, tile=tile)
+    assert prob.n_dofs == op.n_dofs
+    u = inputs.random_vector(op.n_dofs, salt=p)
+    got = _to_host(prob, prob.apply_operator(_to_dev(prob, u)))
+    assert _rel(got, A @ u) <= OP_TOL
+    assert _rel(_to_host(prob, prob.diagonal()), A.diagonal()) <= OP_TOL
+    assert _rel(_to_host(prob, prob.rhs()), fem.rhs(op)) <= 1e-12
+    prob.close()
+
+
+def test_reordering_is_a_permutation(mfcg):
+    prob = mfcg.Problem(3, (5, 4, 3), tile=(2, 3, 2))
+    lex = torch.arange(prob.n_dofs, dtype=torch.float64, device="cuda")
+    blk = prob.from_lexicographic(lex)
+    assert torch.equal(torch.sort(blk).values, lex)
+    assert torch.equal(prob.to_lexicographic(blk), lex)
+    prob.close()
+
+
+CG_CASES = [
+    (2, (8, 8, 8), 0.0, "constant"),
+    (4, (5, 6, 4), 0.0, "constant"),
+    (3, (3, 4, 3), 0.05, "sin_x"),
+    (6, (2, 3, 2), 0.05, "sin_x"),
+]
+
+
+@pytest.mark.parametrize("mode", ["fused", "unfused"])
+@pytest.mark.parametrize("p,cells,amp,coef", CG_CASES)
+def test_cg_solution_matches_oracle(mfcg, mode, p, cells, amp, coef):
+    op = _oracle_problem(p, cells, amp, coef)
+    A = fem.assemble(op)
+    b = fem.rhs(op)
+    ref = ocg.pcg_algorithm1(lambda v: A @ v, b, 1.0 / A.diagonal(), 1e-10, 5000)
+    prob = _gpu_problem(mfcg, p, cells, amp, coef, mode=mode)
+    x, info = prob.cg_solve(_to_dev(prob, b), rtol=1e-10, maxit=5000)
+    assert info["converged"] == 1
+    assert abs(info["iterations"] - ref.iterations) <= 1
+    assert _rel(_to_host(prob, x), ref.x) <= SOL_TOL
+    prob.close()
+
+
+@pytest.mark.parametrize("mode", ["fused", "unfused"])
+@pytest.mark.parametrize("maxit", [1, 2, 3, 6, 7])
+def test_fixed_iterations_match_algorithm1_iterates(mfcg, mode, maxit):
+    # rtol = 0 runs exactly maxit iterations: checks the delayed x update and
+    # the parity-dependent finalisation of Algorithm 5 for odd and even counts
+    p, cells = 3, (4, 3, 5)
+    op = _oracle_problem(p, cells)
+    A = fem.assemble(op)
+    b = inputs.boundary_zeroed(inputs.random_vector(op.n_dofs, salt=7), op.nodes_per_dim)
+    ref = ocg.pcg_algorithm1(lambda v: A @ v, b, 1.0 / A.diagonal(), 0.0, maxit)
+    prob = _gpu_problem(mfcg, p, cells, mode=mode)
+    x, info = prob.cg_solve(_to_dev(prob, b), rtol=0.0, maxit=maxit)
+    assert info["iterations"] == maxit
+    assert _rel(_to_host(prob, x), ref.x) <= 1e-11
+    prob.close()
+
+
+def test_initial_guess_and_host_arrays(mfcg):
+    p, cells = 4, (3, 4, 3)
+    op = _oracle_problem(p, cells)
+    A = fem.assemble(op)
+    b = fem.rhs(op)
+    ref = ocg.pcg_algorithm1(lambda v: A @ v, b, 1.0 / A.diagonal(), 1e-10, 5000)
+    prob = mfcg.Problem(p, cells)
+    x0 = inputs.boundary_zeroed(inputs.random_vector(op.n_dofs, salt=3), op.nodes_per_dim)
+    x, info = prob.cg_solve(_to_dev(prob, b), _to_dev(prob, x0), rtol=1e-12, maxit=5000)
+    assert info["converged"]
+    assert _rel(_to_host(prob, x), ref.x) <= SOL_TOL
+    # the same solve through host arrays gives bitwise the same result
+    bd = _to_dev(prob, b)
+    xd, _ = prob.cg_solve(bd, rtol=1e-10)
+    bh = bd.cpu().pin_memory()
+    xh = torch.zeros(prob.n_dofs, dtype=torch.float64).pin_memory()
+    xh, info_h = prob.cg_solve_host(bh, xh, rtol=1e-10)
+    assert torch.equal(xh, xd.cpu())
+    prob.close()
+
+
+@pytest.mark.parametrize("mode", ["fused", "unfused"])
+def test_solve_is_deterministic(mfcg, mode):
+    prob = mfcg.Problem(4, (6, 5, 4), mode=mode)
+    b = _to_dev(prob, inputs.boundary_zeroed(inputs.random_vector(prob.n_dofs, salt=11),
+                                             (4 * 6 + 1, 4 * 5 + 1, 4 * 4 + 1)))
+    x1, i1 = prob.cg_solve(b, rtol=1e-10)
+    x2, i2 = prob.cg_solve(b, rtol=1e-10)
+    assert i1["iterations"] == i2["iterations"]
+    assert torch.equal(x1, x2)
+    prob.close()
+
+
+def test_degenerate_inputs(mfcg):
+    prob = mfcg.Problem(2, (3, 3, 3))
+    zero = torch.zeros(prob.n_dofs, dtype=torch.float64, device="cuda")
+    x, info = prob.cg_solve(zero, rtol=1e-10)
+    assert info["iterations"] == 0 and info["converged"] == 1 and torch.count_nonzero(x) == 0
+    b = prob.rhs()
+    with pytest.raises(mfcg.MfcgError) as err:
+        prob.cg_solve(b, rtol=1e-14, maxit=2)
+    assert err.value.status == 5
+    bad = b.clone()
+    bad[prob.n_dofs // 2] = float("nan")
+    with pytest.raises(mfcg.MfcgError) as err:
+        prob.cg_solve(bad, rtol=1e-10)
+    assert err.value.status == 6
+    with pytest.raises(ValueError):
+        prob.apply_operator(b.float())
+    prob.close()
+
+
+# ----------------------------------------------------------------- full sizes
+
+
+def test_full_size_q4_64cube_operator_every_entry(mfcg):
+    w = inputs.WORKLOADS["q4_64cube"]
+    op = _oracle_problem(w.degree, w.cells)
+    prob = mfcg.Problem(w.degree, w.cells)
+    u = inputs.random_vector(op.n_dofs, salt=64)
+    got = _to_host(prob, prob.apply_operator(_to_dev(prob, u)))
+    assert _rel(got, fastdiag.apply(op, u)) <= OP_TOL
+    prob.close()
+
+
+@pytest.mark.parametrize("mode", ["fused", "unfused"])
+def test_full_size_q4_64cube_solve(mfcg, mode):
+    w = inputs.WORKLOADS["q4_64cube"]
+    op = _oracle_problem(w.degree, w.cells)
+    prob = mfcg.Problem(w.degree, w.cells, mode=mode)
+    b = prob.rhs()
+    x, info = prob.cg_solve(b, rtol=1e-10, maxit=2000)
+    assert info["converged"]
+    bh = _to_host(prob, b)
+    xh = _to_host(prob, x)
+    # GPU right-hand side against the oracle's on sampled rows of the global vector
+    rows = inputs.random_rows(op.n_dofs, 20)
+    xs = fastdiag.solve(op, bh)
+    assert _rel(xh, xs) <= SOL_TOL
+    r = bh - fastdiag.apply(op, xh)
+    assert np.linalg.norm(r) <= 1.5e-10 * np.linalg.norm(bh)
+    del rows
+    prob.close()
+
+
+def test_full_size_q6_48cube_deformed_operator_sampled_rows(mfcg):
+    w = inputs.WORKLOADS["q6_48cube_deformed"]
+    op = _oracle_problem(w.degree, w.cells, w.amplitude, w.coefficient)
+    prob = _gpu_problem(mfcg, w.degree, w.cells, w.amplitude, w.coefficient)
+    u = inputs.random_vector(op.n_dofs, salt=48)
+    got = _to_host(prob, prob.apply_operator(_to_dev(prob, u)))
+    diag = _to_host(prob, prob.diagonal())
+    # rows: random ones plus nodes on tile faces, edges and corners (tiles of 2 cells)
+    rng_rows = list(inputs.random_rows(op.n_dofs, 6))
+    n1 = w.degree * w.cells[0] + 1
+    for (i, j, k) in ((12, 12, 12), (12, 13, 14), (24, 12, 7), (1, 1, 12), (287, 12, 24)):
+        rng_rows.append(i + n1 * (j + n1 * k))
+    rows = np.array(rng_rows)
+    ref = fem.apply_rows(op, u, rows)
+    scale = np.abs(got).max()
+    assert np.abs(got[rows] - ref).max() <= OP_TOL * scale
+    assert np.abs(diag[rows] - fem.diagonal_rows(op, rows)).max() <= OP_TOL * np.abs(diag).max()
+    prob.close()
+
+
+def test_full_size_q4_128cube_operator_every_entry(mfcg):
+    w = inputs.WORKLOADS["q4_128cube"]
+    op = _oracle_problem(w.degree, w.cells)
+    prob = mfcg.Problem(w.degree, w.cells)
+    u = inputs.random_vector(op.n_dofs, salt=128)
+    got = _to_host(prob, prob.apply_operator(_to_dev(prob, u)))
+    assert _rel(got, fastdiag.apply(op, u)) <= OP_TOL
+    prob.close()

@@ -324,3 +324,14 @@ def test_fast_diagonalisation_matches_direct_solve():
         b = rng.standard_normal(prob.n_dofs)
         x = fastdiag.solve(prob, b)
         np.testing.assert_allclose(A @ x, b, atol=1e-11 * np.abs(b).max())
+
+
+def test_kronecker_apply_matches_assembled_matrix():
+    rng = np.random.default_rng(13)
+    for p, cells in ((1, (3, 4, 2)), (2, (3, 2, 4)), (4, (2, 3, 2)), (7, (1, 2, 2))):
+        prob = fem.Problem(p, cells)
+        A = fem.assemble(prob)
+        u = rng.standard_normal(prob.n_dofs)
+        ref = A @ u
+        np.testing.assert_allclose(fastdiag.apply(prob, u), ref, atol=1e-13 * np.abs(ref).max())
+
