@@ -1,0 +1,386 @@
+#!/usr/bin/env python3
+"""Benchmark of the fused matrix-free Jacobi-CG (Algorithm 5) on GB300.
+
+One step = one CG solve of the workload with a fixed number of iterations
+(default 200, x0 = 0, manufactured right-hand side): start-up (r0 = b - A x0,
+scalars), the fused iterations (pre, sum-factorised operator, post, seven
+sums, device-side reduction and scalars) and the parity-dependent
+finalisation of x.  The metric is GDoF-iterations/s = n * iterations / s and
+its fraction of the HBM roofline, for the fused path and for the plain unfused
+GPU CG (separate operator, axpy, Jacobi and dot kernels) on the same workload.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With --gpus N > 1 (launched by torchrun) every rank runs an independent
+replica of the workload (the method has no cross-replica exchange): value is
+the sum over ranks, time the maximum over ranks.  --impl reference times the
+CPU oracle (assembled sparse matrix + textbook Algorithm 1) on the host.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CG GDoF-iterations/s and % of HBM roofline, fused vs unfused GPU CG at rtol 1e-10"
+UNIT = "GDoF-it/s"
+FP64_PEAK_TFLOPS = 1.25          # nominal FP64 rate of GB300 (dense, FMA = 2 flops)
+FALLBACK_HBM_GBS = 6800.0
+KERNEL_SOURCES = ["paper_2205_08909_gb300/csrc/tile_kernels.cuh", "paper_2205_08909_gb300/csrc/mfcg_internal.h"]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
+
+
+def kernel_sources_hash() -> str:
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def stored_traffic(workload: str):
+    """DRAM bytes per launch of the fused tile kernel from the committed ncu
+    summary, or None if it is missing or was taken on different kernel sources."""
+    path = os.path.join(ROOT, "profiles", f"fused_cg_tile_kernel_{workload}.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    s = re.search(r"kernel_sources_sha256:\s*([0-9a-f]+)", text)
+    if not m or not s or s.group(1) != kernel_sources_hash():
+        return None
+    return float(m.group(1))
+
+
+# ------------------------------------------------------------------------------ algorithmic counts
+
+def algorithmic_flops_per_iteration(degree: int, n_cells: int, n_dofs: int) -> float:
+    """FP64 flops of one fused iteration: seven 1D sweeps of (p+1)^4 FMAs per
+    cell (Kronecker form of the affine cell operator) plus the vector work per
+    unknown (r, z, p updates 5, x update 5 every other iteration, seven sums
+    with M^-1 r and M^-1 v 16)."""
+    return 2.0 * 7 * (degree + 1) ** 4 * n_cells + 23.5 * n_dofs
+
+
+ALGORITHMIC_BYTES_PER_DOF = 64.0  # r, p, v read+write, D^-1 read, x read+write every other iteration
+
+
+# ------------------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.25)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except OSError:
+            pass
+        finally:
+            if self.path:
+                os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------------------ CPU oracle
+
+def oracle_sample(degree: int, cells: int, iters: int):
+    """Times the oracle's Algorithm 1 (assembled CSR, scipy SpMV, numpy vector
+    ops, one host thread) on a Cartesian Q_degree mesh of cells^3 for a fixed
+    number of iterations.  Returns (GDoF-it/s, seconds, n_dofs, setup seconds)."""
+    from oracle import cg as ocg
+    from oracle import fem
+
+    t0 = time.perf_counter()
+    prob = fem.Problem(degree, (cells, cells, cells))
+    A = fem.assemble(prob)
+    b = fem.rhs(prob)
+    inv_diag = 1.0 / A.diagonal()
+    setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    res = ocg.pcg_algorithm1(lambda v: A @ v, b, inv_diag, 0.0, iters)
+    dt = time.perf_counter() - t0
+    return prob.n_dofs * res.iterations / dt / 1e9, dt, prob.n_dofs, setup
+
+
+# ------------------------------------------------------------------------------ distributed
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        backend = "nccl" if (args.impl == "ours" and torch.cuda.is_available()) else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------------------ arms
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return None
+    from paper_2205_08909_gb300 import inputs
+
+    w = inputs.WORKLOADS[args.workload]
+    cells = args.ref_cells
+    for _ in range(args.warmup):
+        oracle_sample(w.degree, cells, 2)
+    vals, secs = [], []
+    n = 0
+    for _ in range(args.steps):
+        v, dt, n, _setup = oracle_sample(w.degree, cells, args.ref_iters)
+        vals.append(v)
+        secs.append(dt)
+    value = sum(vals) / len(vals)
+    sample = (f"oracle Algorithm 1 (assembled CSR, scipy SpMV) on Q{w.degree} {cells}^3 Cartesian "
+              f"({n} DoFs), {args.ref_iters} fixed iterations per step, same degree as {w.name}")
+    return {
+        "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * sum(secs) / len(secs), 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "degree": w.degree, "cells": list(w.cells), "sample_cells": [cells] * 3},
+        "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    import paper_2205_08909_gb300 as mfcg
+    from paper_2205_08909_gb300 import build, inputs
+
+    build.build()
+    torch.cuda.set_device(local)
+    w = inputs.WORKLOADS[args.workload]
+    n_cells = w.cells[0] * w.cells[1] * w.cells[2]
+    K, W, iters = args.steps, args.warmup, args.iters
+    peaks, peak_kind = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+
+    def make(mode, instrument=False):
+        return mfcg.Problem(w.degree, w.cells, amplitude=w.amplitude, geometry=w.geometry,
+                            coefficient=w.coefficient, mode=mode, instrument=instrument)
+
+    def timed_steps(prob, b, K, W):
+        xs = [torch.zeros(prob.n_dofs, dtype=torch.float64, device="cuda") for _ in range(max(K, W))]
+        for i in range(W):
+            prob.cg_solve(b, xs[i], rtol=0.0, maxit=iters)
+        launches = 0
+        torch.cuda.synchronize()
+        barrier(world)
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for i in range(K):
+            _, info = prob.cg_solve(b, xs[i], rtol=0.0, maxit=iters)
+            launches += info["kernel_launches"]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        ms = e0.elapsed_time(e1)
+        return max_over_ranks(ms, world), launches, xs[0]
+
+    # ---------------- fused FP64 (the product path)
+    fused = make("fused")
+    b = fused.rhs()
+    with ClockSampler(local) as clk:
+        ms_f, launches_f, _ = timed_steps(fused, b, K, W)
+    clocks = clk.summary()
+    dof_its = w.n_dofs * iters * K * world
+    value = dof_its / (ms_f / 1e3) / 1e9
+
+    # ---------------- converged solve to rtol 1e-10
+    xc = torch.zeros(w.n_dofs, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, info_c = fused.cg_solve(b, xc, rtol=1e-10, maxit=100000)
+    torch.cuda.synchronize()
+    solve_ms = 1e3 * (time.perf_counter() - t0)
+
+    # ---------------- unfused comparator (Algorithm 1, one kernel per vector op)
+    unfused_line = None
+    if not args.skip_unfused:
+        unf = make("unfused")
+        ms_u, _, _ = timed_steps(unf, b, K, W)
+        value_u = dof_its / (ms_u / 1e3) / 1e9
+        xu = torch.zeros(w.n_dofs, dtype=torch.float64, device="cuda")
+        _, info_u = unf.cg_solve(b, xu, rtol=1e-10, maxit=100000)
+        unfused_line = {"value": round(value_u, 4), "ms_per_step": round(ms_u / K, 3),
+                        "fused_over_unfused": round(value / value_u, 4),
+                        "hbm_roofline_frac": round(value_u * 152.0 / hbm, 4),
+                        "algorithmic_bytes_per_dof": 152, "solve_rtol_1e-10_iterations": info_u["iterations"],
+                        "kernels_per_iteration": 9}
+        unf.close()
+
+    # ---------------- dominant kernel: fused tile kernel, CUDA events around every launch
+    inst = make("fused", instrument=True)
+    xi = torch.zeros(w.n_dofs, dtype=torch.float64, device="cuda")
+    inst.cg_solve(b, xi, rtol=0.0, maxit=min(iters, 8))
+    _, info_i = inst.cg_solve(b, xi.zero_(), rtol=0.0, maxit=iters)
+    kernel_ms = info_i["main_kernel_ms"] / max(info_i["main_kernel_launches"], 1)
+    inst.close()
+    flops = algorithmic_flops_per_iteration(w.degree, n_cells, w.n_dofs)
+    achieved_tflops = flops / (kernel_ms / 1e3) / 1e12
+    traffic = stored_traffic(w.name)
+    roofline = {"bound": "alu", "achieved": round(achieved_tflops, 4), "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": round(achieved_tflops / FP64_PEAK_TFLOPS, 4),
+                "traffic": traffic, "kernel": "tile_kernel<4, MODE_CG, GEOM_AFFINE>",
+                "kernel_ms": round(kernel_ms, 4), "algorithmic_flops_per_launch": flops,
+                "peak_kind": "nominal FP64 (recipe table)",
+                "hbm_view": {"achieved_gbs": round(ALGORITHMIC_BYTES_PER_DOF * w.n_dofs / (kernel_ms / 1e3) / 1e9, 1),
+                             "peak_gbs": hbm, "peak_kind": peak_kind,
+                             "frac": round(ALGORITHMIC_BYTES_PER_DOF * w.n_dofs / (kernel_ms / 1e3) / 1e9 / hbm, 4)}}
+
+    # ---------------- end to end through the host-array entry point
+    e2e = None
+    if not args.skip_e2e:
+        bh = b.cpu().pin_memory()
+        xh = [torch.zeros(w.n_dofs, dtype=torch.float64).pin_memory() for _ in range(K)]
+        fused.cg_solve_host(bh, torch.zeros(w.n_dofs, dtype=torch.float64).pin_memory(), rtol=0.0, maxit=iters)
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        for i in range(K):
+            fused.cg_solve_host(bh, xh[i], rtol=0.0, maxit=iters)
+        torch.cuda.synchronize()
+        barrier(world)
+        sec = max_over_ranks(time.perf_counter() - t0, world)
+        e2e = {"value": round(dof_its / sec / 1e9, 4), "unit": UNIT,
+               "h2d_bytes_per_step": 2 * 8 * w.n_dofs, "d2h_bytes_per_step": 8 * w.n_dofs}
+    fused.close()
+
+    line = {
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": round(ms_f / K, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic: manufactured right-hand side of u = sin(pi x) sin(pi y) sin(pi z), x0 = 0",
+        "config": {"workload": w.name, "degree": w.degree, "cells": list(w.cells), "n_dofs": w.n_dofs,
+                   "geometry": w.geometry, "iterations_per_step": iters, "parallelism": f"replicas x{world}",
+                   "l2": f"inputs larger than L2: {8 * w.n_dofs / 1e6:.0f} MB per vector, 8 vectors"},
+        "hbm_roofline_frac": round(value / world * ALGORITHMIC_BYTES_PER_DOF / hbm, 4),
+        "algorithmic_bytes_per_dof": ALGORITHMIC_BYTES_PER_DOF,
+        "unfused": unfused_line,
+        "solve_rtol_1e-10": {"iterations": info_c["iterations"], "ms": round(solve_ms, 3),
+                             "converged": info_c["converged"]},
+        "roofline": roofline,
+        "e2e": e2e,
+        "gpu_launches": launches_f,
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        v, dt, n, _setup = oracle_sample(w.degree, args.ref_cells, args.ref_iters)
+        line["cpu_baseline"] = {"value": round(v, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"Algorithm 1 on the assembled CSR matrix, Q{w.degree} {args.ref_cells}^3 "
+                                          f"Cartesian ({n} DoFs), {args.ref_iters} iterations, {dt:.1f} s"}
+    return line if rank == 0 else None
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="q4_64cube")
+    ap.add_argument("--iters", type=int, default=200, help="CG iterations per step")
+    ap.add_argument("--ref-cells", type=int, default=16, help="cells per direction of the oracle sample")
+    ap.add_argument("--ref-iters", type=int, default=150, help="iterations of the oracle sample")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-unfused", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        line = run_reference(args, world, rank)
+    else:
+        line = run_ours(args, world, rank, local)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
