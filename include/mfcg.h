@@ -135,8 +135,8 @@ int mfcg_rhs(mfcg_problem* prob, double* b);
  *   b   in : device, n doubles, must be zero on Dirichlet nodes (INVALID_ARG is
  *            not checked on the device; a nonzero value there is solved as an
  *            identity row).
- *   x   in/out: device, n doubles; initial guess on entry (all-zero skips A x0),
- *            solution on return.
+ *   x   in/out: device, n doubles; initial guess on entry (r_0 = b - A x_0 is
+ *            always formed), solution on return.
  *   info out: may be NULL.
  * Synchronises the stream.  Returns OK, NOT_CONVERGED, BREAKDOWN or CUDA_ERROR. */
 int mfcg_cg_solve(mfcg_problem* prob, const double* b, double* x, double rtol, int maxit,
