@@ -36,7 +36,8 @@ METRIC = "CG GDoF-iterations/s and % of HBM roofline, fused vs unfused GPU CG at
 UNIT = "GDoF-it/s"
 FP64_PEAK_TFLOPS = 1.25          # nominal FP64 rate of GB300 (dense, FMA = 2 flops)
 FALLBACK_HBM_GBS = 6800.0
-KERNEL_SOURCES = ["paper_2205_08909_gb300/csrc/tile_kernels.cuh", "paper_2205_08909_gb300/csrc/mfcg_internal.h"]
+KERNEL_SOURCES = ["paper_2205_08909_gb300/csrc/tile_kernels.cuh", "paper_2205_08909_gb300/csrc/mfcg_internal.h",
+                  "paper_2205_08909_gb300/csrc/precision.cuh"]
 
 
 def measured_peaks():
@@ -55,10 +56,10 @@ def kernel_sources_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def stored_traffic(workload: str):
+def stored_traffic(workload: str, precision: str):
     """DRAM bytes per launch of the fused tile kernel from the committed ncu
     summary, or None if it is missing or was taken on different kernel sources."""
-    path = os.path.join(ROOT, "profiles", f"fused_cg_tile_kernel_{workload}.md")
+    path = os.path.join(ROOT, "profiles", f"fused_cg_tile_kernel_{workload}_{precision}.md")
     try:
         text = open(path).read()
     except OSError:
@@ -223,6 +224,28 @@ def run_reference(args, world, rank):
     }
 
 
+def dd_ops_per_dof(degree: int, n_cells: int, n_dofs: int) -> float:
+    """FP32-pipe operations of one fused double-float iteration per unknown,
+    counted from the error-free transformations: a product accumulated into a
+    (s, t) pair costs 12 (TwoProduct 2, cross terms 2, TwoSum 6, error sum 2),
+    the first product of a sum 4, a normalisation 3, a pair addition 11, a pair
+    product 7.  Operator: per cell and pencil the z sweep (M, K_z), the y sweep
+    (M; K_y + M) and the x sweep (K_x + M, added into the node brick)."""
+    n1 = degree + 1
+    mv = n1 * (4 + 12 * (n1 - 1) + 3)
+    mv2 = n1 * (4 + 12 * (2 * n1 - 1) + 3)
+    per_cell = n1 * n1 * (2 * mv + (mv + mv2) + (mv2 + 11 * n1))
+    pre = 34.0 * 1.2                                  # r and p updates on the tile brick (~1.2x the owned nodes)
+    x_update = 48.0 / 2                               # every other iteration
+    post = 2 * 7 + 7 * 12                             # M^-1 r, M^-1 v and seven accumulations
+    return per_cell * n_cells / n_dofs + pre + x_update + post
+
+
+def fp32_pipe_peak_tops() -> float:
+    """152 SMs x 128 FP32 lanes x 2.07 GHz (maximum SM clock)."""
+    return 152 * 128 * 2.07e9 / 1e12
+
+
 def run_ours(args, world, rank, local):
     import torch
 
@@ -236,13 +259,14 @@ def run_ours(args, world, rank, local):
     K, W, iters = args.steps, args.warmup, args.iters
     peaks, peak_kind = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    main_prec = args.precision
 
-    def make(mode, instrument=False):
+    def make(mode, precision, instrument=False):
         return mfcg.Problem(w.degree, w.cells, amplitude=w.amplitude, geometry=w.geometry,
-                            coefficient=w.coefficient, mode=mode, instrument=instrument)
+                            coefficient=w.coefficient, mode=mode, precision=precision, instrument=instrument)
 
     def timed_steps(prob, b, K, W):
-        xs = [torch.zeros(prob.n_dofs, dtype=torch.float64, device="cuda") for _ in range(max(K, W))]
+        xs = [torch.zeros(prob.n_dofs, dtype=torch.float64, device="cuda") for _ in range(max(K, W, 1))]
         for i in range(W):
             prob.cg_solve(b, xs[i], rtol=0.0, maxit=iters)
         launches = 0
@@ -259,58 +283,85 @@ def run_ours(args, world, rank, local):
         torch.cuda.synchronize()
         barrier(world)
         ms = e0.elapsed_time(e1)
-        return max_over_ranks(ms, world), launches, xs[0]
+        return max_over_ranks(ms, world), launches
 
-    # ---------------- fused FP64 (the product path)
-    fused = make("fused")
+    def converged_solve(prob, b):
+        xc = torch.zeros(w.n_dofs, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, info = prob.cg_solve(b, xc, rtol=1e-10, maxit=100000)
+        torch.cuda.synchronize()
+        return {"iterations": info["iterations"], "ms": round(1e3 * (time.perf_counter() - t0), 3),
+                "converged": info["converged"], "outer_cycles": info["outer_cycles"]}
+
+    dof_its = w.n_dofs * iters * K * world
+
+    # ---------------- headline: fused CG in the requested precision
+    fused = make("fused", main_prec)
     b = fused.rhs()
     with ClockSampler(local) as clk:
-        ms_f, launches_f, _ = timed_steps(fused, b, K, W)
+        ms_f, launches_f = timed_steps(fused, b, K, W)
     clocks = clk.summary()
-    dof_its = w.n_dofs * iters * K * world
     value = dof_its / (ms_f / 1e3) / 1e9
+    solve_main = converged_solve(fused, b)
 
-    # ---------------- converged solve to rtol 1e-10
-    xc = torch.zeros(w.n_dofs, dtype=torch.float64, device="cuda")
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    _, info_c = fused.cg_solve(b, xc, rtol=1e-10, maxit=100000)
-    torch.cuda.synchronize()
-    solve_ms = 1e3 * (time.perf_counter() - t0)
+    # ---------------- comparators on the same workload
+    variants = {}
+    for mode, prec in (("unfused", main_prec), ("fused", "fp64"), ("unfused", "fp64")):
+        if args.skip_unfused and mode == "unfused":
+            continue
+        if prec == main_prec and mode == "fused":
+            continue
+        prob = make(mode, prec)
+        ms_v, _ = timed_steps(prob, b, K, W)
+        v = dof_its / (ms_v / 1e3) / 1e9
+        bytes_per_dof = 64 if mode == "fused" else 152
+        variants[f"{mode}_{prec}"] = {"value": round(v, 4), "ms_per_step": round(ms_v / K, 3),
+                                      "hbm_roofline_frac": round(v / world * bytes_per_dof / hbm, 4),
+                                      "algorithmic_bytes_per_dof": bytes_per_dof,
+                                      "solve_rtol_1e-10": converged_solve(prob, b)}
+        prob.close()
+    unf_key = f"unfused_{main_prec}"
+    fused_over_unfused = round(value / variants[unf_key]["value"], 4) if unf_key in variants else None
 
-    # ---------------- unfused comparator (Algorithm 1, one kernel per vector op)
-    unfused_line = None
-    if not args.skip_unfused:
-        unf = make("unfused")
-        ms_u, _, _ = timed_steps(unf, b, K, W)
-        value_u = dof_its / (ms_u / 1e3) / 1e9
-        xu = torch.zeros(w.n_dofs, dtype=torch.float64, device="cuda")
-        _, info_u = unf.cg_solve(b, xu, rtol=1e-10, maxit=100000)
-        unfused_line = {"value": round(value_u, 4), "ms_per_step": round(ms_u / K, 3),
-                        "fused_over_unfused": round(value / value_u, 4),
-                        "hbm_roofline_frac": round(value_u * 152.0 / hbm, 4),
-                        "algorithmic_bytes_per_dof": 152, "solve_rtol_1e-10_iterations": info_u["iterations"],
-                        "kernels_per_iteration": 9}
-        unf.close()
+    # ---------------- FP64 defect correction around the FP32 fused CG (time to rtol 1e-10)
+    dc = None
+    if not args.skip_dc:
+        dcp = make("fused", "fp32_inner")
+        converged_solve(dcp, b)
+        dc = converged_solve(dcp, b)
+        dcp.close()
 
     # ---------------- dominant kernel: fused tile kernel, CUDA events around every launch
-    inst = make("fused", instrument=True)
+    inst = make("fused", main_prec, instrument=True)
     xi = torch.zeros(w.n_dofs, dtype=torch.float64, device="cuda")
     inst.cg_solve(b, xi, rtol=0.0, maxit=min(iters, 8))
     _, info_i = inst.cg_solve(b, xi.zero_(), rtol=0.0, maxit=iters)
     kernel_ms = info_i["main_kernel_ms"] / max(info_i["main_kernel_launches"], 1)
     inst.close()
-    flops = algorithmic_flops_per_iteration(w.degree, n_cells, w.n_dofs)
-    achieved_tflops = flops / (kernel_ms / 1e3) / 1e12
-    traffic = stored_traffic(w.name)
-    roofline = {"bound": "alu", "achieved": round(achieved_tflops, 4), "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": round(achieved_tflops / FP64_PEAK_TFLOPS, 4),
-                "traffic": traffic, "kernel": "tile_kernel<4, MODE_CG, GEOM_AFFINE>",
-                "kernel_ms": round(kernel_ms, 4), "algorithmic_flops_per_launch": flops,
-                "peak_kind": "nominal FP64 (recipe table)",
-                "hbm_view": {"achieved_gbs": round(ALGORITHMIC_BYTES_PER_DOF * w.n_dofs / (kernel_ms / 1e3) / 1e9, 1),
-                             "peak_gbs": hbm, "peak_kind": peak_kind,
-                             "frac": round(ALGORITHMIC_BYTES_PER_DOF * w.n_dofs / (kernel_ms / 1e3) / 1e9 / hbm, 4)}}
+    hbm_gbs = ALGORITHMIC_BYTES_PER_DOF * w.n_dofs / (kernel_ms / 1e3) / 1e9
+    traffic = stored_traffic(w.name, main_prec)
+    if main_prec == "fp64":
+        flops = algorithmic_flops_per_iteration(w.degree, n_cells, w.n_dofs)
+        achieved = flops / (kernel_ms / 1e3) / 1e12
+        roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
+                    "peak_kind": "nominal FP64 (recipe table)", "algorithmic_flops_per_launch": flops}
+    elif main_prec == "double_float":
+        ops = dd_ops_per_dof(w.degree, n_cells, w.n_dofs) * w.n_dofs
+        achieved = ops / (kernel_ms / 1e3) / 1e12
+        peak = fp32_pipe_peak_tops()
+        roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 2),
+                    "unit": "T FP32-pipe ops/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+                    "peak_kind": "152 SMs x 128 FP32 lanes x 2.07 GHz", "algorithmic_ops_per_launch": ops}
+    else:
+        achieved = hbm_gbs / 2  # FP32 storage: 32 B per unknown
+        roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                    "frac": round(achieved / hbm, 4), "traffic": traffic, "peak_kind": peak_kind}
+    roofline.update({"kernel": f"tile_kernel<{w.degree}, MODE_CG, GEOM_{w.geometry.upper()}, {main_prec}>",
+                     "kernel_ms": round(kernel_ms, 4),
+                     "hbm_view": {"achieved_gbs": round(hbm_gbs, 1), "peak_gbs": hbm, "peak_kind": peak_kind,
+                                  "frac": round(hbm_gbs / hbm, 4)}})
 
     # ---------------- end to end through the host-array entry point
     e2e = None
@@ -330,18 +381,23 @@ def run_ours(args, world, rank, local):
                "h2d_bytes_per_step": 2 * 8 * w.n_dofs, "d2h_bytes_per_step": 8 * w.n_dofs}
     fused.close()
 
+    dtype = {"fp64": "f64", "double_float": "f32x2 (double-float, ~48-bit; FP64 scalars and reductions)",
+             "fp32_inner": "f32"}[main_prec]
     line = {
         "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": round(ms_f / K, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic: manufactured right-hand side of u = sin(pi x) sin(pi y) sin(pi z), x0 = 0",
+        "dtype": dtype,
+        "data": "synthetic: manufactured right-hand side of u = sin(pi x) sin(pi y) sin(pi z), x0 = 0",
         "config": {"workload": w.name, "degree": w.degree, "cells": list(w.cells), "n_dofs": w.n_dofs,
-                   "geometry": w.geometry, "iterations_per_step": iters, "parallelism": f"replicas x{world}",
+                   "geometry": w.geometry, "precision": main_prec, "iterations_per_step": iters,
+                   "parallelism": f"replicas x{world}",
                    "l2": f"inputs larger than L2: {8 * w.n_dofs / 1e6:.0f} MB per vector, 8 vectors"},
         "hbm_roofline_frac": round(value / world * ALGORITHMIC_BYTES_PER_DOF / hbm, 4),
         "algorithmic_bytes_per_dof": ALGORITHMIC_BYTES_PER_DOF,
-        "unfused": unfused_line,
-        "solve_rtol_1e-10": {"iterations": info_c["iterations"], "ms": round(solve_ms, 3),
-                             "converged": info_c["converged"]},
+        "fused_over_unfused": fused_over_unfused,
+        "solve_rtol_1e-10": solve_main,
+        "variants": variants,
+        "defect_correction_fp32_inner": dc,
         "roofline": roofline,
         "e2e": e2e,
         "gpu_launches": launches_f,
@@ -368,6 +424,9 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-unfused", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-dc", action="store_true", help="skip the FP32-inner defect-correction solve")
+    ap.add_argument("--precision", default="double_float", choices=["fp64", "double_float", "fp32_inner"],
+                    help="arithmetic of the headline fused path")
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":

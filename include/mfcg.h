@@ -74,13 +74,26 @@ typedef enum mfcg_mode {
   MFCG_MODE_UNFUSED = 1     /* Algorithm 1 with a separate operator, axpy, Jacobi and dot kernel   */
 } mfcg_mode;
 
+/* Arithmetic of the operator and of the CG vectors.  The ABI is FP64 in every case. */
+typedef enum mfcg_precision {
+  MFCG_PREC_FP64 = 0,         /* native FP64 everywhere                                                 */
+  MFCG_PREC_DOUBLE_FLOAT = 1, /* operator and fused CG vectors as unevaluated pairs of FP32 numbers
+                                 (about 48 significant bits) on the FP32 pipes; operator results
+                                 within 1e-13 (normwise) of FP64; scalars and reductions in FP64      */
+  MFCG_PREC_FP32_INNER = 2    /* FP64 defect correction: the true residual b - A x with the FP64
+                                 operator, inner fused CG in FP32 (sums reduced in FP64) to
+                                 inner_rtol per cycle, x updated in FP64; FUSED mode only             */
+} mfcg_precision;
+
 typedef struct mfcg_options {
   int32_t mode;             /* mfcg_mode                                                            */
   int32_t graph_iterations; /* CG iterations per captured CUDA graph (even; 0 = 16)                   */
   int32_t instrument;       /* 1: launch without graphs and time every operator-pass kernel with
                                CUDA events (mfcg_solve_info.main_kernel_ms); 0: graphs, no timing      */
   int32_t tile[3];          /* cells per tile and direction; 0 = chosen from the degree               */
-  int32_t reserved[2];      /* must be zero                                                          */
+  int32_t precision;        /* mfcg_precision                                                       */
+  int32_t reserved;         /* must be zero                                                          */
+  double inner_rtol;        /* MFCG_PREC_FP32_INNER: residual reduction of each inner solve (0 = 1e-3) */
 } mfcg_options;
 
 typedef struct mfcg_solve_info {
@@ -92,6 +105,8 @@ typedef struct mfcg_solve_info {
   double rhs_norm_sq;         /* ||b||^2                                                           */
   double main_kernel_ms;      /* summed CUDA-event time of the operator-pass kernels (instrument = 1) */
   int64_t kernel_launches;    /* kernels this call enqueued, graph replays included                */
+  int32_t outer_cycles;       /* MFCG_PREC_FP32_INNER: defect-correction cycles, else 0            */
+  int32_t reserved2;
 } mfcg_solve_info;
 
 typedef struct mfcg_problem mfcg_problem;
@@ -105,7 +120,8 @@ typedef struct mfcg_problem mfcg_problem;
  *   cuda_stream   in: cudaStream_t (NULL = legacy default stream) used by every call.
  *   out           out: new handle; release with mfcg_destroy.
  * Errors: INVALID_ARG (cells < 1, |amplitude| >= 0.1, affine kind with A != 0 or
- * a != 1, bad enums), UNSUPPORTED_DEGREE, OUT_OF_MEMORY, CUDA_ERROR. */
+ * a != 1, bad enums, FP32_INNER with UNFUSED), UNSUPPORTED_DEGREE,
+ * OUT_OF_MEMORY, CUDA_ERROR. */
 int mfcg_setup(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, const mfcg_options* opt,
                void* cuda_stream, mfcg_problem** out);
 
@@ -131,7 +147,9 @@ int mfcg_rhs(mfcg_problem* prob, double* b);
 /* mfcg_cg_solve -- Jacobi-preconditioned CG from the initial guess in x
  * (Algorithm 5 in FUSED mode, Algorithm 1 in UNFUSED mode) until
  * ||r_k|| < rtol ||b|| (unpreconditioned residual, Sec. 3.1) or maxit products
- * A p.  rtol == 0 runs exactly maxit iterations and returns MFCG_OK.
+ * A p.  rtol == 0 runs exactly maxit iterations and returns MFCG_OK (not
+ * available with MFCG_PREC_FP32_INNER, which stops on the true residual
+ * ||b - A x|| < rtol ||b|| and counts maxit over all inner iterations).
  *   b   in : device, n doubles, must be zero on Dirichlet nodes (INVALID_ARG is
  *            not checked on the device; a nonzero value there is solved as an
  *            identity row).

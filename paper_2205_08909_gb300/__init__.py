@@ -34,13 +34,16 @@ class Problem:
     degree: 1..8; cells: (Nx, Ny, Nz); amplitude: sine deformation of the mesh
     (needs geometry="deformed"); coefficient: "constant" (a = 1) or "sin_x"
     (a = 1 + 0.5 sin(pi x)); mode: "fused" (Algorithm 5 inside the operator
-    pass) or "unfused" (Algorithm 1, one kernel per vector operation).
+    pass) or "unfused" (Algorithm 1, one kernel per vector operation);
+    precision: "fp64", "double_float" (FP32 pairs, ~48 bits) or "fp32_inner"
+    (FP64 defect correction around an FP32 fused CG, inner_rtol per cycle).
     Vectors are float64 CUDA tensors in the library's tile-blocked order.
     """
 
     def __init__(self, degree: int, cells, amplitude: float = 0.0, geometry: str = "affine",
-                 coefficient: str = "constant", mode: str = "fused", graph_iterations: int = 0,
-                 instrument: bool = False, tile=None, stream: torch.cuda.Stream | None = None):
+                 coefficient: str = "constant", mode: str = "fused", precision: str = "fp64",
+                 inner_rtol: float = 0.0, graph_iterations: int = 0, instrument: bool = False, tile=None,
+                 stream: torch.cuda.Stream | None = None):
         if not torch.cuda.is_available():
             raise RuntimeError("paper_2205_08909_gb300 needs a CUDA device (no CPU fallback)")
         self._lib = _binding.load()
@@ -52,6 +55,8 @@ class Problem:
         geom = _binding.Geometry(_binding.GEOM[geometry], _binding.COEF[coefficient])
         opt = _binding.Options()
         opt.mode = _binding.MODE[mode]
+        opt.precision = _binding.PRECISION[precision]
+        opt.inner_rtol = float(inner_rtol)
         opt.graph_iterations = int(graph_iterations)
         opt.instrument = 1 if instrument else 0
         if tile is not None:

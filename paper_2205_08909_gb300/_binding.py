@@ -22,6 +22,7 @@ OK, NOT_CONVERGED, BREAKDOWN = 0, 5, 6
 GEOM = {"affine": 0, "deformed": 1}
 COEF = {"constant": 0, "sin_x": 1}
 MODE = {"fused": 0, "unfused": 1}
+PRECISION = {"fp64": 0, "double_float": 1, "fp32_inner": 2}
 
 
 class Mesh(ctypes.Structure):
@@ -34,14 +35,15 @@ class Geometry(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("graph_iterations", ctypes.c_int32), ("instrument", ctypes.c_int32),
-                ("tile", ctypes.c_int32 * 3), ("reserved", ctypes.c_int32 * 2)]
+                ("tile", ctypes.c_int32 * 3), ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("inner_rtol", ctypes.c_double)]
 
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("converged", ctypes.c_int32), ("status", ctypes.c_int32),
                 ("main_kernel_launches", ctypes.c_int32), ("residual_sq_est", ctypes.c_double),
                 ("rhs_norm_sq", ctypes.c_double), ("main_kernel_ms", ctypes.c_double),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("outer_cycles", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}

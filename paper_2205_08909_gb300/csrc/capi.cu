@@ -1,6 +1,7 @@
 // C ABI of the library (include/mfcg.h): problem setup, operator, diagonal,
 // right-hand side, the fused (Algorithm 5) and unfused (Algorithm 1) CG
-// drivers and the reordering helpers.
+// drivers, the FP64 defect correction around an FP32 fused CG, and the
+// reordering helpers.
 //
 // Execution model: every call runs on a private non-blocking stream that is
 // ordered after the caller's stream on entry and before it on exit (events),
@@ -17,6 +18,7 @@
 #include <vector>
 
 #include "mfcg_internal.h"
+#include "precision.cuh"
 
 namespace mfcg {
 void build_coeffs(int p, const double h[3], double amplitude, int coef, OperatorCoeffs& c);
@@ -37,19 +39,30 @@ struct mfcg_problem {
   TileGeom g{};
   OperatorCoeffs c{};
   int geom_kind = GEOM_AFFINE;
-  double* r[2] = {nullptr, nullptr};
-  double* p[2] = {nullptr, nullptr};
-  double* v[2] = {nullptr, nullptr};
-  double* x = nullptr;
-  double* z = nullptr;
-  double* work = nullptr;
+  int op_prec = PREC_F64;  // apply_operator and FP64-accurate residuals
+  int cg_prec = PREC_F64;  // fused CG iterations
+  // fused CG vectors in the storage type of cg_prec (ping-pong r, p, v), x, M^{-1}
+  void* r[2] = {nullptr, nullptr};
+  void* p[2] = {nullptr, nullptr};
+  void* v[2] = {nullptr, nullptr};
+  void* xs = nullptr;
+  void* dinv_s = nullptr;
+  // FP64 vectors
+  double* x = nullptr;      // unfused iterate / defect-correction iterate
+  double* z = nullptr;      // unfused M^{-1} r
+  double* ur = nullptr;     // unfused r
+  double* up = nullptr;     // unfused p
+  double* uv = nullptr;     // unfused v
+  double* work = nullptr;   // A x0, residuals
   double* bdev = nullptr;   // host-array solves: b
   double* xdev = nullptr;   // host-array solves: x
   double* diag = nullptr;
   double* diag_inv = nullptr;
-  double* shell = nullptr;
+  void* shell = nullptr;
   double* partial = nullptr;
-  double* geo = nullptr;
+  double* geo = nullptr;    // FP64 per-point metric (deformed)
+  void* geo_op = nullptr;   // metric in the operator precision
+  void* geo_cg = nullptr;   // metric in the CG precision
   CGState* state = nullptr;
   CGState* h_state = nullptr;  // pinned, two slots
   int64_t tail_nodes = 0;
@@ -59,6 +72,7 @@ struct mfcg_problem {
   cudaGraphExec_t graph_fused = nullptr;
   cudaGraphExec_t graph_unfused = nullptr;
   int64_t launches = 0;
+  std::vector<void*> owned;  // every device allocation
 };
 
 namespace {
@@ -69,12 +83,16 @@ namespace {
     if (e_ != cudaSuccess) return MFCG_CUDA_ERROR; \
   } while (0)
 
-int alloc(double** p, int64_t n) {
-  if (cudaMalloc(p, (size_t)std::max<int64_t>(n, 1) * sizeof(double)) != cudaSuccess) {
-    *p = nullptr;
+template <typename Ptr>
+int alloc_bytes(mfcg_problem* P, Ptr* p, int64_t bytes) {
+  void* q = nullptr;
+  if (cudaMalloc(&q, (size_t)std::max<int64_t>(bytes, 16)) != cudaSuccess) {
     cudaGetLastError();
+    *p = nullptr;
     return MFCG_OUT_OF_MEMORY;
   }
+  P->owned.push_back(q);
+  *p = static_cast<Ptr>(q);
   return MFCG_OK;
 }
 
@@ -85,23 +103,25 @@ int default_tile(int p, int geom) {
   return geom == GEOM_AFFINE ? affine[p] : deformed[p];
 }
 
-TileArgs base_args(const mfcg_problem* P) {
+TileArgs base_args(const mfcg_problem* P, int prec, const void* geo) {
   TileArgs a{};
   a.g = P->g;
   a.shell = P->shell;
   a.partial = P->partial;
-  a.geo = P->geo;
+  a.geo = geo;
   a.state = P->state;
   a.tail_nodes = P->tail_nodes;
   for (int d = 0; d < 3; ++d) a.fam[d] = P->fam[d];
   a.geom = P->geom_kind;
+  a.prec = prec;
   a.tail_ctas = P->tail_ctas;
   return a;
 }
 
-// operator-like pass (tile kernel + tail): src -> dst in mode
+// operator-like pass (tile kernel + tail) with FP64 input/output
 int run_pass(mfcg_problem* P, int mode, const double* src, double* dst) {
-  TileArgs a = base_args(P);
+  const int prec = mode == MODE_OPERATOR ? P->op_prec : PREC_F64;
+  TileArgs a = base_args(P, prec, mode == MODE_OPERATOR ? P->geo_op : P->geo);
   a.in0 = src;
   a.out0 = dst;
   CK(launch_tile(P->degree, mode, a, P->c, P->exec));
@@ -113,15 +133,15 @@ int run_pass(mfcg_problem* P, int mode, const double* src, double* dst) {
 // one fused CG iteration of the given parity (odd: buffers 0 -> 1)
 int enqueue_fused_iteration(mfcg_problem* P, int odd, cudaEvent_t t0, cudaEvent_t t1) {
   const int o = odd ? 0 : 1, n = odd ? 1 : 0;
-  TileArgs a = base_args(P);
+  TileArgs a = base_args(P, P->cg_prec, P->geo_cg);
   a.in0 = P->r[o];
   a.in1 = P->v[o];
   a.in2 = P->p[o];
-  a.diag_inv = P->diag_inv;
+  a.diag_inv = P->dinv_s;
   a.out0 = P->r[n];
   a.out1 = P->v[n];
   a.out2 = P->p[n];
-  a.x = P->x;
+  a.x = P->xs;
   if (t0) CK(cudaEventRecord(t0, P->exec));
   CK(launch_tile(P->degree, MODE_CG, a, P->c, P->exec));
   if (t1) CK(cudaEventRecord(t1, P->exec));
@@ -134,9 +154,9 @@ UnfusedArgs unfused_args(mfcg_problem* P) {
   u.n = P->g.n_dofs;
   u.diag_inv = P->diag_inv;
   u.x = P->x;
-  u.r = P->r[0];
-  u.p = P->p[0];
-  u.v = P->v[0];
+  u.r = P->ur;
+  u.p = P->up;
+  u.v = P->uv;
   u.z = P->z;
   u.partial = P->partial;
   u.state = P->state;
@@ -147,7 +167,7 @@ int enqueue_unfused_iteration(mfcg_problem* P, cudaEvent_t t0, cudaEvent_t t1) {
   UnfusedArgs u = unfused_args(P);
   if (t0) CK(cudaEventRecord(t0, P->exec));
   // v = A p
-  TileArgs a = base_args(P);
+  TileArgs a = base_args(P, P->op_prec, P->geo_op);
   a.in0 = u.p;
   a.out0 = u.v;
   CK(launch_tile(P->degree, MODE_OPERATOR, a, P->c, P->exec));
@@ -193,30 +213,18 @@ int leave(mfcg_problem* P) {
   return MFCG_OK;
 }
 
-int solve_impl(mfcg_problem* P, const double* b, double* x_user, double rtol, int maxit, mfcg_solve_info* info) {
-  const int64_t n = P->g.n_dofs;
-  const int fused = P->opt.mode == MFCG_MODE_FUSED;
-  const int64_t launches0 = P->launches;
-  int st;
-  // x0 into the internal solution buffer, r0 = b - A x0
-  CK(cudaMemcpyAsync(P->x, x_user, n * sizeof(double), cudaMemcpyDeviceToDevice, P->exec));
-  if ((st = run_pass(P, MODE_OPERATOR, P->x, P->work)) != MFCG_OK) return st;
-  CK(launch_residual(b, P->work, P->r[0], n, P->exec));
-  CK(launch_fill(P->p[0], 0.0, n, P->exec));
-  CK(launch_fill(P->v[0], 0.0, n, P->exec));
-  const int fixed = rtol == 0.0;
-  CK(launch_cg_init(P->state, b, P->r[0], n, rtol, maxit, fixed, P->partial, 0, P->exec));
-  P->launches += 4;
-  if (!fused) {
-    UnfusedArgs u = unfused_args(P);
-    CK(launch_unfused_dot(3, u, P->exec));  // z0 = M^-1 r0, p0 = z0, e0 = r0.z0
-    P->launches += 1;
-  }
-  const int per_iter = fused ? kFusedLaunchesPerIter : kUnfusedLaunchesPerIter;
+struct IterStats {
   double main_ms = 0.0;
   int main_launches = 0;
+};
+
+// Runs CG iterations until the device flag is set or maxit is reached: graphs
+// of G iterations (no per-iteration host synchronisation), or direct launches
+// with CUDA events around every operator-pass kernel when instrumenting.
+int run_iterations(mfcg_problem* P, int fused, int maxit, IterStats& stats) {
+  int st;
+  const int per_iter = fused ? kFusedLaunchesPerIter : kUnfusedLaunchesPerIter;
   if (P->opt.instrument) {
-    // direct launches with an event pair around every operator-pass kernel
     std::vector<cudaEvent_t> ev;
     int done_it = 0;
     while (done_it < maxit) {
@@ -236,64 +244,193 @@ int solve_impl(mfcg_problem* P, const double* b, double* x_user, double rtol, in
       for (int i = 0; i < ran; ++i) {
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]));
-        main_ms += ms;
-        ++main_launches;
+        stats.main_ms += ms;
+        ++stats.main_launches;
       }
       for (auto& e : ev) cudaEventDestroy(e);
       done_it += chunk;
       if (P->h_state->done) break;
     }
-  } else {
-    cudaGraphExec_t* gexec = fused ? &P->graph_fused : &P->graph_unfused;
-    if (!*gexec && (st = capture_graph(P, fused, gexec)) != MFCG_OK) return st;
-    const int G = P->graph_iters;
-    const int n_graphs = (maxit + G - 1) / G;
-    // keep one graph in flight ahead of the flag we read
-    cudaEvent_t evs[2];
-    CK(cudaEventCreateWithFlags(&evs[0], cudaEventDisableTiming));
-    CK(cudaEventCreateWithFlags(&evs[1], cudaEventDisableTiming));
-    int launched = 0, checked = 0;
-    bool finished = false;
-    while (!finished) {
-      while (launched < n_graphs && launched < checked + 2) {
-        CK(cudaGraphLaunch(*gexec, P->exec));
-        CK(cudaMemcpyAsync(P->h_state + (launched & 1), P->state, sizeof(CGState), cudaMemcpyDeviceToHost, P->exec));
-        CK(cudaEventRecord(evs[launched & 1], P->exec));
-        P->launches += (int64_t)G * per_iter;
-        ++launched;
-      }
-      if (checked >= launched) break;
-      CK(cudaEventSynchronize(evs[checked & 1]));
-      if (P->h_state[checked & 1].done) finished = true;
-      ++checked;
-      if (checked >= n_graphs) finished = true;
+    return MFCG_OK;
+  }
+  cudaGraphExec_t* gexec = fused ? &P->graph_fused : &P->graph_unfused;
+  if (!*gexec && (st = capture_graph(P, fused, gexec)) != MFCG_OK) return st;
+  const int G = P->graph_iters;
+  const int n_graphs = (maxit + G - 1) / G;
+  cudaEvent_t evs[2];
+  CK(cudaEventCreateWithFlags(&evs[0], cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&evs[1], cudaEventDisableTiming));
+  int launched = 0, checked = 0;
+  bool finished = n_graphs == 0;
+  while (!finished) {
+    // keep one graph in flight ahead of the flag being read
+    while (launched < n_graphs && launched < checked + 2) {
+      CK(cudaGraphLaunch(*gexec, P->exec));
+      CK(cudaMemcpyAsync(P->h_state + (launched & 1), P->state, sizeof(CGState), cudaMemcpyDeviceToHost, P->exec));
+      CK(cudaEventRecord(evs[launched & 1], P->exec));
+      P->launches += (int64_t)G * per_iter;
+      ++launched;
     }
-    CK(cudaStreamSynchronize(P->exec));
-    cudaEventDestroy(evs[0]);
-    cudaEventDestroy(evs[1]);
+    if (checked >= launched) break;
+    CK(cudaEventSynchronize(evs[checked & 1]));
+    if (P->h_state[checked & 1].done) finished = true;
+    ++checked;
+    if (checked >= n_graphs) finished = true;
   }
+  CK(cudaStreamSynchronize(P->exec));
+  cudaEventDestroy(evs[0]);
+  cudaEventDestroy(evs[1]);
+  return MFCG_OK;
+}
+
+// Fused CG (Algorithm 5) in P->cg_prec on the system A x = b with the FP64
+// initial residual r0 and the initial guess already in P->xs.
+int fused_core(mfcg_problem* P, const double* b, const double* r0, double rtol, int maxit, int fixed,
+               IterStats& stats) {
+  const int64_t n = P->g.n_dofs;
+  const size_t es = prec_bytes(P->cg_prec);
+  CK(launch_cg_init(P->state, b, r0, n, rtol, maxit, fixed, P->partial, 0, P->exec));
+  CK(launch_to_prec(P->cg_prec, r0, P->r[0], n, P->exec));
+  CK(cudaMemsetAsync(P->p[0], 0, n * es, P->exec));
+  CK(cudaMemsetAsync(P->v[0], 0, n * es, P->exec));
+  P->launches += 2;
+  int st = run_iterations(P, 1, maxit, stats);
+  if (st != MFCG_OK) return st;
+  CK(launch_finalize_fused(P->cg_prec, n, P->state, P->xs, P->p[0], P->p[1], P->r[0], P->r[1], P->dinv_s, P->exec));
+  P->launches += 1;
+  return MFCG_OK;
+}
+
+void fill_info(mfcg_problem* P, mfcg_solve_info* info, int status, int iterations, const IterStats& stats,
+               int64_t launches0, int outer) {
+  if (!info) return;
+  const CGState& S = *P->h_state;
+  info->iterations = iterations;
+  info->converged = status == MFCG_OK && S.done == 1;
+  info->status = status;
+  info->main_kernel_launches = stats.main_launches;
+  info->residual_sq_est = S.gamma_next;
+  info->rhs_norm_sq = S.sums[7];
+  info->main_kernel_ms = stats.main_ms;
+  info->kernel_launches = P->launches - launches0;
+  info->outer_cycles = outer;
+  info->reserved2 = 0;
+}
+
+int solve_direct(mfcg_problem* P, const double* b, double* x_user, double rtol, int maxit, mfcg_solve_info* info) {
+  const int64_t n = P->g.n_dofs;
+  const int fused = P->opt.mode == MFCG_MODE_FUSED;
+  const int64_t launches0 = P->launches;
+  const int fixed = rtol == 0.0;
+  IterStats stats;
+  int st;
+  // r0 = b - A x0 in FP64 (operator in the operator precision)
+  if ((st = run_pass(P, MODE_OPERATOR, x_user, P->work)) != MFCG_OK) return st;
+  CK(launch_residual(b, P->work, P->work, n, P->exec));
+  P->launches += 1;
   if (fused) {
-    CK(launch_finalize_fused(P->g, P->state, P->x, P->p[0], P->p[1], P->r[0], P->r[1], P->diag_inv, P->exec));
-    P->launches += 1;
+    CK(launch_to_prec(P->cg_prec, x_user, P->xs, n, P->exec));
+    if ((st = fused_core(P, b, P->work, rtol, maxit, fixed, stats)) != MFCG_OK) return st;
+    CK(launch_from_prec(P->cg_prec, P->xs, x_user, n, 0, P->exec));
+    P->launches += 2;
+  } else {
+    CK(cudaMemcpyAsync(P->x, x_user, n * sizeof(double), cudaMemcpyDeviceToDevice, P->exec));
+    CK(cudaMemcpyAsync(P->ur, P->work, n * sizeof(double), cudaMemcpyDeviceToDevice, P->exec));
+    CK(cudaMemsetAsync(P->uv, 0, n * sizeof(double), P->exec));
+    CK(launch_cg_init(P->state, b, P->ur, n, rtol, maxit, fixed, P->partial, 0, P->exec));
+    UnfusedArgs u = unfused_args(P);
+    CK(launch_unfused_dot(3, u, P->exec));  // z0 = M^-1 r0, p0 = z0, e0 = r0.z0
+    P->launches += 2;
+    if ((st = run_iterations(P, 0, maxit, stats)) != MFCG_OK) return st;
+    CK(cudaMemcpyAsync(x_user, P->x, n * sizeof(double), cudaMemcpyDeviceToDevice, P->exec));
   }
-  CK(cudaMemcpyAsync(x_user, P->x, n * sizeof(double), cudaMemcpyDeviceToDevice, P->exec));
   CK(cudaMemcpyAsync(P->h_state, P->state, sizeof(CGState), cudaMemcpyDeviceToHost, P->exec));
   CK(cudaStreamSynchronize(P->exec));
   const CGState& S = *P->h_state;
   int status = MFCG_OK;
   if (S.done == 3) status = MFCG_BREAKDOWN;
   else if (S.done != 1 && !fixed) status = MFCG_NOT_CONVERGED;
+  fill_info(P, info, status, S.iterations, stats, launches0, 0);
+  return status;
+}
+
+// FP64 defect correction: x_{j+1} = x_j + d_j with A d_j = b - A x_j solved by
+// the FP32 fused CG to a relative reduction inner_rtol; the true residual is
+// formed with the FP64 operator and FP64 vectors.
+int solve_defect_correction(mfcg_problem* P, const double* b, double* x_user, double rtol, int maxit,
+                            mfcg_solve_info* info) {
+  const int64_t n = P->g.n_dofs;
+  const int64_t launches0 = P->launches;
+  const double inner = P->opt.inner_rtol > 0.0 ? P->opt.inner_rtol : 1e-3;
+  IterStats stats;
+  int st;
+  CK(cudaMemcpyAsync(P->x, x_user, n * sizeof(double), cudaMemcpyDeviceToDevice, P->exec));
+  // ||b||^2 once (the reduction kernel of the CG start-up, applied to b alone)
+  CK(launch_cg_init(P->state, b, b, n, 0.0, 1, 0, P->partial, 0, P->exec));
+  CK(cudaMemcpyAsync(P->h_state, P->state, sizeof(CGState), cudaMemcpyDeviceToHost, P->exec));
+  CK(cudaStreamSynchronize(P->exec));
+  P->launches += 1;
+  const double bb = P->h_state->sums[7];
+  int total_it = 0, cycles = 0, status = MFCG_NOT_CONVERGED;
+  double rr = 0.0;
+  while (true) {
+    // true residual r = b - A x; the start-up reduction of the inner CG on
+    // (r, r) gives ||r||^2 and the inner tolerance inner_rtol^2 ||r||^2
+    if ((st = run_pass(P, MODE_OPERATOR, P->x, P->work)) != MFCG_OK) return st;
+    CK(launch_residual(b, P->work, P->work, n, P->exec));
+    CK(launch_cg_init(P->state, P->work, P->work, n, inner, std::max(maxit - total_it, 1), 0, P->partial, 0,
+                      P->exec));
+    CK(cudaMemcpyAsync(P->h_state, P->state, sizeof(CGState), cudaMemcpyDeviceToHost, P->exec));
+    CK(cudaStreamSynchronize(P->exec));
+    P->launches += 2;
+    rr = P->h_state->gamma_next;
+    if (!std::isfinite(rr)) {
+      status = MFCG_BREAKDOWN;
+      break;
+    }
+    if (rr < rtol * rtol * bb || rr == 0.0) {
+      status = MFCG_OK;
+      break;
+    }
+    if (total_it >= maxit) break;
+    // inner FP32 solve of A d = r from d = 0 (its scalars were set by cg_init above)
+    const size_t es = prec_bytes(P->cg_prec);
+    CK(launch_to_prec(P->cg_prec, P->work, P->r[0], n, P->exec));
+    CK(cudaMemsetAsync(P->p[0], 0, n * es, P->exec));
+    CK(cudaMemsetAsync(P->v[0], 0, n * es, P->exec));
+    CK(cudaMemsetAsync(P->xs, 0, n * es, P->exec));
+    P->launches += 1;
+    if ((st = run_iterations(P, 1, maxit - total_it, stats)) != MFCG_OK) return st;
+    CK(launch_finalize_fused(P->cg_prec, n, P->state, P->xs, P->p[0], P->p[1], P->r[0], P->r[1], P->dinv_s,
+                             P->exec));
+    CK(launch_from_prec(P->cg_prec, P->xs, P->x, n, 1, P->exec));  // x += d in FP64
+    CK(cudaMemcpyAsync(P->h_state, P->state, sizeof(CGState), cudaMemcpyDeviceToHost, P->exec));
+    CK(cudaStreamSynchronize(P->exec));
+    P->launches += 2;
+    total_it += P->h_state->iterations;
+    ++cycles;
+    if (P->h_state->done == 3) {
+      status = MFCG_BREAKDOWN;
+      break;
+    }
+  }
+  CK(cudaMemcpyAsync(x_user, P->x, n * sizeof(double), cudaMemcpyDeviceToDevice, P->exec));
+  CK(cudaStreamSynchronize(P->exec));
+  fill_info(P, info, status, total_it, stats, launches0, cycles);
   if (info) {
-    info->iterations = S.iterations;
-    info->converged = S.done == 1;
-    info->status = status;
-    info->main_kernel_launches = main_launches;
-    info->residual_sq_est = S.gamma_next;
-    info->rhs_norm_sq = S.sums[7];
-    info->main_kernel_ms = main_ms;
-    info->kernel_launches = P->launches - launches0;
+    info->converged = status == MFCG_OK;
+    info->residual_sq_est = rr;  // true residual of the last check
+    info->rhs_norm_sq = bb;
   }
   return status;
+}
+
+int solve_impl(mfcg_problem* P, const double* b, double* x_user, double rtol, int maxit, mfcg_solve_info* info) {
+  if (P->opt.precision == MFCG_PREC_FP32_INNER) {
+    if (rtol <= 0.0) return MFCG_INVALID_ARG;
+    return solve_defect_correction(P, b, x_user, rtol, maxit, info);
+  }
+  return solve_direct(P, b, x_user, rtol, maxit, info);
 }
 
 }  // namespace
@@ -320,11 +457,7 @@ int mfcg_destroy(mfcg_problem* P) {
   if (P->exec) cudaStreamSynchronize(P->exec);
   if (P->graph_fused) cudaGraphExecDestroy(P->graph_fused);
   if (P->graph_unfused) cudaGraphExecDestroy(P->graph_unfused);
-  double* bufs[] = {P->r[0], P->r[1], P->p[0], P->p[1], P->v[0], P->v[1], P->x, P->z, P->work,
-                    P->bdev, P->xdev, P->diag, P->diag_inv, P->shell, P->partial, P->geo};
-  for (double* b : bufs)
-    if (b) cudaFree(b);
-  if (P->state) cudaFree(P->state);
+  for (void* q : P->owned) cudaFree(q);
   if (P->h_state) cudaFreeHost(P->h_state);
   if (P->ev_in) cudaEventDestroy(P->ev_in);
   if (P->ev_out) cudaEventDestroy(P->ev_out);
@@ -348,6 +481,9 @@ int mfcg_setup(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, con
   if (opt) o = *opt;
   if (o.mode != MFCG_MODE_FUSED && o.mode != MFCG_MODE_UNFUSED) return MFCG_INVALID_ARG;
   if (o.graph_iterations < 0 || (o.graph_iterations & 1)) return MFCG_INVALID_ARG;
+  if (o.precision < MFCG_PREC_FP64 || o.precision > MFCG_PREC_FP32_INNER) return MFCG_INVALID_ARG;
+  if (o.precision == MFCG_PREC_FP32_INNER && o.mode != MFCG_MODE_FUSED) return MFCG_INVALID_ARG;
+  if (!(o.inner_rtol >= 0.0 && o.inner_rtol < 1.0)) return MFCG_INVALID_ARG;
   for (int d = 0; d < 3; ++d)
     if (o.tile[d] < 0) return MFCG_INVALID_ARG;
   const int64_t nn[3] = {(int64_t)degree * mesh->nx + 1, (int64_t)degree * mesh->ny + 1, (int64_t)degree * mesh->nz + 1};
@@ -367,6 +503,10 @@ int mfcg_setup(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, con
   P->geom = *geom;
   P->opt = o;
   P->geom_kind = geom->kind == MFCG_GEOM_AFFINE ? GEOM_AFFINE : GEOM_DEFORMED;
+  // the defect correction forms its outer residual with the native FP64
+  // operator: its true-residual floor is 2^5 lower than the double-float one
+  P->op_prec = o.precision == MFCG_PREC_DOUBLE_FLOAT ? PREC_DD : PREC_F64;
+  P->cg_prec = o.precision == MFCG_PREC_FP64 ? PREC_F64 : (o.precision == MFCG_PREC_DOUBLE_FLOAT ? PREC_DD : PREC_F32);
   P->graph_iters = o.graph_iterations ? o.graph_iterations : 16;
   if (cudaStreamCreateWithFlags(&P->exec, cudaStreamNonBlocking) != cudaSuccess) return fail(MFCG_CUDA_ERROR);
   if (cudaEventCreateWithFlags(&P->ev_in, cudaEventDisableTiming) != cudaSuccess) return fail(MFCG_CUDA_ERROR);
@@ -380,13 +520,14 @@ int mfcg_setup(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, con
     if (degree == 1 && T[d] < 2) T[d] = 2;
   }
   init_tile_geom(degree, N, T, g, P->fam);
-  const size_t smem = tile_smem_bytes(degree, P->geom_kind, g) + 8 * (kThreads / 32) * sizeof(double);
   int max_smem = 0;
   cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device);
-  if (smem > (size_t)max_smem) return fail(MFCG_INVALID_ARG);
-  if (prepare_tile(degree, P->geom_kind, tile_smem_bytes(degree, P->geom_kind, g)) != cudaSuccess)
-    return fail(MFCG_CUDA_ERROR);
-
+  const int precs[3] = {PREC_F64, P->op_prec, P->cg_prec};
+  for (int pr : precs) {
+    const size_t smem = tile_smem_bytes(degree, P->geom_kind, pr, g);
+    if (smem + 8 * (kThreads / 32) * sizeof(double) > (size_t)max_smem) return fail(MFCG_INVALID_ARG);
+    if (prepare_tile(degree, P->geom_kind, pr, smem) != cudaSuccess) return fail(MFCG_CUDA_ERROR);
+  }
   P->tail_nodes = P->fam[0] + P->fam[1] + P->fam[2];
   P->tail_ctas = (int)std::min<int64_t>(std::max<int64_t>((P->tail_nodes + kThreads - 1) / kThreads, 1), 152 * 8);
 
@@ -394,31 +535,59 @@ int mfcg_setup(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, con
   build_coeffs(degree, h, mesh->amplitude, geom->coefficient, P->c);
 
   const int64_t n = g.n_dofs;
-  for (int i = 0; i < 2 && st == MFCG_OK; ++i) {
-    if ((st = alloc(&P->r[i], n)) != MFCG_OK) break;
-    if ((st = alloc(&P->p[i], n)) != MFCG_OK) break;
-    st = alloc(&P->v[i], n);
+  const int64_t n8 = n * 8;
+  const int fused = o.mode == MFCG_MODE_FUSED;
+  if (fused) {
+    for (int i = 0; i < 2 && st == MFCG_OK; ++i) {
+      if ((st = alloc_bytes(P, &P->r[i], n8)) != MFCG_OK) break;
+      if ((st = alloc_bytes(P, &P->p[i], n8)) != MFCG_OK) break;
+      st = alloc_bytes(P, &P->v[i], n8);
+    }
+    if (st == MFCG_OK) st = alloc_bytes(P, &P->xs, n8);
+    if (st == MFCG_OK) st = alloc_bytes(P, &P->dinv_s, n8);
+    if (st == MFCG_OK && o.precision == MFCG_PREC_FP32_INNER) st = alloc_bytes(P, &P->x, n8);
+  } else {
+    if (st == MFCG_OK) st = alloc_bytes(P, &P->x, n8);
+    if (st == MFCG_OK) st = alloc_bytes(P, &P->z, n8);
+    if (st == MFCG_OK) st = alloc_bytes(P, &P->ur, n8);
+    if (st == MFCG_OK) st = alloc_bytes(P, &P->up, n8);
+    if (st == MFCG_OK) st = alloc_bytes(P, &P->uv, n8);
   }
-  if (st == MFCG_OK) st = alloc(&P->x, n);
-  if (st == MFCG_OK && o.mode == MFCG_MODE_UNFUSED) st = alloc(&P->z, n);
-  if (st == MFCG_OK) st = alloc(&P->work, n);
-  if (st == MFCG_OK) st = alloc(&P->diag, n);
-  if (st == MFCG_OK) st = alloc(&P->diag_inv, n);
-  if (st == MFCG_OK) st = alloc(&P->shell, g.n_tiles * g.face_stride);
+  if (st == MFCG_OK) st = alloc_bytes(P, &P->work, n8);
+  if (st == MFCG_OK) st = alloc_bytes(P, &P->diag, n8);
+  if (st == MFCG_OK) st = alloc_bytes(P, &P->diag_inv, n8);
+  if (st == MFCG_OK) st = alloc_bytes(P, &P->shell, g.n_tiles * g.face_stride * 8);
   const int64_t nparts = std::max<int64_t>(g.n_tiles + P->tail_ctas, 152 * 8);
-  if (st == MFCG_OK) st = alloc(&P->partial, nparts * 8);
-  if (st == MFCG_OK && P->geom_kind == GEOM_DEFORMED)
-    st = alloc(&P->geo, (int64_t)N[0] * N[1] * N[2] * 10 * (degree + 1) * (degree + 1) * (degree + 1));
+  if (st == MFCG_OK) st = alloc_bytes(P, &P->partial, nparts * 8 * 8);
+  const int64_t ngeo = (int64_t)N[0] * N[1] * N[2] * 10 * (degree + 1) * (degree + 1) * (degree + 1);
+  if (st == MFCG_OK && P->geom_kind == GEOM_DEFORMED) {
+    st = alloc_bytes(P, &P->geo, ngeo * 8);
+    if (st == MFCG_OK && P->op_prec != PREC_F64) st = alloc_bytes(P, &P->geo_op, ngeo * 8);
+    if (st == MFCG_OK && P->cg_prec != PREC_F64 && P->cg_prec != P->op_prec)
+      st = alloc_bytes(P, &P->geo_cg, ngeo * prec_bytes(P->cg_prec));
+  }
   if (st != MFCG_OK) return fail(st);
-  if (cudaMalloc(&P->state, sizeof(CGState)) != cudaSuccess) return fail(MFCG_OUT_OF_MEMORY);
+  if (P->geom_kind == GEOM_DEFORMED) {
+    if (!P->geo_op) P->geo_op = P->geo;
+    if (!P->geo_cg) P->geo_cg = P->cg_prec == PREC_F64 ? (void*)P->geo : P->geo_op;
+  }
+  if (alloc_bytes(P, &P->state, sizeof(CGState)) != MFCG_OK) return fail(MFCG_OUT_OF_MEMORY);
   if (cudaMallocHost(&P->h_state, 2 * sizeof(CGState)) != cudaSuccess) return fail(MFCG_OUT_OF_MEMORY);
   if (cudaMemsetAsync(P->state, 0, sizeof(CGState), P->exec) != cudaSuccess) return fail(MFCG_CUDA_ERROR);
   if (enter(P) != MFCG_OK) return fail(MFCG_CUDA_ERROR);
-  if (P->geom_kind == GEOM_DEFORMED && launch_geometry(g, P->c, P->geo, P->exec) != cudaSuccess)
-    return fail(MFCG_CUDA_ERROR);
-  // Jacobi preconditioner: exact diagonal and its inverse
+  if (P->geom_kind == GEOM_DEFORMED) {
+    if (launch_geometry(g, P->c, P->geo, P->exec) != cudaSuccess) return fail(MFCG_CUDA_ERROR);
+    if (P->geo_op != P->geo && launch_to_prec(P->op_prec, P->geo, P->geo_op, ngeo, P->exec) != cudaSuccess)
+      return fail(MFCG_CUDA_ERROR);
+    if (P->geo_cg != P->geo && P->geo_cg != P->geo_op &&
+        launch_to_prec(P->cg_prec, P->geo, P->geo_cg, ngeo, P->exec) != cudaSuccess)
+      return fail(MFCG_CUDA_ERROR);
+  }
+  // Jacobi preconditioner: exact diagonal and its inverse (FP64, converted for the fused CG)
   if ((st = run_pass(P, MODE_DIAG, nullptr, P->diag)) != MFCG_OK) return fail(st);
   if (launch_invert(P->diag, P->diag_inv, n, P->exec) != cudaSuccess) return fail(MFCG_CUDA_ERROR);
+  if (fused && launch_to_prec(P->cg_prec, P->diag_inv, P->dinv_s, n, P->exec) != cudaSuccess)
+    return fail(MFCG_CUDA_ERROR);
   if (cudaStreamSynchronize(P->exec) != cudaSuccess) return fail(MFCG_CUDA_ERROR);
   if (leave(P) != MFCG_OK) return fail(MFCG_CUDA_ERROR);
   *out = P;
@@ -470,8 +639,8 @@ int mfcg_cg_solve_host(mfcg_problem* P, const double* b_host, double* x_host, do
   const int64_t n = P->g.n_dofs;
   int st;
   if ((st = enter(P)) != MFCG_OK) return st;
-  if (!P->bdev && (st = alloc(&P->bdev, n)) != MFCG_OK) return st;
-  if (!P->xdev && (st = alloc(&P->xdev, n)) != MFCG_OK) return st;
+  if (!P->bdev && (st = alloc_bytes(P, &P->bdev, n * 8)) != MFCG_OK) return st;
+  if (!P->xdev && (st = alloc_bytes(P, &P->xdev, n * 8)) != MFCG_OK) return st;
   CK(cudaMemcpyAsync(P->bdev, b_host, n * sizeof(double), cudaMemcpyHostToDevice, P->exec));
   CK(cudaMemcpyAsync(P->xdev, x_host, n * sizeof(double), cudaMemcpyHostToDevice, P->exec));
   st = solve_impl(P, P->bdev, P->xdev, rtol, maxit, info);

@@ -7,6 +7,7 @@
 // fixed order, then the last CTA to finish (elected with an atomic ticket, no
 // waiting) adds the partials in CTA order and updates the scalars.
 #include "mfcg_internal.h"
+#include "precision.cuh"
 
 namespace mfcg {
 
@@ -154,18 +155,42 @@ __global__ void cg_init_kernel(CGState* st, const double* b, const double* r0, i
 
 // Finalisation of Algorithm 5 after the last iteration k: odd k: x += alpha_k p_k;
 // even k: x += alpha_k p_k + alpha_{k-1}/beta_{k-1} (p_k - M^{-1} r_k).
-__global__ void finalize_fused_kernel(const TileGeom g, const CGState* st, double* x, const double* p0,
-                                      const double* p1, const double* r0, const double* r1, const double* dinv) {
+template <int PREC>
+__global__ void finalize_fused_kernel(int64_t n, const CGState* st, void* xv, const void* p0v, const void* p1v,
+                                      const void* r0v, const void* r1v, const void* dinvv) {
+  using T = typename Num<PREC>::T;
   const int k = st->iterations;
   if (k < 1 || st->done == 3) return;
-  const double* p = (k & 1) ? p1 : p0;  // iteration k wrote buffer k & 1
-  const double* r = (k & 1) ? r1 : r0;
-  const double a = st->alpha_cur;
-  const double c = (k & 1) ? 0.0 : st->alpha_prev / st->beta_prev;
-  for (int64_t i = blockIdx.x * (int64_t)kVecThreads + threadIdx.x; i < g.n_dofs; i += (int64_t)gridDim.x * kVecThreads) {
-    const double pk = p[i];
-    x[i] += (k & 1) ? a * pk : fma(a, pk, c * (pk - dinv[i] * r[i]));
+  const T* p = static_cast<const T*>((k & 1) ? p1v : p0v);  // iteration k wrote buffer k & 1
+  const T* r = static_cast<const T*>((k & 1) ? r1v : r0v);
+  const T* dinv = static_cast<const T*>(dinvv);
+  T* x = static_cast<T*>(xv);
+  const T a = t_from_double<PREC>(st->alpha_cur);
+  const T c = t_from_double<PREC>((k & 1) ? 0.0 : st->alpha_prev / st->beta_prev);
+  for (int64_t i = blockIdx.x * (int64_t)kVecThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVecThreads) {
+    const T pk = p[i];
+    if (k & 1)
+      x[i] = t_axpy<PREC>(a, pk, x[i]);
+    else
+      x[i] = t_add<PREC>(x[i], t_axby<PREC>(a, pk, c, t_sub<PREC>(pk, t_mul<PREC>(dinv[i], r[i]))));
   }
+}
+
+// conversions between FP64 vectors and the storage type of a precision
+template <int PREC>
+__global__ void to_prec_kernel(const double* in, void* outv, int64_t n) {
+  using T = typename Num<PREC>::T;
+  T* out = static_cast<T*>(outv);
+  for (int64_t i = blockIdx.x * (int64_t)kVecThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVecThreads)
+    out[i] = t_from_double<PREC>(in[i]);
+}
+
+template <int PREC>
+__global__ void from_prec_kernel(const void* inv, double* out, int64_t n, int accumulate) {
+  using T = typename Num<PREC>::T;
+  const T* in = static_cast<const T*>(inv);
+  for (int64_t i = blockIdx.x * (int64_t)kVecThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVecThreads)
+    out[i] = accumulate ? out[i] + t_to_double<PREC>(in[i]) : t_to_double<PREC>(in[i]);
 }
 
 // ---------------------------- unfused Algorithm 1 ----------------------------------
@@ -275,9 +300,36 @@ cudaError_t launch_cg_init(CGState* st, const double* b, const double* r0, int64
   return cudaGetLastError();
 }
 
-cudaError_t launch_finalize_fused(const TileGeom& g, CGState* st, double* x, const double* p0, const double* p1,
-                                  const double* r0, const double* r1, const double* diag_inv, cudaStream_t s) {
-  finalize_fused_kernel<<<grid_for(g.n_dofs), kVecThreads, 0, s>>>(g, st, x, p0, p1, r0, r1, diag_inv);
+cudaError_t launch_finalize_fused(int prec, int64_t n, CGState* st, void* x, const void* p0, const void* p1,
+                                  const void* r0, const void* r1, const void* diag_inv, cudaStream_t s) {
+  if (prec == PREC_F64)
+    finalize_fused_kernel<PREC_F64><<<grid_for(n), kVecThreads, 0, s>>>(n, st, x, p0, p1, r0, r1, diag_inv);
+  else if (prec == PREC_DD)
+    finalize_fused_kernel<PREC_DD><<<grid_for(n), kVecThreads, 0, s>>>(n, st, x, p0, p1, r0, r1, diag_inv);
+  else
+    finalize_fused_kernel<PREC_F32><<<grid_for(n), kVecThreads, 0, s>>>(n, st, x, p0, p1, r0, r1, diag_inv);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_prec(int prec, const double* in, void* out, int64_t n, cudaStream_t s) {
+  if (prec == PREC_F64)
+    return cudaMemcpyAsync(out, in, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  if (prec == PREC_DD)
+    to_prec_kernel<PREC_DD><<<grid_for(n), kVecThreads, 0, s>>>(in, out, n);
+  else
+    to_prec_kernel<PREC_F32><<<grid_for(n), kVecThreads, 0, s>>>(in, out, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_from_prec(int prec, const void* in, double* out, int64_t n, int accumulate, cudaStream_t s) {
+  if (prec == PREC_F64 && !accumulate)
+    return cudaMemcpyAsync(out, in, n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  if (prec == PREC_F64)
+    from_prec_kernel<PREC_F64><<<grid_for(n), kVecThreads, 0, s>>>(in, out, n, accumulate);
+  else if (prec == PREC_DD)
+    from_prec_kernel<PREC_DD><<<grid_for(n), kVecThreads, 0, s>>>(in, out, n, accumulate);
+  else
+    from_prec_kernel<PREC_F32><<<grid_for(n), kVecThreads, 0, s>>>(in, out, n, accumulate);
   return cudaGetLastError();
 }
 

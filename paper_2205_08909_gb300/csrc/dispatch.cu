@@ -7,7 +7,7 @@ namespace mfcg {
 #define MFCG_DECLARE_DEG(P)                                                                         \
   cudaError_t launch_tile_deg##P(int mode, const TileArgs& a, const OperatorCoeffs& c, cudaStream_t s); \
   cudaError_t launch_tail_deg##P(int mode, const TileArgs& a, cudaStream_t s);                      \
-  cudaError_t prepare_tile_deg##P(int geom, size_t smem);
+  cudaError_t prepare_tile_deg##P(int geom, int prec, size_t smem);
 MFCG_DECLARE_DEG(1)
 MFCG_DECLARE_DEG(2)
 MFCG_DECLARE_DEG(3)
@@ -46,22 +46,22 @@ cudaError_t launch_tail(int degree, int mode, const TileArgs& a, cudaStream_t s)
   }
 }
 
-cudaError_t prepare_tile(int degree, int geom, size_t smem) {
+cudaError_t prepare_tile(int degree, int geom, int prec, size_t smem) {
   switch (degree) {
-    case 1: return prepare_tile_deg1(geom, smem);
-    case 2: return prepare_tile_deg2(geom, smem);
-    case 3: return prepare_tile_deg3(geom, smem);
-    case 4: return prepare_tile_deg4(geom, smem);
-    case 5: return prepare_tile_deg5(geom, smem);
-    case 6: return prepare_tile_deg6(geom, smem);
-    case 7: return prepare_tile_deg7(geom, smem);
-    case 8: return prepare_tile_deg8(geom, smem);
+    case 1: return prepare_tile_deg1(geom, prec, smem);
+    case 2: return prepare_tile_deg2(geom, prec, smem);
+    case 3: return prepare_tile_deg3(geom, prec, smem);
+    case 4: return prepare_tile_deg4(geom, prec, smem);
+    case 5: return prepare_tile_deg5(geom, prec, smem);
+    case 6: return prepare_tile_deg6(geom, prec, smem);
+    case 7: return prepare_tile_deg7(geom, prec, smem);
+    case 8: return prepare_tile_deg8(geom, prec, smem);
     default: return cudaErrorInvalidValue;
   }
 }
 
-size_t tile_smem_bytes(int degree, int geom, const TileGeom& g) {
-  return tile_smem_doubles(degree, geom, g) * sizeof(double);
+size_t tile_smem_bytes(int degree, int geom, int prec, const TileGeom& g) {
+  return tile_smem_elems(degree, geom, g) * prec_bytes(prec);
 }
 
 }  // namespace mfcg

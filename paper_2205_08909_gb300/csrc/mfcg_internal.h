@@ -190,18 +190,21 @@ enum TileMode { MODE_OPERATOR = 0, MODE_CG = 1, MODE_RHS = 2, MODE_DIAG = 3 };
 
 enum GeomKind { GEOM_AFFINE = 0, GEOM_DEFORMED = 1 };
 
+enum MatId { MAT_M = 0, MAT_K0 = 1, MAT_K1 = 2, MAT_K2 = 3, MAT_S = 4, MAT_DC = 5, NMAT = 6 };
+constexpr int kMat = (kMaxDegree + 1) * (kMaxDegree + 1);
+
 struct OperatorCoeffs {
-  // 1D matrices, row-major (P+1)x(P+1): for the affine Kronecker form the mass
-  // matrix M and the per-direction scaled stiffness matrices K_d; for the
-  // deformed form the interpolation S (Gauss points x GL nodes) and the Gauss
-  // collocation derivative Dc.
-  double M[(kMaxDegree + 1) * (kMaxDegree + 1)];
-  double K[3][(kMaxDegree + 1) * (kMaxDegree + 1)];
-  double S[(kMaxDegree + 1) * (kMaxDegree + 1)];
-  double Dc[(kMaxDegree + 1) * (kMaxDegree + 1)];
+  // 1D matrices, row-major (P+1)x(P+1): MAT_M the reference mass matrix,
+  // MAT_K0..2 the reference stiffness scaled per direction for box cells
+  // (h_y h_z / h_x, ...), MAT_S the interpolation from the Gauss-Lobatto
+  // nodes to the Gauss points, MAT_DC the Gauss collocation derivative.
+  double mat[NMAT][kMat];
   // products of 1D tables used by the exact diagonal: SS = S.*S, DS = D.*S,
-  // DD = D.*D with D[q][a] = L_a'(g_q) (Gauss points x GL nodes)
-  double T2[3][(kMaxDegree + 1) * (kMaxDegree + 1)];
+  // DD = D.*D with D[q][a] = L_a'(g_q)
+  double T2[3][kMat];
+  // the same matrices as float pairs (hi + lo) for the double-float and FP32 paths
+  float fh[NMAT][kMat];
+  float fl[NMAT][kMat];
   double w[kMaxDegree + 1];  // Gauss weights on [0,1]
   double g[kMaxDegree + 1];  // Gauss points on [0,1]
   double h[3];               // cell sizes
@@ -211,31 +214,33 @@ struct OperatorCoeffs {
 
 struct TileArgs {
   TileGeom g;
-  // operator mode: in0 = src, out0 = dst
-  // CG mode: in0 = r_old, in1 = v_old, in2 = p_old, diag_inv; out0 = r_new, out1 = v_new, out2 = p_new, x
-  const double* in0;
-  const double* in1;
-  const double* in2;
-  const double* diag_inv;
-  double* out0;
-  double* out1;
-  double* out2;
-  double* x;
-  double* shell;
+  // operator / right-hand side / diagonal modes: in0 = src (FP64), out0 = dst (FP64)
+  // CG mode (vectors in the storage type of the precision): in0 = r_old,
+  // in1 = v_old, in2 = p_old, diag_inv; out0 = r_new, out1 = v_new, out2 = p_new, x
+  const void* in0;
+  const void* in1;
+  const void* in2;
+  const void* diag_inv;
+  void* out0;
+  void* out1;
+  void* out2;
+  void* x;
+  void* shell;           // partial sums of shared-face nodes, arithmetic type of the precision
   double* partial;       // [n_tiles][8] (main) and [tail CTAs][8] (tail)
-  const double* geo;     // deformed: [cell][10][nq] = J^{-1} row-major, JxW*a
+  const void* geo;       // deformed: [cell][10][nq] = J^{-1} row-major, JxW*a (precision's type)
   CGState* state;
   int64_t tail_nodes;    // number of shared-face nodes handled by the tail kernel
   int64_t fam[3];        // tail enumeration: nodes in the x / y / z boundary-plane families
   int geom;              // GeomKind
+  int prec;              // Prec (precision.cuh)
   int tail_ctas;
 };
 
 // launchers (one set per degree, see tile_kernels.cuh)
 cudaError_t launch_tile(int degree, int mode, const TileArgs& a, const OperatorCoeffs& c, cudaStream_t s);
 cudaError_t launch_tail(int degree, int mode, const TileArgs& a, cudaStream_t s);
-size_t tile_smem_bytes(int degree, int geom, const TileGeom& g);
-cudaError_t prepare_tile(int degree, int geom, size_t smem);
+size_t tile_smem_bytes(int degree, int geom, int prec, const TileGeom& g);
+cudaError_t prepare_tile(int degree, int geom, int prec, size_t smem);
 
 // BLAS-1 / reduction / utility kernels (cg_kernels.cu)
 cudaError_t launch_fill(double* v, double value, int64_t n, cudaStream_t s);
@@ -261,7 +266,9 @@ cudaError_t launch_unfused_axpy(int which, const UnfusedArgs& a, cudaStream_t s)
 cudaError_t launch_cg_init(CGState* st, const double* b, const double* r0, int64_t n, double rtol, int maxit,
                            int fixed, double* partial, int n_ctas, cudaStream_t s);
 cudaError_t launch_residual(const double* b, const double* ax, double* r, int64_t n, cudaStream_t s);
-cudaError_t launch_finalize_fused(const TileGeom& g, CGState* st, double* x, const double* p0, const double* p1,
-                                  const double* r0, const double* r1, const double* diag_inv, cudaStream_t s);
+cudaError_t launch_finalize_fused(int prec, int64_t n, CGState* st, void* x, const void* p0, const void* p1,
+                                  const void* r0, const void* r1, const void* diag_inv, cudaStream_t s);
+cudaError_t launch_to_prec(int prec, const double* in, void* out, int64_t n, cudaStream_t s);
+cudaError_t launch_from_prec(int prec, const void* in, double* out, int64_t n, int accumulate, cudaStream_t s);
 
 }  // namespace mfcg

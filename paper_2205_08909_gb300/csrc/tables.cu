@@ -114,14 +114,21 @@ void build_coeffs(int p, const double h[3], double amplitude, int coef, Operator
   // affine box cell: x-stiffness scaled by h_y h_z / h_x, etc.; mass unscaled
   const double scale[3] = {h[1] * h[2] / h[0], h[0] * h[2] / h[1], h[0] * h[1] / h[2]};
   for (int i = 0; i < n1 * n1; ++i) {
-    c.M[i] = M[i];
-    for (int d = 0; d < 3; ++d) c.K[d][i] = scale[d] * K[i];
-    c.S[i] = S[i];
-    c.Dc[i] = Dc[i];
+    c.mat[MAT_M][i] = M[i];
+    for (int d = 0; d < 3; ++d) c.mat[MAT_K0 + d][i] = scale[d] * K[i];
+    c.mat[MAT_S][i] = S[i];
+    c.mat[MAT_DC][i] = Dc[i];
     c.T2[0][i] = S[i] * S[i];
     c.T2[1][i] = D[i] * S[i];
     c.T2[2][i] = D[i] * D[i];
   }
+  // float pairs: hi = nearest float, lo = nearest float of the remainder
+  for (int m = 0; m < NMAT; ++m)
+    for (int i = 0; i < n1 * n1; ++i) {
+      const float hi = (float)c.mat[m][i];
+      c.fh[m][i] = hi;
+      c.fl[m][i] = (float)(c.mat[m][i] - (double)hi);
+    }
   for (int q = 0; q < n1; ++q) {
     c.w[q] = w[q];
     c.g[q] = g[q];

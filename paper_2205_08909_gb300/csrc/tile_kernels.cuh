@@ -17,34 +17,95 @@
 // order, finishes their post operation and, in its last CTA, reduces all
 // per-CTA sums in a fixed order and computes alpha_k, the Eq. 8 residual
 // estimate, the convergence flag and beta_k (Eq. 7) on the device.
+//
+// Every kernel is a template on the degree P, the mode, the geometry kind and
+// the arithmetic precision (precision.cuh): FP64, double-float or FP32.
 #pragma once
 
 #include "mfcg_internal.h"
+#include "precision.cuh"
 
 namespace mfcg {
 
 // ------------------------------------------------------------------------------------
 // 1D contractions on a pencil of N1 = P+1 values held in registers
 // ------------------------------------------------------------------------------------
-template <int N1>
-__device__ __forceinline__ void matvec(const double* __restrict__ A, const double (&x)[N1], double (&y)[N1]) {
+template <int N1, bool TRANS>
+__device__ __forceinline__ int midx(int i, int j) {
+  return TRANS ? j * N1 + i : i * N1 + j;
+}
+
+// y = A x (or A^T x) with the 1D matrix m of the coefficient block
+template <int PREC, int N1, bool TRANS>
+__device__ __forceinline__ void mv(const OperatorCoeffs& c, int m, const typename Num<PREC>::T (&x)[N1],
+                                   typename Num<PREC>::T (&y)[N1]) {
 #pragma unroll
   for (int i = 0; i < N1; ++i) {
-    double s = 0.0;
+    if constexpr (PREC == PREC_DD) {
+      dd_acc a;
+      acc_set(a, dd{c.fh[m][midx<N1, TRANS>(i, 0)], c.fl[m][midx<N1, TRANS>(i, 0)]}, x[0]);
 #pragma unroll
-    for (int j = 0; j < N1; ++j) s = fma(A[i * N1 + j], x[j], s);
-    y[i] = s;
+      for (int j = 1; j < N1; ++j) acc_madd(a, dd{c.fh[m][midx<N1, TRANS>(i, j)], c.fl[m][midx<N1, TRANS>(i, j)]}, x[j]);
+      y[i] = acc_get(a);
+    } else if constexpr (PREC == PREC_F64) {
+      double s = 0.0;
+#pragma unroll
+      for (int j = 0; j < N1; ++j) s = fma(c.mat[m][midx<N1, TRANS>(i, j)], x[j], s);
+      y[i] = s;
+    } else {
+      float s = 0.f;
+#pragma unroll
+      for (int j = 0; j < N1; ++j) s = fmaf(c.fh[m][midx<N1, TRANS>(i, j)], x[j], s);
+      y[i] = s;
+    }
   }
 }
 
-template <int N1>
-__device__ __forceinline__ void matvec_t(const double* __restrict__ A, const double (&x)[N1], double (&y)[N1]) {
+// y = A x + B z
+template <int PREC, int N1>
+__device__ __forceinline__ void mv2(const OperatorCoeffs& c, int ma, const typename Num<PREC>::T (&x)[N1], int mb,
+                                    const typename Num<PREC>::T (&z)[N1], typename Num<PREC>::T (&y)[N1]) {
 #pragma unroll
   for (int i = 0; i < N1; ++i) {
-    double s = 0.0;
+    if constexpr (PREC == PREC_DD) {
+      dd_acc a;
+      acc_set(a, dd{c.fh[ma][i * N1], c.fl[ma][i * N1]}, x[0]);
 #pragma unroll
-    for (int j = 0; j < N1; ++j) s = fma(A[j * N1 + i], x[j], s);
-    y[i] = s;
+      for (int j = 1; j < N1; ++j) acc_madd(a, dd{c.fh[ma][i * N1 + j], c.fl[ma][i * N1 + j]}, x[j]);
+#pragma unroll
+      for (int j = 0; j < N1; ++j) acc_madd(a, dd{c.fh[mb][i * N1 + j], c.fl[mb][i * N1 + j]}, z[j]);
+      y[i] = acc_get(a);
+    } else if constexpr (PREC == PREC_F64) {
+      double s = 0.0;
+#pragma unroll
+      for (int j = 0; j < N1; ++j) s = fma(c.mat[ma][i * N1 + j], x[j], s);
+#pragma unroll
+      for (int j = 0; j < N1; ++j) s = fma(c.mat[mb][i * N1 + j], z[j], s);
+      y[i] = s;
+    } else {
+      float s = 0.f;
+#pragma unroll
+      for (int j = 0; j < N1; ++j) s = fmaf(c.fh[ma][i * N1 + j], x[j], s);
+#pragma unroll
+      for (int j = 0; j < N1; ++j) s = fmaf(c.fh[mb][i * N1 + j], z[j], s);
+      y[i] = s;
+    }
+  }
+}
+
+// a0 b0 + a1 b1 + a2 b2
+template <int PREC>
+__device__ __forceinline__ typename Num<PREC>::T dot3(typename Num<PREC>::T a0, typename Num<PREC>::T b0,
+                                                     typename Num<PREC>::T a1, typename Num<PREC>::T b1,
+                                                     typename Num<PREC>::T a2, typename Num<PREC>::T b2) {
+  if constexpr (PREC == PREC_DD) {
+    dd_acc a;
+    acc_set(a, a0, b0);
+    acc_madd(a, a1, b1);
+    acc_madd(a, a2, b2);
+    return acc_get(a);
+  } else {
+    return fma(a0, b0, fma(a1, b1, a2 * b2));
   }
 }
 
@@ -60,18 +121,20 @@ __device__ __forceinline__ int pencil_idx(int dir, int e1, int e2, int s) {
   return dir == 0 ? cidx<N1>(s, e1, e2) : (dir == 1 ? cidx<N1>(e1, s, e2) : cidx<N1>(e1, e2, s));
 }
 
-// In-place application of a 1D matrix (or its transpose) along `dir` to the
-// cell arrays arr + ci*stride, ci < nc.  Ends with a barrier.
-template <int P, bool TRANS>
-__device__ __forceinline__ void sweep_inplace(double* arr, int stride, int nc, int dir, const double* __restrict__ A) {
+// In-place application of the 1D matrix m (or its transpose) along `dir` to
+// the cell arrays arr + ci*stride, ci < nc.  Ends with a barrier.
+template <int PREC, int P, bool TRANS>
+__device__ __forceinline__ void sweep_inplace(typename Num<PREC>::T* arr, int stride, int nc, int dir,
+                                              const OperatorCoeffs& c, int m) {
+  using T = typename Num<PREC>::T;
   constexpr int N1 = P + 1, N2 = N1 * N1;
   for (int t = threadIdx.x; t < nc * N2; t += kThreads) {
     const int ci = t / N2, e = t - ci * N2, e1 = e % N1, e2 = e / N1;
-    double* a = arr + ci * stride;
-    double x[N1], y[N1];
+    T* a = arr + ci * stride;
+    T x[N1], y[N1];
 #pragma unroll
     for (int s = 0; s < N1; ++s) x[s] = a[pencil_idx<N1>(dir, e1, e2, s)];
-    if (TRANS) matvec_t<N1>(A, x, y); else matvec<N1>(A, x, y);
+    mv<PREC, N1, TRANS>(c, m, x, y);
 #pragma unroll
     for (int s = 0; s < N1; ++s) a[pencil_idx<N1>(dir, e1, e2, s)] = y[s];
   }
@@ -79,22 +142,44 @@ __device__ __forceinline__ void sweep_inplace(double* arr, int stride, int nc, i
 }
 
 // out (+)= A^(T) in along `dir`, separate arrays.  Ends with a barrier.
-template <int P, bool TRANS, bool ACCUM>
-__device__ __forceinline__ void sweep_copy(const double* in, double* out, int stride, int nc, int dir,
-                                           const double* __restrict__ A) {
+template <int PREC, int P, bool TRANS, bool ACCUM>
+__device__ __forceinline__ void sweep_copy(const typename Num<PREC>::T* in, typename Num<PREC>::T* out, int stride,
+                                           int nc, int dir, const OperatorCoeffs& c, int m) {
+  using T = typename Num<PREC>::T;
   constexpr int N1 = P + 1, N2 = N1 * N1;
   for (int t = threadIdx.x; t < nc * N2; t += kThreads) {
     const int ci = t / N2, e = t - ci * N2, e1 = e % N1, e2 = e / N1;
-    const double* a = in + ci * stride;
-    double* o = out + ci * stride;
-    double x[N1], y[N1];
+    const T* a = in + ci * stride;
+    T* o = out + ci * stride;
+    T x[N1], y[N1];
 #pragma unroll
     for (int s = 0; s < N1; ++s) x[s] = a[pencil_idx<N1>(dir, e1, e2, s)];
-    if (TRANS) matvec_t<N1>(A, x, y); else matvec<N1>(A, x, y);
+    mv<PREC, N1, TRANS>(c, m, x, y);
 #pragma unroll
     for (int s = 0; s < N1; ++s) {
       const int id = pencil_idx<N1>(dir, e1, e2, s);
-      o[id] = ACCUM ? o[id] + y[s] : y[s];
+      o[id] = ACCUM ? t_add<PREC>(o[id], y[s]) : y[s];
+    }
+  }
+  __syncthreads();
+}
+
+// FP64 sweep with the transpose of a raw 1D table (exact diagonal)
+template <int P>
+__device__ __forceinline__ void sweep_inplace_table_t(double* arr, int stride, int nc, int dir, const double* A) {
+  constexpr int N1 = P + 1, N2 = N1 * N1;
+  for (int t = threadIdx.x; t < nc * N2; t += kThreads) {
+    const int ci = t / N2, e = t - ci * N2, e1 = e % N1, e2 = e / N1;
+    double* a = arr + ci * stride;
+    double x[N1];
+#pragma unroll
+    for (int s = 0; s < N1; ++s) x[s] = a[pencil_idx<N1>(dir, e1, e2, s)];
+#pragma unroll
+    for (int i = 0; i < N1; ++i) {
+      double s = 0.0;
+#pragma unroll
+      for (int j = 0; j < N1; ++j) s = fma(A[j * N1 + i], x[j], s);
+      a[pencil_idx<N1>(dir, e1, e2, i)] = s;
     }
   }
   __syncthreads();
@@ -119,24 +204,25 @@ struct ColorCells {
 // Affine box cells: the cell matrix of Eq. 5 is the Kronecker sum
 // K_x (x) M (x) M + M (x) K_y (x) M + M (x) M (x) K_z (K_d scaled by the cell
 // sizes), applied in seven 1D sweeps with shared intermediates.
-template <int P>
-__device__ void cell_op_affine(const OperatorCoeffs& c, const double* U, double* V, double* S, int bx, int by,
-                               const ColorCells& cc) {
+template <int PREC, int P>
+__device__ void cell_op_affine(const OperatorCoeffs& c, const typename Num<PREC>::T* U, typename Num<PREC>::T* V,
+                               typename Num<PREC>::T* S, int bx, int by, const ColorCells& cc) {
+  using T = typename Num<PREC>::T;
   constexpr int N1 = P + 1, N2 = N1 * N1, N3 = N2 * N1;
   const int nc = cc.count();
-  // z direction: s1 = M_z u, s2 = K_z u
+  // z direction: s1 = M u, s2 = K_z u
   for (int t = threadIdx.x; t < nc * N2; t += kThreads) {
     const int ci = t / N2, e = t - ci * N2, a = e % N1, b = e / N1;
     int cx, cy, cz;
     cc.cell(ci, cx, cy, cz);
-    const double* u0 = U + (P * cx + a) + bx * ((P * cy + b) + by * (P * cz));
-    double x[N1], y1[N1], y2[N1];
+    const T* u0 = U + (P * cx + a) + bx * ((P * cy + b) + by * (P * cz));
+    T x[N1], y1[N1], y2[N1];
 #pragma unroll
     for (int s = 0; s < N1; ++s) x[s] = u0[s * bx * by];
-    matvec<N1>(c.M, x, y1);
-    matvec<N1>(c.K[2], x, y2);
-    double* s1 = S + ci * 2 * N3;
-    double* s2 = s1 + N3;
+    mv<PREC, N1, false>(c, MAT_M, x, y1);
+    mv<PREC, N1, false>(c, MAT_K2, x, y2);
+    T* s1 = S + ci * 2 * N3;
+    T* s2 = s1 + N3;
 #pragma unroll
     for (int s = 0; s < N1; ++s) {
       s1[cidx<N1>(a, b, s)] = y1[s];
@@ -144,50 +230,43 @@ __device__ void cell_op_affine(const OperatorCoeffs& c, const double* U, double*
     }
   }
   __syncthreads();
-  // y direction: s1 <- M_y s1, s2 <- K_y s1 + M_y s2
+  // y direction: s1 <- M s1, s2 <- K_y s1 + M s2
   for (int t = threadIdx.x; t < nc * N2; t += kThreads) {
     const int ci = t / N2, e = t - ci * N2, a = e % N1, cz = e / N1;
-    double* s1 = S + ci * 2 * N3;
-    double* s2 = s1 + N3;
-    double m[N1], k[N1], y1[N1], y2[N1], y3[N1];
+    T* s1 = S + ci * 2 * N3;
+    T* s2 = s1 + N3;
+    T m[N1], k[N1], y1[N1], y2[N1];
 #pragma unroll
     for (int s = 0; s < N1; ++s) {
       m[s] = s1[cidx<N1>(a, s, cz)];
       k[s] = s2[cidx<N1>(a, s, cz)];
     }
-    matvec<N1>(c.M, m, y1);
-    matvec<N1>(c.K[1], m, y2);
-    matvec<N1>(c.M, k, y3);
+    mv<PREC, N1, false>(c, MAT_M, m, y1);
+    mv2<PREC, N1>(c, MAT_K1, m, MAT_M, k, y2);
 #pragma unroll
     for (int s = 0; s < N1; ++s) {
       s1[cidx<N1>(a, s, cz)] = y1[s];
-      s2[cidx<N1>(a, s, cz)] = y2[s] + y3[s];
+      s2[cidx<N1>(a, s, cz)] = y2[s];
     }
   }
   __syncthreads();
-  // x direction: out = K_x s1 + M_x s2, added into V
+  // x direction: out = K_x s1 + M s2, added into V
   for (int t = threadIdx.x; t < nc * N2; t += kThreads) {
     const int ci = t / N2, e = t - ci * N2, b = e % N1, cz = e / N1;
     int cx, cy, czz;
     cc.cell(ci, cx, cy, czz);
-    const double* s1 = S + ci * 2 * N3;
-    const double* s2 = s1 + N3;
-    double m[N1], k[N1];
+    const T* s1 = S + ci * 2 * N3;
+    const T* s2 = s1 + N3;
+    T m[N1], k[N1], y[N1];
 #pragma unroll
     for (int s = 0; s < N1; ++s) {
       m[s] = s1[cidx<N1>(s, b, cz)];
       k[s] = s2[cidx<N1>(s, b, cz)];
     }
-    double* v0 = V + (P * cx) + bx * ((P * cy + b) + by * (P * czz + cz));
+    mv2<PREC, N1>(c, MAT_K0, m, MAT_M, k, y);
+    T* v0 = V + (P * cx) + bx * ((P * cy + b) + by * (P * czz + cz));
 #pragma unroll
-    for (int i = 0; i < N1; ++i) {
-      double s = 0.0;
-#pragma unroll
-      for (int j = 0; j < N1; ++j) s = fma(c.K[0][i * N1 + j], m[j], s);
-#pragma unroll
-      for (int j = 0; j < N1; ++j) s = fma(c.M[i * N1 + j], k[j], s);
-      v0[i] += s;
-    }
+    for (int i = 0; i < N1; ++i) v0[i] = t_add<PREC>(v0[i], y[i]);
   }
   __syncthreads();
 }
@@ -196,10 +275,12 @@ __device__ void cell_op_affine(const OperatorCoeffs& c, const double* U, double*
 // Gauss points by three sweeps with the interpolation matrix S, reference
 // gradients by three sweeps with the Gauss collocation derivative Dc, the
 // per-point metric J^{-1} (JxW a) J^{-T}, and the transposed sweeps back.
-template <int P>
-__device__ void cell_op_deformed(const OperatorCoeffs& c, const double* U, double* V, double* S, int bx, int by,
-                                 const ColorCells& cc, const double* __restrict__ geo, int64_t cell_base_x,
-                                 int64_t cell_base_y, int64_t cell_base_z, const TileGeom& g) {
+template <int PREC, int P>
+__device__ void cell_op_deformed(const OperatorCoeffs& c, const typename Num<PREC>::T* U, typename Num<PREC>::T* V,
+                                 typename Num<PREC>::T* S, int bx, int by, const ColorCells& cc,
+                                 const typename Num<PREC>::T* __restrict__ geo, int cell_base_x, int cell_base_y,
+                                 int cell_base_z, const TileGeom& g) {
+  using T = typename Num<PREC>::T;
   constexpr int N1 = P + 1, N2 = N1 * N1, N3 = N2 * N1;
   const int nc = cc.count();
   const int stride = 4 * N3;
@@ -211,20 +292,20 @@ __device__ void cell_op_deformed(const OperatorCoeffs& c, const double* U, doubl
     S[ci * stride + e] = U[(P * cx + a) + bx * ((P * cy + b) + by * (P * czz + cz))];
   }
   __syncthreads();
-  sweep_inplace<P, false>(S, stride, nc, 0, c.S);
-  sweep_inplace<P, false>(S, stride, nc, 1, c.S);
-  sweep_inplace<P, false>(S, stride, nc, 2, c.S);
+  sweep_inplace<PREC, P, false>(S, stride, nc, 0, c, MAT_S);
+  sweep_inplace<PREC, P, false>(S, stride, nc, 1, c, MAT_S);
+  sweep_inplace<PREC, P, false>(S, stride, nc, 2, c, MAT_S);
   // reference gradients at the Gauss points (single pass over all three directions)
   for (int t = threadIdx.x; t < nc * N2 * 3; t += kThreads) {
     const int dir = t / (nc * N2);
     const int tt = t - dir * nc * N2;
     const int ci = tt / N2, e = tt - ci * N2, e1 = e % N1, e2 = e / N1;
-    const double* a = S + ci * stride;
-    double* o = S + ci * stride + (1 + dir) * N3;
-    double x[N1], y[N1];
+    const T* a = S + ci * stride;
+    T* o = S + ci * stride + (1 + dir) * N3;
+    T x[N1], y[N1];
 #pragma unroll
     for (int s = 0; s < N1; ++s) x[s] = a[pencil_idx<N1>(dir, e1, e2, s)];
-    matvec<N1>(c.Dc, x, y);
+    mv<PREC, N1, false>(c, MAT_DC, x, y);
 #pragma unroll
     for (int s = 0; s < N1; ++s) o[pencil_idx<N1>(dir, e1, e2, s)] = y[s];
   }
@@ -235,47 +316,47 @@ __device__ void cell_op_deformed(const OperatorCoeffs& c, const double* U, doubl
     int cx, cy, cz;
     cc.cell(ci, cx, cy, cz);
     const int64_t cell = (cell_base_x + cx) + (int64_t)g.N[0] * ((cell_base_y + cy) + (int64_t)g.N[1] * (cell_base_z + cz));
-    const double* gq = geo + cell * 10 * N3 + q;
-    double Ji[9];
+    const T* gq = geo + cell * 10 * N3 + q;
+    T Ji[9];
 #pragma unroll
-    for (int m = 0; m < 9; ++m) Ji[m] = __ldg(gq + m * N3);
-    const double jxw = __ldg(gq + 9 * N3);
-    double* s = S + ci * stride;
-    const double g0 = s[N3 + q], g1 = s[2 * N3 + q], g2 = s[3 * N3 + q];
+    for (int m = 0; m < 9; ++m) Ji[m] = gq[m * N3];
+    const T jxw = gq[9 * N3];
+    T* s = S + ci * stride;
+    const T g0 = s[N3 + q], g1 = s[2 * N3 + q], g2 = s[3 * N3 + q];
     // physical gradient (J^{-T} g)_m = sum_n Ji[n][m] g_n, scaled by JxW a
-    const double f0 = jxw * fma(Ji[0], g0, fma(Ji[3], g1, Ji[6] * g2));
-    const double f1 = jxw * fma(Ji[1], g0, fma(Ji[4], g1, Ji[7] * g2));
-    const double f2 = jxw * fma(Ji[2], g0, fma(Ji[5], g1, Ji[8] * g2));
-    s[N3 + q] = fma(Ji[0], f0, fma(Ji[1], f1, Ji[2] * f2));
-    s[2 * N3 + q] = fma(Ji[3], f0, fma(Ji[4], f1, Ji[5] * f2));
-    s[3 * N3 + q] = fma(Ji[6], f0, fma(Ji[7], f1, Ji[8] * f2));
+    const T f0 = t_mul<PREC>(jxw, dot3<PREC>(Ji[0], g0, Ji[3], g1, Ji[6], g2));
+    const T f1 = t_mul<PREC>(jxw, dot3<PREC>(Ji[1], g0, Ji[4], g1, Ji[7], g2));
+    const T f2 = t_mul<PREC>(jxw, dot3<PREC>(Ji[2], g0, Ji[5], g1, Ji[8], g2));
+    s[N3 + q] = dot3<PREC>(Ji[0], f0, Ji[1], f1, Ji[2], f2);
+    s[2 * N3 + q] = dot3<PREC>(Ji[3], f0, Ji[4], f1, Ji[5], f2);
+    s[3 * N3 + q] = dot3<PREC>(Ji[6], f0, Ji[7], f1, Ji[8], f2);
   }
   __syncthreads();
   // transposed derivative sweeps, summed into s0
-  sweep_copy<P, true, false>(S + N3, S, stride, nc, 0, c.Dc);
-  sweep_copy<P, true, true>(S + 2 * N3, S, stride, nc, 1, c.Dc);
-  sweep_copy<P, true, true>(S + 3 * N3, S, stride, nc, 2, c.Dc);
-  sweep_inplace<P, true>(S, stride, nc, 0, c.S);
-  sweep_inplace<P, true>(S, stride, nc, 1, c.S);
+  sweep_copy<PREC, P, true, false>(S + N3, S, stride, nc, 0, c, MAT_DC);
+  sweep_copy<PREC, P, true, true>(S + 2 * N3, S, stride, nc, 1, c, MAT_DC);
+  sweep_copy<PREC, P, true, true>(S + 3 * N3, S, stride, nc, 2, c, MAT_DC);
+  sweep_inplace<PREC, P, true>(S, stride, nc, 0, c, MAT_S);
+  sweep_inplace<PREC, P, true>(S, stride, nc, 1, c, MAT_S);
   // last sweep writes straight into the node brick
   for (int t = threadIdx.x; t < nc * N2; t += kThreads) {
     const int ci = t / N2, e = t - ci * N2, a = e % N1, b = e / N1;
     int cx, cy, cz;
     cc.cell(ci, cx, cy, cz);
-    const double* s0 = S + ci * stride;
-    double x[N1], y[N1];
+    const T* s0 = S + ci * stride;
+    T x[N1], y[N1];
 #pragma unroll
     for (int s = 0; s < N1; ++s) x[s] = s0[cidx<N1>(a, b, s)];
-    matvec_t<N1>(c.S, x, y);
-    double* v0 = V + (P * cx + a) + bx * ((P * cy + b) + by * (P * cz));
+    mv<PREC, N1, true>(c, MAT_S, x, y);
+    T* v0 = V + (P * cx + a) + bx * ((P * cy + b) + by * (P * cz));
 #pragma unroll
-    for (int s = 0; s < N1; ++s) v0[s * bx * by] += y[s];
+    for (int s = 0; s < N1; ++s) v0[s * bx * by] = t_add<PREC>(v0[s * bx * by], y[s]);
   }
   __syncthreads();
 }
 
 // Right-hand side b_e = sum_q w_q det J_q f(x_q) phi(xhat_q): forcing at the
-// Gauss points, then three transposed interpolation sweeps.
+// Gauss points, then three transposed interpolation sweeps (FP64).
 __device__ inline double manufactured_forcing(double x, double y, double z, int coef) {
   const double pi = 3.14159265358979323846;
   const double u = sin(pi * x) * sin(pi * y) * sin(pi * z);
@@ -307,9 +388,9 @@ __device__ void cell_rhs(const OperatorCoeffs& c, double* V, double* S, int bx, 
     S[ci * stride + q] = c.w[qa] * c.w[qb] * c.w[qc] * detJ * f;
   }
   __syncthreads();
-  sweep_inplace<P, true>(S, stride, nc, 0, c.S);
-  sweep_inplace<P, true>(S, stride, nc, 1, c.S);
-  sweep_inplace<P, true>(S, stride, nc, 2, c.S);
+  sweep_inplace<PREC_F64, P, true>(S, stride, nc, 0, c, MAT_S);
+  sweep_inplace<PREC_F64, P, true>(S, stride, nc, 1, c, MAT_S);
+  sweep_inplace<PREC_F64, P, true>(S, stride, nc, 2, c, MAT_S);
   for (int t = threadIdx.x; t < nc * N3; t += kThreads) {
     const int ci = t / N3, e = t - ci * N3, a = e % N1, b = (e / N1) % N1, cz = e / N2;
     int cx, cy, czz;
@@ -319,7 +400,7 @@ __device__ void cell_rhs(const OperatorCoeffs& c, double* V, double* S, int bx, 
   __syncthreads();
 }
 
-// Exact diagonal of the cell matrix of Eq. 5 with the same Gauss rule:
+// Exact diagonal of the cell matrix of Eq. 5 with the same Gauss rule (FP64):
 // diag_e(i) = sum_q sum_{d,d'} G_d(q,i) C_q^{dd'} G_{d'}(q,i), C_q = JxW a J^{-1} J^{-T},
 // where G_d(q,i) is a product of 1D tables; each (d,d') term is a 3D
 // contraction of C^{dd'} with the element-wise products SS, DS or DD of the 1D
@@ -360,7 +441,7 @@ __device__ void cell_diag(const OperatorCoeffs& c, double* V, double* S, int bx,
 #pragma unroll 1
     for (int dim = 0; dim < 3; ++dim) {
       const int nd = (dim == d0) + (dim == d1);
-      sweep_inplace<P, true>(S, stride, nc, dim, c.T2[nd]);
+      sweep_inplace_table_t<P>(S, stride, nc, dim, c.T2[nd]);
     }
     for (int t = threadIdx.x; t < nc * N3; t += kThreads) {
       const int ci = t / N3, e = t - ci * N3;
@@ -405,39 +486,43 @@ __device__ __forceinline__ void block_reduce(double (&v)[NV], double* red) {
 }
 
 // accumulate the seven sums of Algorithm 5 for one finalised node
-__device__ __forceinline__ void post_sums(double (&sm)[7], double r, double p, double v, double dinv) {
-  const double z = dinv * r;      // M^{-1} r
-  const double zv = dinv * v;     // M^{-1} v
-  sm[0] = fma(r, r, sm[0]);       // gamma = r.r
-  sm[1] = fma(p, v, sm[1]);       // a = p.v
-  sm[2] = fma(r, v, sm[2]);       // b = r.v
-  sm[3] = fma(v, v, sm[3]);       // c = v.v
-  sm[4] = fma(r, z, sm[4]);       // d = r.M^-1 r
-  sm[5] = fma(r, zv, sm[5]);      // e = r.M^-1 v
-  sm[6] = fma(v, zv, sm[6]);      // f = v.M^-1 v
+template <int PREC>
+__device__ __forceinline__ void post_sums(DotAcc<PREC> (&sm)[7], typename Num<PREC>::T r, typename Num<PREC>::T p,
+                                          typename Num<PREC>::T v, typename Num<PREC>::T dinv) {
+  using T = typename Num<PREC>::T;
+  const T z = t_mul<PREC>(dinv, r);   // M^{-1} r
+  const T zv = t_mul<PREC>(dinv, v);  // M^{-1} v
+  sm[0].madd(r, r);                    // gamma = r.r
+  sm[1].madd(p, v);                    // a = p.v
+  sm[2].madd(r, v);                    // b = r.v
+  sm[3].madd(v, v);                    // c = v.v
+  sm[4].madd(r, z);                    // d = r.M^-1 r
+  sm[5].madd(r, zv);                   // e = r.M^-1 v
+  sm[6].madd(v, zv);                   // f = v.M^-1 v
 }
 
 // ------------------------------------------------------------------------------------
 // The tile kernel
 // ------------------------------------------------------------------------------------
-template <int P, int MODE, int GEOM>
+template <int P, int MODE, int GEOM, int PREC>
 __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a, const OperatorCoeffs c) {
-  extern __shared__ double smem[];
+  using T = typename Num<PREC>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[8 * (kThreads / 32)];
   constexpr int N1 = P + 1, N3 = N1 * N1 * N1;
   const TileGeom& g = a.g;
 
-  double alpha_prev = 0.0, beta_prev = 0.0, xa = 0.0, xr = 0.0;
+  T alpha_m = t_zero<PREC>(), beta_t = t_zero<PREC>(), xa = t_zero<PREC>(), xr = t_zero<PREC>();
   bool xupd = false;
-  if (MODE == MODE_CG) {
+  if constexpr (MODE == MODE_CG) {
     const CGState* st = a.state;
     if (st->done) return;
-    alpha_prev = st->alpha_prev;
-    beta_prev = st->beta_prev;
+    alpha_m = t_from_double<PREC>(-st->alpha_prev);
+    beta_t = t_from_double<PREC>(st->beta_prev);
     const int k = st->k;
     xupd = (k > 1) && (k & 1);
-    xa = alpha_prev;
-    xr = xupd ? st->alpha_prev2 / st->beta_prev2 : 0.0;
+    xa = t_from_double<PREC>(st->alpha_prev);
+    xr = t_from_double<PREC>(xupd ? st->alpha_prev2 / st->beta_prev2 : 0.0);
   }
 
   const int64_t tile = blockIdx.x;
@@ -453,32 +538,37 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a, const 
   const int pTx = P * g.T[0], pTy = P * g.T[1], pTz = P * g.T[2];
   const bool lastx = tx == g.nt[0] - 1, lasty = ty == g.nt[1] - 1, lastz = tz == g.nt[2] - 1;
 
-  double* U = smem;
-  double* V = smem + Bmax;
-  double* S = smem + 2 * Bmax;
+  T* U = reinterpret_cast<T*>(smem_raw);
+  T* V = U + Bmax;
+  T* S = U + 2 * Bmax;
 
   // ---------------- phase 1: pre ----------------
   for (int n = threadIdx.x; n < bsize; n += kThreads) {
     const int li = n % bx, lj = (n / bx) % by, lk = n / (bx * by);
     const int i = gi0 + li, j = gj0 + lj, k = gk0 + lk;
-    if (MODE == MODE_OPERATOR) {
+    if constexpr (MODE == MODE_OPERATOR) {
       const bool dir = is_dirichlet(g, i, j, k);
-      U[n] = dir ? 0.0 : a.in0[node_index(g, i, j, k)];
-    } else if (MODE == MODE_CG) {
+      U[n] = dir ? t_zero<PREC>() : t_from_double<PREC>(static_cast<const double*>(a.in0)[node_index(g, i, j, k)]);
+    } else if constexpr (MODE == MODE_CG) {
       const bool dir = is_dirichlet(g, i, j, k);
       const int64_t gi = node_index(g, i, j, k);
-      const double r_o = a.in0[gi], v_o = a.in1[gi], p_o = a.in2[gi], dinv = a.diag_inv[gi];
-      const double rk = fma(-alpha_prev, v_o, r_o);
-      const double pk = fma(beta_prev, p_o, dinv * rk);
-      U[n] = dir ? 0.0 : pk;
+      const T r_o = static_cast<const T*>(a.in0)[gi], v_o = static_cast<const T*>(a.in1)[gi];
+      const T p_o = static_cast<const T*>(a.in2)[gi], dinv = static_cast<const T*>(a.diag_inv)[gi];
+      const T rk = t_axpy<PREC>(alpha_m, v_o, r_o);       // r_{k-1} - alpha_{k-1} v_{k-1}
+      const T pk = t_axby<PREC>(dinv, rk, beta_t, p_o);   // M^{-1} r_k + beta_{k-1} p_{k-1}
+      U[n] = dir ? t_zero<PREC>() : pk;
       const bool owned = (li < pTx || lastx) && (lj < pTy || lasty) && (lk < pTz || lastz);
       if (owned) {
-        a.out0[gi] = rk;
-        a.out2[gi] = pk;
-        if (xupd) a.x[gi] += fma(xa, p_o, xr * (p_o - dinv * r_o));
+        static_cast<T*>(a.out0)[gi] = rk;
+        static_cast<T*>(a.out2)[gi] = pk;
+        if (xupd) {
+          T* x = static_cast<T*>(a.x);
+          const T dp = t_sub<PREC>(p_o, t_mul<PREC>(dinv, r_o));  // p_{k-1} - M^{-1} r_{k-1}
+          x[gi] = t_add<PREC>(x[gi], t_axby<PREC>(xa, p_o, xr, dp));
+        }
       }
     }
-    V[n] = 0.0;
+    V[n] = t_zero<PREC>();
   }
   __syncthreads();
 
@@ -492,19 +582,21 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a, const 
     cc.my = (ncy - cc.py + 1) / 2;
     cc.mz = (ncz - cc.pz + 1) / 2;
     if (cc.count() == 0) continue;
-    if (MODE == MODE_RHS) {
+    if constexpr (MODE == MODE_RHS) {
       cell_rhs<P>(c, V, S, bx, by, cc, cx0, cy0, cz0, (GEOM == GEOM_AFFINE ? 2 : 4) * N3);
-    } else if (MODE == MODE_DIAG) {
-      cell_diag<P, GEOM>(c, V, S, bx, by, cc, a.geo, cx0, cy0, cz0, g, (GEOM == GEOM_AFFINE ? 2 : 4) * N3);
-    } else if (GEOM == GEOM_AFFINE) {
-      cell_op_affine<P>(c, U, V, S, bx, by, cc);
+    } else if constexpr (MODE == MODE_DIAG) {
+      cell_diag<P, GEOM>(c, V, S, bx, by, cc, static_cast<const double*>(a.geo), cx0, cy0, cz0, g,
+                         (GEOM == GEOM_AFFINE ? 2 : 4) * N3);
+    } else if constexpr (GEOM == GEOM_AFFINE) {
+      cell_op_affine<PREC, P>(c, U, V, S, bx, by, cc);
     } else {
-      cell_op_deformed<P>(c, U, V, S, bx, by, cc, a.geo, cx0, cy0, cz0, g);
+      cell_op_deformed<PREC, P>(c, U, V, S, bx, by, cc, static_cast<const T*>(a.geo), cx0, cy0, cz0, g);
     }
   }
 
   // ---------------- phase 3: post ----------------
-  double sm[7] = {0, 0, 0, 0, 0, 0, 0};
+  DotAcc<PREC> sm[7];
+  T* shell = static_cast<T*>(a.shell);
   for (int n = threadIdx.x; n < bsize; n += kThreads) {
     const int li = n % bx, lj = (n / bx) % by, lk = n / (bx * by);
     const int i = gi0 + li, j = gj0 + lj, k = gk0 + lk;
@@ -512,31 +604,35 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a, const 
     const bool shared = !dir && ((li == 0 && tx > 0) || (li == bx - 1 && !lastx) || (lj == 0 && ty > 0) ||
                                  (lj == by - 1 && !lasty) || (lk == 0 && tz > 0) || (lk == bz - 1 && !lastz));
     if (shared) {
-      a.shell[tile * g.face_stride + shell_slot(g, li, lj, lk, bx, by, bz)] = V[n];
+      shell[tile * g.face_stride + shell_slot(g, li, lj, lk, bx, by, bz)] = V[n];
       continue;
     }
     const bool owned = (li < pTx || lastx) && (lj < pTy || lasty) && (lk < pTz || lastz);
     if (!owned) continue;
     const int64_t gi = node_index(g, i, j, k);
-    if (MODE == MODE_OPERATOR) {
-      a.out0[gi] = dir ? a.in0[gi] : V[n];
-    } else if (MODE == MODE_RHS) {
-      a.out0[gi] = dir ? 0.0 : V[n];
-    } else if (MODE == MODE_DIAG) {
-      a.out0[gi] = dir ? 1.0 : V[n];
+    if constexpr (MODE == MODE_OPERATOR) {
+      const double* src = static_cast<const double*>(a.in0);
+      static_cast<double*>(a.out0)[gi] = dir ? src[gi] : t_to_double<PREC>(V[n]);
+    } else if constexpr (MODE == MODE_RHS) {
+      static_cast<double*>(a.out0)[gi] = dir ? 0.0 : t_to_double<PREC>(V[n]);
+    } else if constexpr (MODE == MODE_DIAG) {
+      static_cast<double*>(a.out0)[gi] = dir ? 1.0 : t_to_double<PREC>(V[n]);
     } else {
-      const double pk = dir ? a.out2[gi] : U[n];
-      const double v = dir ? pk : V[n];
-      const double rk = a.out0[gi];
-      a.out1[gi] = v;
-      post_sums(sm, rk, pk, v, a.diag_inv[gi]);
+      const T pk = dir ? static_cast<const T*>(a.out2)[gi] : U[n];
+      const T v = dir ? pk : V[n];
+      const T rk = static_cast<const T*>(a.out0)[gi];
+      static_cast<T*>(a.out1)[gi] = v;
+      post_sums<PREC>(sm, rk, pk, v, static_cast<const T*>(a.diag_inv)[gi]);
     }
   }
-  if (MODE == MODE_CG) {
-    block_reduce<7>(sm, red);
+  if constexpr (MODE == MODE_CG) {
+    double s[7];
+#pragma unroll
+    for (int m = 0; m < 7; ++m) s[m] = sm[m].get();
+    block_reduce<7>(s, red);
     if (threadIdx.x == 0) {
 #pragma unroll
-      for (int m = 0; m < 7; ++m) a.partial[tile * 8 + m] = sm[m];
+      for (int m = 0; m < 7; ++m) a.partial[tile * 8 + m] = s[m];
     }
   }
 }
@@ -544,9 +640,7 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a, const 
 // ------------------------------------------------------------------------------------
 // Tail: shared-face nodes and the scalar step of Algorithm 5
 // ------------------------------------------------------------------------------------
-
-template <int MODE>
-__device__ void cg_scalar_step(CGState* st, const double (&s)[7]) {
+__device__ inline void cg_scalar_step(CGState* st, const double (&s)[7]) {
   const double gam = s[0], av = s[1], bv = s[2], cv = s[3], dv = s[4], ev = s[5], fv = s[6];
   const int k = st->k;
   for (int m = 0; m < 7; ++m) st->sums[m] = s[m];
@@ -583,13 +677,15 @@ __device__ void cg_scalar_step(CGState* st, const double (&s)[7]) {
   st->k = k + 1;
 }
 
-template <int P, int MODE>
+template <int P, int MODE, int PREC>
 __global__ void __launch_bounds__(kThreads) tail_kernel(const TileArgs a) {
+  using T = typename Num<PREC>::T;
   __shared__ double red[8 * (kThreads / 32)];
   __shared__ int is_last;
   const TileGeom& g = a.g;
   if (MODE == MODE_CG && a.state->done) return;
-  double sm[7] = {0, 0, 0, 0, 0, 0, 0};
+  DotAcc<PREC> sm[7];
+  const T* shell = static_cast<const T*>(a.shell);
   for (int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x; t < a.tail_nodes; t += (int64_t)gridDim.x * kThreads) {
     int i, j, k;
     decode_tail_node(g, a.fam, t, i, j, k);
@@ -597,54 +693,58 @@ __global__ void __launch_bounds__(kThreads) tail_kernel(const TileArgs a) {
     const int nx = contributors(g, 0, i, txs, lis);
     const int ny = contributors(g, 1, j, tys, ljs);
     const int nz = contributors(g, 2, k, tzs, lks);
-    double v = 0.0;
+    T v = t_zero<PREC>();
     for (int cz = 0; cz < nz; ++cz)
       for (int cy = 0; cy < ny; ++cy)
         for (int cx = 0; cx < nx; ++cx) {
           const int64_t tl = txs[cx] + (int64_t)g.nt[0] * (tys[cy] + (int64_t)g.nt[1] * tzs[cz]);
           const int bx = brick_extent(g, 0, txs[cx]), by = brick_extent(g, 1, tys[cy]),
                     bz = brick_extent(g, 2, tzs[cz]);
-          v += a.shell[tl * g.face_stride + shell_slot(g, lis[cx], ljs[cy], lks[cz], bx, by, bz)];
+          v = t_add<PREC>(v, shell[tl * g.face_stride + shell_slot(g, lis[cx], ljs[cy], lks[cz], bx, by, bz)]);
         }
     const int64_t gi = node_index(g, i, j, k);
-    if (MODE == MODE_CG) {
-      const double rk = a.out0[gi], pk = a.out2[gi];
-      a.out1[gi] = v;
-      post_sums(sm, rk, pk, v, a.diag_inv[gi]);
+    if constexpr (MODE == MODE_CG) {
+      const T rk = static_cast<const T*>(a.out0)[gi], pk = static_cast<const T*>(a.out2)[gi];
+      static_cast<T*>(a.out1)[gi] = v;
+      post_sums<PREC>(sm, rk, pk, v, static_cast<const T*>(a.diag_inv)[gi]);
     } else {
-      a.out0[gi] = v;
+      static_cast<double*>(a.out0)[gi] = t_to_double<PREC>(v);
     }
   }
-  if (MODE != MODE_CG) return;
-  block_reduce<7>(sm, red);
-  double* tail_partial = a.partial + a.g.n_tiles * 8;
-  if (threadIdx.x == 0) {
-    for (int m = 0; m < 7; ++m) tail_partial[blockIdx.x * 8 + m] = sm[m];
-    __threadfence();
-    const unsigned prev = atomicAdd(&a.state->ticket, 1u);
-    is_last = (prev == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (!is_last) return;
-  __threadfence();
-  // last CTA: fixed-order reduction of all per-CTA sums
-  const int64_t nparts = a.g.n_tiles + gridDim.x;
-  double s[7] = {0, 0, 0, 0, 0, 0, 0};
-  for (int64_t t = threadIdx.x; t < nparts; t += kThreads) {
+  if constexpr (MODE == MODE_CG) {
+    double s7[7];
 #pragma unroll
-    for (int m = 0; m < 7; ++m) s[m] += __ldcg(a.partial + t * 8 + m);
-  }
-  block_reduce<7>(s, red);
-  if (threadIdx.x == 0) {
-    cg_scalar_step<MODE>(a.state, s);
-    a.state->ticket = 0u;
+    for (int m = 0; m < 7; ++m) s7[m] = sm[m].get();
+    block_reduce<7>(s7, red);
+    double* tail_partial = a.partial + a.g.n_tiles * 8;
+    if (threadIdx.x == 0) {
+      for (int m = 0; m < 7; ++m) tail_partial[blockIdx.x * 8 + m] = s7[m];
+      __threadfence();
+      const unsigned prev = atomicAdd(&a.state->ticket, 1u);
+      is_last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    // last CTA: fixed-order reduction of all per-CTA sums
+    const int64_t nparts = a.g.n_tiles + gridDim.x;
+    double s[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int64_t t = threadIdx.x; t < nparts; t += kThreads) {
+#pragma unroll
+      for (int m = 0; m < 7; ++m) s[m] += __ldcg(a.partial + t * 8 + m);
+    }
+    block_reduce<7>(s, red);
+    if (threadIdx.x == 0) {
+      cg_scalar_step(a.state, s);
+      a.state->ticket = 0u;
+    }
   }
 }
 
 // ------------------------------------------------------------------------------------
 // launch helpers
 // ------------------------------------------------------------------------------------
-inline size_t tile_smem_doubles(int P, int geom, const TileGeom& g) {
+inline size_t tile_smem_elems(int P, int geom, const TileGeom& g) {
   const size_t Bmax = (size_t)(P * g.T[0] + 1) * (P * g.T[1] + 1) * (P * g.T[2] + 1);
   const size_t cpc = (size_t)((g.T[0] + 1) / 2) * ((g.T[1] + 1) / 2) * ((g.T[2] + 1) / 2);
   const size_t n3 = (size_t)(P + 1) * (P + 1) * (P + 1);
@@ -654,26 +754,35 @@ inline size_t tile_smem_doubles(int P, int geom, const TileGeom& g) {
 template <int P>
 using TileFn = void (*)(const TileArgs, const OperatorCoeffs);
 
+// supported (mode, precision) pairs; nullptr otherwise
 template <int P, int GEOM>
-TileFn<P> tile_fn_g(int mode) {
+TileFn<P> tile_fn_g(int mode, int prec) {
   switch (mode) {
-    case MODE_CG: return tile_kernel<P, MODE_CG, GEOM>;
-    case MODE_OPERATOR: return tile_kernel<P, MODE_OPERATOR, GEOM>;
-    case MODE_RHS: return tile_kernel<P, MODE_RHS, GEOM>;
-    default: return tile_kernel<P, MODE_DIAG, GEOM>;
+    case MODE_CG:
+      return prec == PREC_F64 ? tile_kernel<P, MODE_CG, GEOM, PREC_F64>
+                              : (prec == PREC_DD ? tile_kernel<P, MODE_CG, GEOM, PREC_DD>
+                                                 : tile_kernel<P, MODE_CG, GEOM, PREC_F32>);
+    case MODE_OPERATOR:
+      return prec == PREC_F64 ? tile_kernel<P, MODE_OPERATOR, GEOM, PREC_F64>
+                              : (prec == PREC_DD ? tile_kernel<P, MODE_OPERATOR, GEOM, PREC_DD> : nullptr);
+    case MODE_RHS: return prec == PREC_F64 ? tile_kernel<P, MODE_RHS, GEOM, PREC_F64> : nullptr;
+    case MODE_DIAG: return prec == PREC_F64 ? tile_kernel<P, MODE_DIAG, GEOM, PREC_F64> : nullptr;
+    default: return nullptr;
   }
 }
 
 template <int P>
-TileFn<P> tile_fn(int mode, int geom) {
-  return geom == GEOM_AFFINE ? tile_fn_g<P, GEOM_AFFINE>(mode) : tile_fn_g<P, GEOM_DEFORMED>(mode);
+TileFn<P> tile_fn(int mode, int geom, int prec) {
+  return geom == GEOM_AFFINE ? tile_fn_g<P, GEOM_AFFINE>(mode, prec) : tile_fn_g<P, GEOM_DEFORMED>(mode, prec);
 }
 
 // once per problem (outside any stream capture): allow the dynamic shared memory
 template <int P>
-cudaError_t prepare_tile_p(int geom, size_t smem) {
+cudaError_t prepare_tile_p(int geom, int prec, size_t smem) {
   for (int mode = 0; mode < 4; ++mode) {
-    cudaError_t e = cudaFuncSetAttribute(tile_fn<P>(mode, geom), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    TileFn<P> fn = tile_fn<P>(mode, geom, prec);
+    if (!fn) continue;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -681,18 +790,25 @@ cudaError_t prepare_tile_p(int geom, size_t smem) {
 
 template <int P>
 cudaError_t launch_tile_p(int mode, const TileArgs& a, const OperatorCoeffs& c, cudaStream_t s) {
-  const size_t smem = tile_smem_doubles(P, a.geom, a.g) * sizeof(double);
-  tile_fn<P>(mode, a.geom)<<<(unsigned)a.g.n_tiles, kThreads, smem, s>>>(a, c);
+  TileFn<P> fn = tile_fn<P>(mode, a.geom, a.prec);
+  if (!fn) return cudaErrorInvalidValue;
+  const size_t smem = tile_smem_elems(P, a.geom, a.g) * prec_bytes(a.prec);
+  fn<<<(unsigned)a.g.n_tiles, kThreads, smem, s>>>(a, c);
   return cudaGetLastError();
 }
 
 template <int P>
 cudaError_t launch_tail_p(int mode, const TileArgs& a, cudaStream_t s) {
   const unsigned grid = (unsigned)(a.tail_ctas > 0 ? a.tail_ctas : 1);
-  if (mode == MODE_CG)
-    tail_kernel<P, MODE_CG><<<grid, kThreads, 0, s>>>(a);
-  else
-    tail_kernel<P, MODE_OPERATOR><<<grid, kThreads, 0, s>>>(a);
+  if (mode == MODE_CG) {
+    if (a.prec == PREC_F64) tail_kernel<P, MODE_CG, PREC_F64><<<grid, kThreads, 0, s>>>(a);
+    else if (a.prec == PREC_DD) tail_kernel<P, MODE_CG, PREC_DD><<<grid, kThreads, 0, s>>>(a);
+    else tail_kernel<P, MODE_CG, PREC_F32><<<grid, kThreads, 0, s>>>(a);
+  } else {
+    if (a.prec == PREC_DD) tail_kernel<P, MODE_OPERATOR, PREC_DD><<<grid, kThreads, 0, s>>>(a);
+    else if (a.prec == PREC_F64) tail_kernel<P, MODE_OPERATOR, PREC_F64><<<grid, kThreads, 0, s>>>(a);
+    else return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

@@ -7,5 +7,5 @@ cudaError_t launch_tile_deg5(int mode, const TileArgs& a, const OperatorCoeffs& 
   return launch_tile_p<5>(mode, a, c, s);
 }
 cudaError_t launch_tail_deg5(int mode, const TileArgs& a, cudaStream_t s) { return launch_tail_p<5>(mode, a, s); }
-cudaError_t prepare_tile_deg5(int geom, size_t smem) { return prepare_tile_p<5>(geom, smem); }
+cudaError_t prepare_tile_deg5(int geom, int prec, size_t smem) { return prepare_tile_p<5>(geom, prec, smem); }
 }  // namespace mfcg

@@ -7,5 +7,5 @@ cudaError_t launch_tile_deg6(int mode, const TileArgs& a, const OperatorCoeffs& 
   return launch_tile_p<6>(mode, a, c, s);
 }
 cudaError_t launch_tail_deg6(int mode, const TileArgs& a, cudaStream_t s) { return launch_tail_p<6>(mode, a, s); }
-cudaError_t prepare_tile_deg6(int geom, size_t smem) { return prepare_tile_p<6>(geom, smem); }
+cudaError_t prepare_tile_deg6(int geom, int prec, size_t smem) { return prepare_tile_p<6>(geom, prec, smem); }
 }  // namespace mfcg
