@@ -67,6 +67,7 @@ struct mfcg_problem {
   CGState* h_state = nullptr;  // pinned, two slots
   int64_t tail_nodes = 0;
   int64_t fam[3] = {0, 0, 0};
+  TailDiv tdiv{};
   int tail_ctas = 1;
   int graph_iters = 16;
   cudaGraphExec_t graph_fused = nullptr;
@@ -112,6 +113,7 @@ TileArgs base_args(const mfcg_problem* P, int prec, const void* geo) {
   a.state = P->state;
   a.tail_nodes = P->tail_nodes;
   for (int d = 0; d < 3; ++d) a.fam[d] = P->fam[d];
+  a.tdiv = P->tdiv;
   a.geom = P->geom_kind;
   a.prec = prec;
   a.tail_ctas = P->tail_ctas;
@@ -485,7 +487,7 @@ int mfcg_setup(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, con
   if (o.precision == MFCG_PREC_FP32_INNER && o.mode != MFCG_MODE_FUSED) return MFCG_INVALID_ARG;
   if (!(o.inner_rtol >= 0.0 && o.inner_rtol < 1.0)) return MFCG_INVALID_ARG;
   for (int d = 0; d < 3; ++d)
-    if (o.tile[d] < 0) return MFCG_INVALID_ARG;
+    if (o.tile[d] < 0 || o.tile[d] > 16) return MFCG_INVALID_ARG;
   const int64_t nn[3] = {(int64_t)degree * mesh->nx + 1, (int64_t)degree * mesh->ny + 1, (int64_t)degree * mesh->nz + 1};
   if (nn[0] > (1 << 20) || nn[1] > (1 << 20) || nn[2] > (1 << 20)) return MFCG_INVALID_ARG;
 
@@ -519,13 +521,14 @@ int mfcg_setup(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, con
     T[d] = o.tile[d] ? o.tile[d] : default_tile(degree, P->geom_kind);
     if (degree == 1 && T[d] < 2) T[d] = 2;
   }
-  init_tile_geom(degree, N, T, g, P->fam);
+  init_tile_geom(degree, N, T, g, P->fam, &P->tdiv);
   int max_smem = 0;
   cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device);
   const int precs[3] = {PREC_F64, P->op_prec, P->cg_prec};
   for (int pr : precs) {
     const size_t smem = tile_smem_bytes(degree, P->geom_kind, pr, g);
-    if (smem + 8 * (kThreads / 32) * sizeof(double) > (size_t)max_smem) return fail(MFCG_INVALID_ARG);
+    const size_t static_smem = 8 * (kThreads / 32) * sizeof(double) + 2 * 512 * sizeof(int);
+    if (smem + static_smem > (size_t)max_smem) return fail(MFCG_INVALID_ARG);
     if (prepare_tile(degree, P->geom_kind, pr, smem) != cudaSuccess) return fail(MFCG_CUDA_ERROR);
   }
   P->tail_nodes = P->fam[0] + P->fam[1] + P->fam[2];

@@ -24,6 +24,30 @@ constexpr int kThreads = 256;  // threads per CTA of every tile kernel
 // lexicographic order, x fastest; inside a tile lexicographic), which is the
 // GPU form of "unknowns touched by a single cell batch are numbered together".
 // ------------------------------------------------------------------------------------
+// Division by a runtime constant d >= 1 with a multiply-high and a shift
+// (round-up method): for n < 2^31, n / d == (umulhi(n, m) + n) >> s.
+struct FastDiv {
+  uint32_t d, m, s;
+};
+
+__host__ __device__ inline FastDiv make_fastdiv(uint32_t d) {
+  FastDiv f;
+  f.d = d;
+  uint32_t l = 0;
+  while ((1ull << l) < d) ++l;  // ceil(log2 d)
+  f.s = l;
+  f.m = (uint32_t)((((1ull << l) - d) << 32) / d + 1);
+  return f;
+}
+
+__host__ __device__ inline uint32_t fdiv(uint32_t n, const FastDiv& f) {
+#ifdef __CUDA_ARCH__
+  return (__umulhi(n, f.m) + n) >> f.s;
+#else
+  return (uint32_t)((((uint64_t)n * f.m) >> 32) + n) >> f.s;
+#endif
+}
+
 struct TileGeom {
   int p;
   int N[3];         // cells per direction
@@ -31,18 +55,26 @@ struct TileGeom {
   int nt[3];        // tiles per direction
   int nn[3];        // nodes per direction, p*N+1
   int own_last[3];  // nodes owned by the last tile per direction
-  int face_stride;  // doubles per tile in the shell (face partial) buffer
+  int face_stride;  // values per tile in the shell (face partial) buffer
   int64_t n_tiles;
   int64_t n_dofs;
+  FastDiv div_pT[3];  // division by p*T[d]
 };
-
-__host__ __device__ inline int tile_of(const TileGeom& g, int d, int i) {
-  int t = i / (g.p * g.T[d]);
-  return t < g.nt[d] - 1 ? t : g.nt[d] - 1;
-}
 
 __host__ __device__ inline int owned_count(const TileGeom& g, int d, int t) {
   return t == g.nt[d] - 1 ? g.own_last[d] : g.p * g.T[d];
+}
+
+__host__ __device__ inline int tile_of(const TileGeom& g, int d, int i) {
+  const int t = (int)fdiv((uint32_t)i, g.div_pT[d]);
+  return t < g.nt[d] - 1 ? t : g.nt[d] - 1;
+}
+
+// first index of the owned block of tile (tx, ty, tz)
+__host__ __device__ inline int64_t tile_base(const TileGeom& g, int tx, int ty, int tz) {
+  const int oy = owned_count(g, 1, ty), oz = owned_count(g, 2, tz);
+  return (int64_t)g.nn[0] * g.nn[1] * (g.p * g.T[2]) * tz + (int64_t)g.nn[0] * (g.p * g.T[1]) * ty * oz +
+         (int64_t)(g.p * g.T[0]) * tx * oy * oz;
 }
 
 // position of node (i,j,k) in the tile-blocked vector
@@ -82,54 +114,63 @@ __host__ __device__ inline int shell_slot(const TileGeom& g, int li, int lj, int
 // three families (on an x plane; on a y plane but no x plane; on a z plane
 // only), each a product set that is decoded arithmetically.
 // ------------------------------------------------------------------------------------
-// rank r of an interior node index that is not a tile boundary plane -> index
-__host__ __device__ inline int skip_planes(int r, int pT) { return r + 1 + r / (pT - 1); }
+// Divisors of the tail enumeration (fixed per problem).
+struct TailDiv {
+  FastDiv yz;    // (nn_y - 2)(nn_z - 2): x-plane family
+  FastDiv y;     // nn_y - 2
+  FastDiv xz;    // nxr (nn_z - 2): y-plane family
+  FastDiv xr;    // nxr = interior x indices off the x planes
+  FastDiv xy;    // nxr * nyr: z-plane family
+  FastDiv pTm1[2];  // p*T - 1 along x and y (rank -> index off the planes)
+};
 
-__host__ __device__ inline void decode_tail_node(const TileGeom& g, const int64_t (&fam)[3], int64_t t, int& i, int& j, int& k) {
+// rank r of an interior node index that is not a tile boundary plane -> index
+__host__ __device__ inline int skip_planes(int r, const FastDiv& pTm1) { return r + 1 + (int)fdiv((uint32_t)r, pTm1); }
+
+__host__ __device__ inline void decode_tail_node(const TileGeom& g, const int64_t (&fam)[3], const TailDiv& td,
+                                                 int64_t t64, int& i, int& j, int& k) {
   const int pTx = g.p * g.T[0], pTy = g.p * g.T[1], pTz = g.p * g.T[2];
-  const int niy = g.nn[1] - 2, niz = g.nn[2] - 2;
-  const int nbx = g.nt[0] - 1, nby = g.nt[1] - 1;
-  if (t < fam[0]) {  // i on an x plane, j, k interior
-    const int64_t per = (int64_t)niy * niz;
-    const int b = (int)(t / per);
-    const int64_t rem = t - b * per;
-    i = pTx * (b + 1);
-    j = 1 + (int)(rem % niy);
-    k = 1 + (int)(rem / niy);
+  uint32_t t = (uint32_t)t64;
+  if (t64 < fam[0]) {  // i on an x plane, j, k interior
+    const uint32_t b = fdiv(t, td.yz);
+    const uint32_t rem = t - b * td.yz.d;
+    const uint32_t q = fdiv(rem, td.y);
+    i = pTx * (int)(b + 1);
+    j = 1 + (int)(rem - q * td.y.d);
+    k = 1 + (int)q;
     return;
   }
-  t -= fam[0];
-  const int nxr = g.nn[0] - 2 - nbx;  // interior x indices off the x planes
-  if (t < fam[1]) {  // j on a y plane
-    const int64_t per = (int64_t)nxr * niz;
-    const int b = (int)(t / per);
-    const int64_t rem = t - b * per;
-    j = pTy * (b + 1);
-    i = skip_planes((int)(rem % nxr), pTx);
-    k = 1 + (int)(rem / nxr);
+  t = (uint32_t)(t64 - fam[0]);
+  if (t64 < fam[0] + fam[1]) {  // j on a y plane
+    const uint32_t b = fdiv(t, td.xz);
+    const uint32_t rem = t - b * td.xz.d;
+    const uint32_t q = fdiv(rem, td.xr);
+    j = pTy * (int)(b + 1);
+    i = skip_planes((int)(rem - q * td.xr.d), td.pTm1[0]);
+    k = 1 + (int)q;
     return;
   }
-  t -= fam[1];
-  const int nyr = g.nn[1] - 2 - nby;
-  const int64_t per = (int64_t)nxr * nyr;
-  const int b = (int)(t / per);
-  const int64_t rem = t - b * per;
-  k = pTz * (b + 1);
-  i = skip_planes((int)(rem % nxr), pTx);
-  j = skip_planes((int)(rem / nxr), pTy);
+  t = (uint32_t)(t64 - fam[0] - fam[1]);
+  const uint32_t b = fdiv(t, td.xy);
+  const uint32_t rem = t - b * td.xy.d;
+  const uint32_t q = fdiv(rem, td.xr);
+  k = pTz * (int)(b + 1);
+  i = skip_planes((int)(rem - q * td.xr.d), td.pTm1[0]);
+  j = skip_planes((int)q, td.pTm1[1]);
 }
 
 // tiles containing node index i along direction d: up to two (tile, local index) pairs
 __host__ __device__ inline int contributors(const TileGeom& g, int d, int i, int (&t)[2], int (&l)[2]) {
   const int pT = g.p * g.T[d];
-  if (i % pT == 0 && i > 0 && i < g.nn[d] - 1) {
-    t[0] = i / pT - 1;
+  const int q = (int)fdiv((uint32_t)i, g.div_pT[d]);
+  if (i == q * pT && i > 0 && i < g.nn[d] - 1) {
+    t[0] = q - 1;
     l[0] = pT;
-    t[1] = i / pT;
+    t[1] = q;
     l[1] = 0;
     return 2;
   }
-  t[0] = tile_of(g, d, i);
+  t[0] = q < g.nt[d] - 1 ? q : g.nt[d] - 1;
   l[0] = i - pT * t[0];
   return 1;
 }
@@ -141,7 +182,7 @@ __host__ __device__ inline int brick_extent(const TileGeom& g, int d, int t) {
 
 // Tile geometry for degree p, cells N and tile edges T (each clamped to N),
 // and the sizes of the three tail-node families.
-inline void init_tile_geom(int p, const int N[3], const int T[3], TileGeom& g, int64_t (&fam)[3]) {
+inline void init_tile_geom(int p, const int N[3], const int T[3], TileGeom& g, int64_t (&fam)[3], TailDiv* td = nullptr) {
   g.p = p;
   for (int d = 0; d < 3; ++d) {
     g.N[d] = N[d];
@@ -150,6 +191,7 @@ inline void init_tile_geom(int p, const int N[3], const int T[3], TileGeom& g, i
     g.nn[d] = p * N[d] + 1;
     g.own_last[d] = g.nn[d] - p * g.T[d] * (g.nt[d] - 1);
   }
+  for (int d = 0; d < 3; ++d) g.div_pT[d] = make_fastdiv((uint32_t)(p * g.T[d]));
   const int Bx = p * g.T[0] + 1, By = p * g.T[1] + 1, Bz = p * g.T[2] + 1;
   g.face_stride = 2 * (By * Bz + Bx * Bz + Bx * By);
   g.n_tiles = (int64_t)g.nt[0] * g.nt[1] * g.nt[2];
@@ -161,6 +203,16 @@ inline void init_tile_geom(int p, const int N[3], const int T[3], TileGeom& g, i
     fam[0] = nbx * niy * niz;
     fam[1] = nby * (nix - nbx) * niz;
     fam[2] = nbz * (nix - nbx) * (niy - nby);
+  }
+  if (td) {
+    auto nz1 = [](int64_t v) { return (uint32_t)(v > 0 ? v : 1); };
+    td->yz = make_fastdiv(nz1(niy * niz));
+    td->y = make_fastdiv(nz1(niy));
+    td->xz = make_fastdiv(nz1((nix - nbx) * niz));
+    td->xr = make_fastdiv(nz1(nix - nbx));
+    td->xy = make_fastdiv(nz1((nix - nbx) * (niy - nby)));
+    td->pTm1[0] = make_fastdiv(nz1(p * g.T[0] - 1));
+    td->pTm1[1] = make_fastdiv(nz1(p * g.T[1] - 1));
   }
 }
 
@@ -231,6 +283,7 @@ struct TileArgs {
   CGState* state;
   int64_t tail_nodes;    // number of shared-face nodes handled by the tail kernel
   int64_t fam[3];        // tail enumeration: nodes in the x / y / z boundary-plane families
+  TailDiv tdiv;          // divisors of the tail enumeration
   int geom;              // GeomKind
   int prec;              // Prec (precision.cuh)
   int tail_ctas;

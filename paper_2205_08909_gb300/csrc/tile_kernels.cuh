@@ -27,6 +27,9 @@
 
 namespace mfcg {
 
+// largest number of cells of one colour in a tile (tile edges <= 16 cells)
+constexpr int kMaxColorCells = 512;
+
 // ------------------------------------------------------------------------------------
 // 1D contractions on a pencil of N1 = P+1 values held in registers
 // ------------------------------------------------------------------------------------
@@ -185,15 +188,13 @@ __device__ __forceinline__ void sweep_inplace_table_t(double* arr, int stride, i
   __syncthreads();
 }
 
+// Cells of one colour (parity of the tile-local cell index) with their brick
+// origin offsets and global cell indices tabulated in shared memory.
 struct ColorCells {
-  int mx, my, mz, px, py, pz;
-  __device__ int count() const { return mx * my * mz; }
-  // tile-local cell coordinates of the ci-th cell of this colour
-  __device__ void cell(int ci, int& cx, int& cy, int& cz) const {
-    cx = px + 2 * (ci % mx);
-    cy = py + 2 * ((ci / mx) % my);
-    cz = pz + 2 * (ci / (mx * my));
-  }
+  int n;              // number of cells
+  const int* org;     // brick offset of the cell's (0,0,0) node
+  const int* cell;    // global lexicographic cell index
+  __device__ int count() const { return n; }
 };
 
 // ------------------------------------------------------------------------------------
@@ -213,9 +214,7 @@ __device__ void cell_op_affine(const OperatorCoeffs& c, const typename Num<PREC>
   // z direction: s1 = M u, s2 = K_z u
   for (int t = threadIdx.x; t < nc * N2; t += kThreads) {
     const int ci = t / N2, e = t - ci * N2, a = e % N1, b = e / N1;
-    int cx, cy, cz;
-    cc.cell(ci, cx, cy, cz);
-    const T* u0 = U + (P * cx + a) + bx * ((P * cy + b) + by * (P * cz));
+    const T* u0 = U + cc.org[ci] + a + bx * b;
     T x[N1], y1[N1], y2[N1];
 #pragma unroll
     for (int s = 0; s < N1; ++s) x[s] = u0[s * bx * by];
@@ -253,8 +252,6 @@ __device__ void cell_op_affine(const OperatorCoeffs& c, const typename Num<PREC>
   // x direction: out = K_x s1 + M s2, added into V
   for (int t = threadIdx.x; t < nc * N2; t += kThreads) {
     const int ci = t / N2, e = t - ci * N2, b = e % N1, cz = e / N1;
-    int cx, cy, czz;
-    cc.cell(ci, cx, cy, czz);
     const T* s1 = S + ci * 2 * N3;
     const T* s2 = s1 + N3;
     T m[N1], k[N1], y[N1];
@@ -264,7 +261,7 @@ __device__ void cell_op_affine(const OperatorCoeffs& c, const typename Num<PREC>
       k[s] = s2[cidx<N1>(s, b, cz)];
     }
     mv2<PREC, N1>(c, MAT_K0, m, MAT_M, k, y);
-    T* v0 = V + (P * cx) + bx * ((P * cy + b) + by * (P * czz + cz));
+    T* v0 = V + cc.org[ci] + bx * (b + by * cz);
 #pragma unroll
     for (int i = 0; i < N1; ++i) v0[i] = t_add<PREC>(v0[i], y[i]);
   }
@@ -278,8 +275,7 @@ __device__ void cell_op_affine(const OperatorCoeffs& c, const typename Num<PREC>
 template <int PREC, int P>
 __device__ void cell_op_deformed(const OperatorCoeffs& c, const typename Num<PREC>::T* U, typename Num<PREC>::T* V,
                                  typename Num<PREC>::T* S, int bx, int by, const ColorCells& cc,
-                                 const typename Num<PREC>::T* __restrict__ geo, int cell_base_x, int cell_base_y,
-                                 int cell_base_z, const TileGeom& g) {
+                                 const typename Num<PREC>::T* __restrict__ geo) {
   using T = typename Num<PREC>::T;
   constexpr int N1 = P + 1, N2 = N1 * N1, N3 = N2 * N1;
   const int nc = cc.count();
@@ -287,9 +283,7 @@ __device__ void cell_op_deformed(const OperatorCoeffs& c, const typename Num<PRE
   // gather u into s0
   for (int t = threadIdx.x; t < nc * N3; t += kThreads) {
     const int ci = t / N3, e = t - ci * N3, a = e % N1, b = (e / N1) % N1, cz = e / N2;
-    int cx, cy, czz;
-    cc.cell(ci, cx, cy, czz);
-    S[ci * stride + e] = U[(P * cx + a) + bx * ((P * cy + b) + by * (P * czz + cz))];
+    S[ci * stride + e] = U[cc.org[ci] + a + bx * (b + by * cz)];
   }
   __syncthreads();
   sweep_inplace<PREC, P, false>(S, stride, nc, 0, c, MAT_S);
@@ -313,10 +307,7 @@ __device__ void cell_op_deformed(const OperatorCoeffs& c, const typename Num<PRE
   // metric at each point: flux = J^{-1} (JxW a) J^{-T} grad_ref
   for (int t = threadIdx.x; t < nc * N3; t += kThreads) {
     const int ci = t / N3, q = t - ci * N3;
-    int cx, cy, cz;
-    cc.cell(ci, cx, cy, cz);
-    const int64_t cell = (cell_base_x + cx) + (int64_t)g.N[0] * ((cell_base_y + cy) + (int64_t)g.N[1] * (cell_base_z + cz));
-    const T* gq = geo + cell * 10 * N3 + q;
+    const T* gq = geo + (int64_t)cc.cell[ci] * 10 * N3 + q;
     T Ji[9];
 #pragma unroll
     for (int m = 0; m < 9; ++m) Ji[m] = gq[m * N3];
@@ -341,14 +332,12 @@ __device__ void cell_op_deformed(const OperatorCoeffs& c, const typename Num<PRE
   // last sweep writes straight into the node brick
   for (int t = threadIdx.x; t < nc * N2; t += kThreads) {
     const int ci = t / N2, e = t - ci * N2, a = e % N1, b = e / N1;
-    int cx, cy, cz;
-    cc.cell(ci, cx, cy, cz);
     const T* s0 = S + ci * stride;
     T x[N1], y[N1];
 #pragma unroll
     for (int s = 0; s < N1; ++s) x[s] = s0[cidx<N1>(a, b, s)];
     mv<PREC, N1, true>(c, MAT_S, x, y);
-    T* v0 = V + (P * cx + a) + bx * ((P * cy + b) + by * (P * cz));
+    T* v0 = V + cc.org[ci] + a + bx * b;
 #pragma unroll
     for (int s = 0; s < N1; ++s) v0[s * bx * by] = t_add<PREC>(v0[s * bx * by], y[s]);
   }
@@ -368,17 +357,17 @@ __device__ inline double manufactured_forcing(double x, double y, double z, int 
 
 template <int P>
 __device__ void cell_rhs(const OperatorCoeffs& c, double* V, double* S, int bx, int by, const ColorCells& cc,
-                         int cx0, int cy0, int cz0, int stride) {
+                         const TileGeom& g, int stride) {
   constexpr int N1 = P + 1, N2 = N1 * N1, N3 = N2 * N1;
   const int nc = cc.count();
   const double twopi = 6.28318530717958647692;
   for (int t = threadIdx.x; t < nc * N3; t += kThreads) {
     const int ci = t / N3, q = t - ci * N3, qa = q % N1, qb = (q / N1) % N1, qc = q / N2;
-    int cx, cy, cz;
-    cc.cell(ci, cx, cy, cz);
-    const double X = c.h[0] * (cx0 + cx + c.g[qa]);
-    const double Y = c.h[1] * (cy0 + cy + c.g[qb]);
-    const double Z = c.h[2] * (cz0 + cz + c.g[qc]);
+    const int cell = cc.cell[ci];
+    const int gx = cell % g.N[0], gy = (cell / g.N[0]) % g.N[1], gz = cell / (g.N[0] * g.N[1]);
+    const double X = c.h[0] * (gx + c.g[qa]);
+    const double Y = c.h[1] * (gy + c.g[qb]);
+    const double Z = c.h[2] * (gz + c.g[qc]);
     const double sx = sin(twopi * X), sy = sin(twopi * Y), sz = sin(twopi * Z);
     const double A = c.amplitude;
     const double s = sx * sy * sz;
@@ -393,9 +382,7 @@ __device__ void cell_rhs(const OperatorCoeffs& c, double* V, double* S, int bx, 
   sweep_inplace<PREC_F64, P, true>(S, stride, nc, 2, c, MAT_S);
   for (int t = threadIdx.x; t < nc * N3; t += kThreads) {
     const int ci = t / N3, e = t - ci * N3, a = e % N1, b = (e / N1) % N1, cz = e / N2;
-    int cx, cy, czz;
-    cc.cell(ci, cx, cy, czz);
-    V[(P * cx + a) + bx * ((P * cy + b) + by * (P * czz + cz))] += S[ci * stride + e];
+    V[cc.org[ci] + a + bx * (b + by * cz)] += S[ci * stride + e];
   }
   __syncthreads();
 }
@@ -407,7 +394,7 @@ __device__ void cell_rhs(const OperatorCoeffs& c, double* V, double* S, int bx, 
 // tables along each direction, i.e. three transposed sweeps.
 template <int P, int GEOM>
 __device__ void cell_diag(const OperatorCoeffs& c, double* V, double* S, int bx, int by, const ColorCells& cc,
-                          const double* __restrict__ geo, int cx0, int cy0, int cz0, const TileGeom& g, int stride) {
+                          const double* __restrict__ geo, int stride) {
   constexpr int N1 = P + 1, N2 = N1 * N1, N3 = N2 * N1;
   const int nc = cc.count();
   for (int t = threadIdx.x; t < nc * N3; t += kThreads) {
@@ -426,10 +413,7 @@ __device__ void cell_diag(const OperatorCoeffs& c, double* V, double* S, int bx,
         const int qa = q % N1, qb = (q / N1) % N1, qc = q / N2;
         C = c.w[qa] * c.w[qb] * c.w[qc] * c.h[0] * c.h[1] * c.h[2] / (c.h[d0] * c.h[d0]);
       } else {
-        int cx, cy, cz;
-        cc.cell(ci, cx, cy, cz);
-        const int64_t cell = (cx0 + cx) + (int64_t)g.N[0] * ((cy0 + cy) + (int64_t)g.N[1] * (cz0 + cz));
-        const double* gq = geo + cell * 10 * N3 + q;
+        const double* gq = geo + (int64_t)cc.cell[ci] * 10 * N3 + q;
         double s = 0.0;
 #pragma unroll
         for (int m = 0; m < 3; ++m) s = fma(__ldg(gq + (3 * d0 + m) * N3), __ldg(gq + (3 * d1 + m) * N3), s);
@@ -451,9 +435,7 @@ __device__ void cell_diag(const OperatorCoeffs& c, double* V, double* S, int bx,
   }
   for (int t = threadIdx.x; t < nc * N3; t += kThreads) {
     const int ci = t / N3, e = t - ci * N3, a = e % N1, b = (e / N1) % N1, cz = e / N2;
-    int cx, cy, czz;
-    cc.cell(ci, cx, cy, czz);
-    V[(P * cx + a) + bx * ((P * cy + b) + by * (P * czz + cz))] += S[ci * stride + N3 + e];
+    V[cc.org[ci] + a + bx * (b + by * cz)] += S[ci * stride + N3 + e];
   }
   __syncthreads();
 }
@@ -504,11 +486,25 @@ __device__ __forceinline__ void post_sums(DotAcc<PREC> (&sm)[7], typename Num<PR
 // ------------------------------------------------------------------------------------
 // The tile kernel
 // ------------------------------------------------------------------------------------
+// position in the tile-blocked vector of brick node (li, lj, lk) of tile
+// (tx, ty, tz) whose own block starts at `base` with extents (ox, oy, oz);
+// nodes past the owned extent belong to the next tile along that direction
+__device__ __forceinline__ int64_t brick_global_index(const TileGeom& g, int tx, int ty, int tz, int li, int lj,
+                                                      int lk, int ox, int oy, int oz, int64_t base) {
+  if (li < ox && lj < oy && lk < oz) return base + li + (int64_t)ox * (lj + (int64_t)oy * lk);
+  const int ntx = li < ox ? tx : tx + 1, nty = lj < oy ? ty : ty + 1, ntz = lk < oz ? tz : tz + 1;
+  const int nli = li < ox ? li : li - ox, nlj = lj < oy ? lj : lj - oy, nlk = lk < oz ? lk : lk - oz;
+  const int nox = owned_count(g, 0, ntx), noy = owned_count(g, 1, nty);
+  return tile_base(g, ntx, nty, ntz) + nli + (int64_t)nox * (nlj + (int64_t)noy * nlk);
+}
+
 template <int P, int MODE, int GEOM, int PREC>
 __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a, const OperatorCoeffs c) {
   using T = typename Num<PREC>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[8 * (kThreads / 32)];
+  __shared__ int s_org[kMaxColorCells];
+  __shared__ int s_cell[kMaxColorCells];
   constexpr int N1 = P + 1, N3 = N1 * N1 * N1;
   const TileGeom& g = a.g;
 
@@ -535,8 +531,10 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a, const 
   const int bsize = bx * by * bz;
   const int Bmax = (P * g.T[0] + 1) * (P * g.T[1] + 1) * (P * g.T[2] + 1);
   const int gi0 = P * cx0, gj0 = P * cy0, gk0 = P * cz0;
-  const int pTx = P * g.T[0], pTy = P * g.T[1], pTz = P * g.T[2];
   const bool lastx = tx == g.nt[0] - 1, lasty = ty == g.nt[1] - 1, lastz = tz == g.nt[2] - 1;
+  const int ox = owned_count(g, 0, tx), oy = owned_count(g, 1, ty), oz = owned_count(g, 2, tz);
+  const int64_t base = tile_base(g, tx, ty, tz);
+  const FastDiv fbx = make_fastdiv((uint32_t)bx), fbxy = make_fastdiv((uint32_t)(bx * by));
 
   T* U = reinterpret_cast<T*>(smem_raw);
   T* V = U + Bmax;
@@ -544,20 +542,24 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a, const 
 
   // ---------------- phase 1: pre ----------------
   for (int n = threadIdx.x; n < bsize; n += kThreads) {
-    const int li = n % bx, lj = (n / bx) % by, lk = n / (bx * by);
+    const int lk = (int)fdiv((uint32_t)n, fbxy);
+    const int rem = n - lk * bx * by;
+    const int lj = (int)fdiv((uint32_t)rem, fbx);
+    const int li = rem - lj * bx;
     const int i = gi0 + li, j = gj0 + lj, k = gk0 + lk;
     if constexpr (MODE == MODE_OPERATOR) {
       const bool dir = is_dirichlet(g, i, j, k);
-      U[n] = dir ? t_zero<PREC>() : t_from_double<PREC>(static_cast<const double*>(a.in0)[node_index(g, i, j, k)]);
+      const int64_t gi = brick_global_index(g, tx, ty, tz, li, lj, lk, ox, oy, oz, base);
+      U[n] = dir ? t_zero<PREC>() : t_from_double<PREC>(static_cast<const double*>(a.in0)[gi]);
     } else if constexpr (MODE == MODE_CG) {
       const bool dir = is_dirichlet(g, i, j, k);
-      const int64_t gi = node_index(g, i, j, k);
+      const int64_t gi = brick_global_index(g, tx, ty, tz, li, lj, lk, ox, oy, oz, base);
       const T r_o = static_cast<const T*>(a.in0)[gi], v_o = static_cast<const T*>(a.in1)[gi];
       const T p_o = static_cast<const T*>(a.in2)[gi], dinv = static_cast<const T*>(a.diag_inv)[gi];
       const T rk = t_axpy<PREC>(alpha_m, v_o, r_o);       // r_{k-1} - alpha_{k-1} v_{k-1}
       const T pk = t_axby<PREC>(dinv, rk, beta_t, p_o);   // M^{-1} r_k + beta_{k-1} p_{k-1}
       U[n] = dir ? t_zero<PREC>() : pk;
-      const bool owned = (li < pTx || lastx) && (lj < pTy || lasty) && (lk < pTz || lastz);
+      const bool owned = li < ox && lj < oy && lk < oz;
       if (owned) {
         static_cast<T*>(a.out0)[gi] = rk;
         static_cast<T*>(a.out2)[gi] = pk;
@@ -570,27 +572,29 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a, const 
     }
     V[n] = t_zero<PREC>();
   }
-  __syncthreads();
 
   // ---------------- phase 2: cell integrals, one colour at a time ----------------
   for (int color = 0; color < 8; ++color) {
-    ColorCells cc;
-    cc.px = color & 1;
-    cc.py = (color >> 1) & 1;
-    cc.pz = color >> 2;
-    cc.mx = (ncx - cc.px + 1) / 2;
-    cc.my = (ncy - cc.py + 1) / 2;
-    cc.mz = (ncz - cc.pz + 1) / 2;
-    if (cc.count() == 0) continue;
+    const int px = color & 1, py = (color >> 1) & 1, pz = color >> 2;
+    const int mx = (ncx - px + 1) / 2, my = (ncy - py + 1) / 2, mz = (ncz - pz + 1) / 2;
+    const int nc = mx * my * mz;
+    if (nc == 0) continue;
+    __syncthreads();  // previous colour finished with the tables (and phase 1 with U, V)
+    for (int ci = threadIdx.x; ci < nc; ci += kThreads) {
+      const int cx = px + 2 * (ci % mx), cy = py + 2 * ((ci / mx) % my), cz = pz + 2 * (ci / (mx * my));
+      s_org[ci] = P * cx + bx * (P * cy + by * P * cz);
+      s_cell[ci] = (cx0 + cx) + g.N[0] * ((cy0 + cy) + g.N[1] * (cz0 + cz));
+    }
+    __syncthreads();
+    const ColorCells cc{nc, s_org, s_cell};
     if constexpr (MODE == MODE_RHS) {
-      cell_rhs<P>(c, V, S, bx, by, cc, cx0, cy0, cz0, (GEOM == GEOM_AFFINE ? 2 : 4) * N3);
+      cell_rhs<P>(c, V, S, bx, by, cc, g, (GEOM == GEOM_AFFINE ? 2 : 4) * N3);
     } else if constexpr (MODE == MODE_DIAG) {
-      cell_diag<P, GEOM>(c, V, S, bx, by, cc, static_cast<const double*>(a.geo), cx0, cy0, cz0, g,
-                         (GEOM == GEOM_AFFINE ? 2 : 4) * N3);
+      cell_diag<P, GEOM>(c, V, S, bx, by, cc, static_cast<const double*>(a.geo), (GEOM == GEOM_AFFINE ? 2 : 4) * N3);
     } else if constexpr (GEOM == GEOM_AFFINE) {
       cell_op_affine<PREC, P>(c, U, V, S, bx, by, cc);
     } else {
-      cell_op_deformed<PREC, P>(c, U, V, S, bx, by, cc, static_cast<const T*>(a.geo), cx0, cy0, cz0, g);
+      cell_op_deformed<PREC, P>(c, U, V, S, bx, by, cc, static_cast<const T*>(a.geo));
     }
   }
 
@@ -598,7 +602,10 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a, const 
   DotAcc<PREC> sm[7];
   T* shell = static_cast<T*>(a.shell);
   for (int n = threadIdx.x; n < bsize; n += kThreads) {
-    const int li = n % bx, lj = (n / bx) % by, lk = n / (bx * by);
+    const int lk = (int)fdiv((uint32_t)n, fbxy);
+    const int rem = n - lk * bx * by;
+    const int lj = (int)fdiv((uint32_t)rem, fbx);
+    const int li = rem - lj * bx;
     const int i = gi0 + li, j = gj0 + lj, k = gk0 + lk;
     const bool dir = is_dirichlet(g, i, j, k);
     const bool shared = !dir && ((li == 0 && tx > 0) || (li == bx - 1 && !lastx) || (lj == 0 && ty > 0) ||
@@ -607,9 +614,9 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a, const 
       shell[tile * g.face_stride + shell_slot(g, li, lj, lk, bx, by, bz)] = V[n];
       continue;
     }
-    const bool owned = (li < pTx || lastx) && (lj < pTy || lasty) && (lk < pTz || lastz);
+    const bool owned = li < ox && lj < oy && lk < oz;
     if (!owned) continue;
-    const int64_t gi = node_index(g, i, j, k);
+    const int64_t gi = base + li + (int64_t)ox * (lj + (int64_t)oy * lk);
     if constexpr (MODE == MODE_OPERATOR) {
       const double* src = static_cast<const double*>(a.in0);
       static_cast<double*>(a.out0)[gi] = dir ? src[gi] : t_to_double<PREC>(V[n]);
@@ -688,7 +695,7 @@ __global__ void __launch_bounds__(kThreads) tail_kernel(const TileArgs a) {
   const T* shell = static_cast<const T*>(a.shell);
   for (int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x; t < a.tail_nodes; t += (int64_t)gridDim.x * kThreads) {
     int i, j, k;
-    decode_tail_node(g, a.fam, t, i, j, k);
+    decode_tail_node(g, a.fam, a.tdiv, t, i, j, k);
     int txs[2], lis[2], tys[2], ljs[2], tzs[2], lks[2];
     const int nx = contributors(g, 0, i, txs, lis);
     const int ny = contributors(g, 1, j, tys, ljs);

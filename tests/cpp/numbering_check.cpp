@@ -22,7 +22,8 @@ using namespace mfcg;
 static int check(int p, const int N[3], const int T[3]) {
   TileGeom g;
   int64_t fam[3];
-  init_tile_geom(p, N, T, g, fam);
+  TailDiv td;
+  init_tile_geom(p, N, T, g, fam, &td);
   const int64_t n = g.n_dofs;
   // 1. bijection onto [0, n)
   std::vector<int> hit(n, 0);
@@ -80,7 +81,7 @@ static int check(int p, const int N[3], const int T[3]) {
   int64_t reads = 0;
   for (int64_t t = 0; t < fam[0] + fam[1] + fam[2]; ++t) {
     int i, j, k;
-    decode_tail_node(g, fam, t, i, j, k);
+    decode_tail_node(g, fam, td, t, i, j, k);
     REQUIRE(i > 0 && j > 0 && k > 0 && i < g.nn[0] - 1 && j < g.nn[1] - 1 && k < g.nn[2] - 1);
     const int64_t lex = i + (int64_t)g.nn[0] * (j + (int64_t)g.nn[1] * k);
     REQUIRE(seen[lex] == 0);
@@ -110,8 +111,20 @@ static int check(int p, const int N[3], const int T[3]) {
   return 0;
 }
 
+// multiply-shift division agrees with integer division
+static int check_fastdiv() {
+  const int p = 0, N[3] = {0, 0, 0}, T[3] = {0, 0, 0};
+  for (uint32_t d = 1; d < 3000; ++d) {
+    const FastDiv f = make_fastdiv(d);
+    for (uint32_t n = 0; n < 5000; ++n) REQUIRE(fdiv(n, f) == n / d);
+    for (uint32_t n = (1u << 31) - 5000; n < (1u << 31); n += 7) REQUIRE(fdiv(n, f) == n / d);
+  }
+  return 0;
+}
+
 int main() {
   int count = 0;
+  if (check_fastdiv()) return 1;
   for (int p = 1; p <= 8; ++p) {
     const int meshes[][3] = {{1, 1, 1}, {2, 3, 4}, {5, 4, 3}, {7, 2, 9}, {8, 8, 8}, {9, 5, 6}};
     const int tiles[][3] = {{2, 2, 2}, {4, 4, 4}, {3, 2, 5}, {1, 1, 1}, {2, 3, 1}};
