@@ -261,9 +261,12 @@ def run_ours(args, world, rank, local):
     hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
     main_prec = args.precision
 
+    tile = tuple(int(t) for t in args.tile.split(",")) if args.tile else None
+
     def make(mode, precision, instrument=False):
         return mfcg.Problem(w.degree, w.cells, amplitude=w.amplitude, geometry=w.geometry,
-                            coefficient=w.coefficient, mode=mode, precision=precision, instrument=instrument)
+                            coefficient=w.coefficient, mode=mode, precision=precision, instrument=instrument,
+                            tile=tile)
 
     def timed_steps(prob, b, K, W):
         xs = [torch.zeros(prob.n_dofs, dtype=torch.float64, device="cuda") for _ in range(max(K, W, 1))]
@@ -309,6 +312,8 @@ def run_ours(args, world, rank, local):
     variants = {}
     for mode, prec in (("unfused", main_prec), ("fused", "fp64"), ("unfused", "fp64")):
         if args.skip_unfused and mode == "unfused":
+            continue
+        if args.skip_variants and (mode, prec) != ("unfused", main_prec):
             continue
         if prec == main_prec and mode == "fused":
             continue
@@ -390,6 +395,7 @@ def run_ours(args, world, rank, local):
         "data": "synthetic: manufactured right-hand side of u = sin(pi x) sin(pi y) sin(pi z), x0 = 0",
         "config": {"workload": w.name, "degree": w.degree, "cells": list(w.cells), "n_dofs": w.n_dofs,
                    "geometry": w.geometry, "precision": main_prec, "iterations_per_step": iters,
+                   "tile": list(tile) if tile else "default",
                    "parallelism": f"replicas x{world}",
                    "l2": f"inputs larger than L2: {8 * w.n_dofs / 1e6:.0f} MB per vector, 8 vectors"},
         "hbm_roofline_frac": round(value / world * ALGORITHMIC_BYTES_PER_DOF / hbm, 4),
@@ -425,6 +431,8 @@ def main():
     ap.add_argument("--skip-unfused", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-dc", action="store_true", help="skip the FP32-inner defect-correction solve")
+    ap.add_argument("--skip-variants", action="store_true", help="skip the FP64 comparators")
+    ap.add_argument("--tile", default="", help="cells per tile, e.g. 4,4,2 (default: chosen from the degree)")
     ap.add_argument("--precision", default="double_float", choices=["fp64", "double_float", "fp32_inner"],
                     help="arithmetic of the headline fused path")
     args = ap.parse_args()

@@ -147,9 +147,10 @@ int mfcg_rhs(mfcg_problem* prob, double* b);
 /* mfcg_cg_solve -- Jacobi-preconditioned CG from the initial guess in x
  * (Algorithm 5 in FUSED mode, Algorithm 1 in UNFUSED mode) until
  * ||r_k|| < rtol ||b|| (unpreconditioned residual, Sec. 3.1) or maxit products
- * A p.  rtol == 0 runs exactly maxit iterations and returns MFCG_OK (not
- * available with MFCG_PREC_FP32_INNER, which stops on the true residual
- * ||b - A x|| < rtol ||b|| and counts maxit over all inner iterations).
+ * A p.  rtol == 0 runs exactly maxit iterations and returns MFCG_OK.  With
+ * MFCG_PREC_FP32_INNER the solve stops on the true residual ||b - A x|| <
+ * rtol ||b|| and maxit counts all inner iterations; rtol == 0 there applies
+ * one correction x += d with exactly maxit inner FP32 iterations.
  *   b   in : device, n doubles, must be zero on Dirichlet nodes (INVALID_ARG is
  *            not checked on the device; a nonzero value there is solved as an
  *            identity row).

@@ -427,9 +427,31 @@ int solve_defect_correction(mfcg_problem* P, const double* b, double* x_user, do
   return status;
 }
 
+// rtol == 0 with the FP32 inner form: one correction x += d with exactly maxit
+// inner FP32 iterations on A d = b - A x (benchmark mode of the inner kernel).
+int solve_fixed_inner(mfcg_problem* P, const double* b, double* x_user, int maxit, mfcg_solve_info* info) {
+  const int64_t n = P->g.n_dofs;
+  const int64_t launches0 = P->launches;
+  const size_t es = prec_bytes(P->cg_prec);
+  IterStats stats;
+  int st;
+  if ((st = run_pass(P, MODE_OPERATOR, x_user, P->work)) != MFCG_OK) return st;
+  CK(launch_residual(b, P->work, P->work, n, P->exec));
+  CK(cudaMemsetAsync(P->xs, 0, n * es, P->exec));
+  P->launches += 1;
+  if ((st = fused_core(P, P->work, P->work, 0.0, maxit, 1, stats)) != MFCG_OK) return st;
+  CK(launch_from_prec(P->cg_prec, P->xs, x_user, n, 1, P->exec));
+  CK(cudaMemcpyAsync(P->h_state, P->state, sizeof(CGState), cudaMemcpyDeviceToHost, P->exec));
+  CK(cudaStreamSynchronize(P->exec));
+  P->launches += 1;
+  const int status = P->h_state->done == 3 ? MFCG_BREAKDOWN : MFCG_OK;
+  fill_info(P, info, status, P->h_state->iterations, stats, launches0, 1);
+  return status;
+}
+
 int solve_impl(mfcg_problem* P, const double* b, double* x_user, double rtol, int maxit, mfcg_solve_info* info) {
   if (P->opt.precision == MFCG_PREC_FP32_INNER) {
-    if (rtol <= 0.0) return MFCG_INVALID_ARG;
+    if (rtol == 0.0) return solve_fixed_inner(P, b, x_user, maxit, info);
     return solve_defect_correction(P, b, x_user, rtol, maxit, info);
   }
   return solve_direct(P, b, x_user, rtol, maxit, info);
@@ -532,7 +554,7 @@ int mfcg_setup(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, con
     if (prepare_tile(degree, P->geom_kind, pr, smem) != cudaSuccess) return fail(MFCG_CUDA_ERROR);
   }
   P->tail_nodes = P->fam[0] + P->fam[1] + P->fam[2];
-  P->tail_ctas = (int)std::min<int64_t>(std::max<int64_t>((P->tail_nodes + kThreads - 1) / kThreads, 1), 152 * 8);
+  P->tail_ctas = (int)std::min<int64_t>(std::max<int64_t>((P->tail_nodes + 2 * kThreads - 1) / (2 * kThreads), 1), 152 * 32);
 
   const double h[3] = {1.0 / N[0], 1.0 / N[1], 1.0 / N[2]};
   build_coeffs(degree, h, mesh->amplitude, geom->coefficient, P->c);

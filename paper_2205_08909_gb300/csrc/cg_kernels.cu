@@ -150,6 +150,7 @@ __global__ void cg_init_kernel(CGState* st, const double* b, const double* r0, i
     st->x_every_iter = 0;
     st->done = (tot[1] == 0.0 || maxit <= 0) ? 1 : 0;
     if (!isfinite(tot[0]) || !isfinite(tot[1])) st->done = 3;
+    prepare_iteration_scalars(st);
   }
 }
 

@@ -233,10 +233,28 @@ struct CGState {
   int maxit;
   int iterations;                  // finished iterations
   unsigned int ticket;             // last-CTA election counter
-  int x_every_iter;                // 1 once beta_{k-2} underflows: x updated every iteration
+  int x_every_iter;                // unused (kept for layout)
   int fixed;                       // 1: ignore the tolerance, run maxit iterations
   int pad;
+  // scalars of the next iteration, prepared once by the scalar step so that the
+  // tile kernels need no FP64 arithmetic: ratio = alpha_{k-2}/beta_{k-2} (0 unless
+  // k is odd and > 1), and float pairs (hi, lo) of -alpha_{k-1}, beta_{k-1},
+  // alpha_{k-1}, ratio
+  double ratio;
+  float sc[8];
 };
+
+// fills ratio and sc[] from alpha_prev, beta_prev, alpha_prev2, beta_prev2, k
+__host__ __device__ inline void prepare_iteration_scalars(CGState* st) {
+  const int k = st->k;
+  st->ratio = (k > 1 && (k & 1)) ? st->alpha_prev2 / st->beta_prev2 : 0.0;
+  const double v[4] = {-st->alpha_prev, st->beta_prev, st->alpha_prev, st->ratio};
+  for (int m = 0; m < 4; ++m) {
+    const float hi = (float)v[m];
+    st->sc[2 * m] = hi;
+    st->sc[2 * m + 1] = (float)(v[m] - (double)hi);
+  }
+}
 
 enum TileMode { MODE_OPERATOR = 0, MODE_CG = 1, MODE_RHS = 2, MODE_DIAG = 3 };
 

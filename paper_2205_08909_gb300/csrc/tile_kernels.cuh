@@ -30,6 +30,14 @@ namespace mfcg {
 // largest number of cells of one colour in a tile (tile edges <= 16 cells)
 constexpr int kMaxColorCells = 512;
 
+// Per-cell scratch stride (elements) for ns arrays of (P+1)^3 values, padded
+// so that stride = (P+1)^2 (mod 32): the pencils of consecutive threads then
+// map to consecutive banks across cell boundaries in the first sweep.
+__host__ __device__ constexpr int cell_stride(int P, int ns) {
+  return ns * (P + 1) * (P + 1) * (P + 1) +
+         ((((P + 1) * (P + 1) - ns * (P + 1) * (P + 1) * (P + 1)) % 32) + 32) % 32;
+}
+
 // ------------------------------------------------------------------------------------
 // 1D contractions on a pencil of N1 = P+1 values held in registers
 // ------------------------------------------------------------------------------------
@@ -209,7 +217,7 @@ template <int PREC, int P>
 __device__ void cell_op_affine(const OperatorCoeffs& c, const typename Num<PREC>::T* U, typename Num<PREC>::T* V,
                                typename Num<PREC>::T* S, int bx, int by, const ColorCells& cc) {
   using T = typename Num<PREC>::T;
-  constexpr int N1 = P + 1, N2 = N1 * N1, N3 = N2 * N1;
+  constexpr int N1 = P + 1, N2 = N1 * N1, N3 = N2 * N1, CS = cell_stride(P, 2);
   const int nc = cc.count();
   // z direction: s1 = M u, s2 = K_z u
   for (int t = threadIdx.x; t < nc * N2; t += kThreads) {
@@ -220,7 +228,7 @@ __device__ void cell_op_affine(const OperatorCoeffs& c, const typename Num<PREC>
     for (int s = 0; s < N1; ++s) x[s] = u0[s * bx * by];
     mv<PREC, N1, false>(c, MAT_M, x, y1);
     mv<PREC, N1, false>(c, MAT_K2, x, y2);
-    T* s1 = S + ci * 2 * N3;
+    T* s1 = S + ci * CS;
     T* s2 = s1 + N3;
 #pragma unroll
     for (int s = 0; s < N1; ++s) {
@@ -232,7 +240,7 @@ __device__ void cell_op_affine(const OperatorCoeffs& c, const typename Num<PREC>
   // y direction: s1 <- M s1, s2 <- K_y s1 + M s2
   for (int t = threadIdx.x; t < nc * N2; t += kThreads) {
     const int ci = t / N2, e = t - ci * N2, a = e % N1, cz = e / N1;
-    T* s1 = S + ci * 2 * N3;
+    T* s1 = S + ci * CS;
     T* s2 = s1 + N3;
     T m[N1], k[N1], y1[N1], y2[N1];
 #pragma unroll
@@ -252,7 +260,7 @@ __device__ void cell_op_affine(const OperatorCoeffs& c, const typename Num<PREC>
   // x direction: out = K_x s1 + M s2, added into V
   for (int t = threadIdx.x; t < nc * N2; t += kThreads) {
     const int ci = t / N2, e = t - ci * N2, b = e % N1, cz = e / N1;
-    const T* s1 = S + ci * 2 * N3;
+    const T* s1 = S + ci * CS;
     const T* s2 = s1 + N3;
     T m[N1], k[N1], y[N1];
 #pragma unroll
@@ -279,7 +287,7 @@ __device__ void cell_op_deformed(const OperatorCoeffs& c, const typename Num<PRE
   using T = typename Num<PREC>::T;
   constexpr int N1 = P + 1, N2 = N1 * N1, N3 = N2 * N1;
   const int nc = cc.count();
-  const int stride = 4 * N3;
+  const int stride = cell_stride(P, 4);
   // gather u into s0
   for (int t = threadIdx.x; t < nc * N3; t += kThreads) {
     const int ci = t / N3, e = t - ci * N3, a = e % N1, b = (e / N1) % N1, cz = e / N2;
@@ -441,7 +449,12 @@ __device__ void cell_diag(const OperatorCoeffs& c, double* V, double* S, int bx,
 }
 
 // ------------------------------------------------------------------------------------
-// Block reduction of NV doubles in a fixed order (warp shuffles, then warps in order)
+// Reductions of the seven sums, in a fixed order.  FP64 precision: FP64
+// throughout.  Double-float and FP32 precisions: the per-thread partial sums,
+// the warp and CTA stages and the grid stage are double-float pairs (FP32
+// pipes); only the final seven values are converted to FP64, because on GB300
+// a handful of FP64 operations per thread serialises on the FP64 pipe.
+// Per-CTA rows of `partial` hold 8 doubles (FP64) or 7 float pairs.
 // ------------------------------------------------------------------------------------
 template <int NV>
 __device__ __forceinline__ void block_reduce(double (&v)[NV], double* red) {
@@ -465,6 +478,96 @@ __device__ __forceinline__ void block_reduce(double (&v)[NV], double* red) {
     }
   }
   __syncthreads();
+}
+
+__device__ __forceinline__ dd dd_shfl_down(dd a, int o) {
+  return dd{__shfl_down_sync(0xffffffffu, a.hi, o), __shfl_down_sync(0xffffffffu, a.lo, o)};
+}
+
+// block sum of 7 double-float values; result valid in thread 0; red >= 56 dd
+__device__ __forceinline__ void block_reduce_dd(dd (&v)[7], dd* red) {
+#pragma unroll
+  for (int m = 0; m < 7; ++m) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[m] = dd_add(v[m], dd_shfl_down(v[m], o));
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+#pragma unroll
+    for (int m = 0; m < 7; ++m) red[warp * 7 + m] = v[m];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int m = 0; m < 7; ++m) {
+      dd s = red[m];
+      for (int w = 1; w < kThreads / 32; ++w) s = dd_add(s, red[w * 7 + m]);
+      v[m] = s;
+    }
+  }
+  __syncthreads();
+}
+
+template <int PREC>
+__device__ __forceinline__ dd dot_to_dd(const DotAcc<PREC>& a) {
+  if constexpr (PREC == PREC_DD)
+    return acc_get(a.a);
+  else
+    return dd{(float)a.v, 0.f};
+}
+
+// stores this CTA's seven sums into row `row` of the partial buffer
+template <int PREC>
+__device__ __forceinline__ void store_cta_sums(DotAcc<PREC> (&sm)[7], double* red, double* partial, int64_t row) {
+  if constexpr (PREC == PREC_F64) {
+    double s[7];
+#pragma unroll
+    for (int m = 0; m < 7; ++m) s[m] = sm[m].get();
+    block_reduce<7>(s, red);
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int m = 0; m < 7; ++m) partial[row * 8 + m] = s[m];
+    }
+  } else {
+    dd s[7];
+#pragma unroll
+    for (int m = 0; m < 7; ++m) s[m] = dot_to_dd<PREC>(sm[m]);
+    block_reduce_dd(s, reinterpret_cast<dd*>(red));
+    if (threadIdx.x == 0) {
+      dd* out = reinterpret_cast<dd*>(partial + row * 8);
+#pragma unroll
+      for (int m = 0; m < 7; ++m) out[m] = s[m];
+    }
+  }
+}
+
+// fixed-order sum of rows [0, nrows) of the partial buffer; valid in thread 0
+template <int PREC>
+__device__ __forceinline__ void reduce_partials(const double* partial, int64_t nrows, double* red, double (&out)[7]) {
+  if constexpr (PREC == PREC_F64) {
+#pragma unroll
+    for (int m = 0; m < 7; ++m) out[m] = 0.0;
+    for (int64_t t = threadIdx.x; t < nrows; t += kThreads) {
+#pragma unroll
+      for (int m = 0; m < 7; ++m) out[m] += __ldcg(partial + t * 8 + m);
+    }
+    block_reduce<7>(out, red);
+  } else {
+    dd s[7];
+#pragma unroll
+    for (int m = 0; m < 7; ++m) s[m] = dd{0.f, 0.f};
+    for (int64_t t = threadIdx.x; t < nrows; t += kThreads) {
+      const float2* row = reinterpret_cast<const float2*>(partial + t * 8);
+#pragma unroll
+      for (int m = 0; m < 7; ++m) {
+        const float2 v = __ldcg(row + m);
+        s[m] = dd_add(s[m], dd{v.x, v.y});
+      }
+    }
+    block_reduce_dd(s, reinterpret_cast<dd*>(red));
+#pragma unroll
+    for (int m = 0; m < 7; ++m) out[m] = dd_to_double(s[m]);
+  }
 }
 
 // accumulate the seven sums of Algorithm 5 for one finalised node
@@ -513,12 +616,24 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a, const 
   if constexpr (MODE == MODE_CG) {
     const CGState* st = a.state;
     if (st->done) return;
-    alpha_m = t_from_double<PREC>(-st->alpha_prev);
-    beta_t = t_from_double<PREC>(st->beta_prev);
     const int k = st->k;
     xupd = (k > 1) && (k & 1);
-    xa = t_from_double<PREC>(st->alpha_prev);
-    xr = t_from_double<PREC>(xupd ? st->alpha_prev2 / st->beta_prev2 : 0.0);
+    if constexpr (PREC == PREC_F64) {
+      alpha_m = -st->alpha_prev;
+      beta_t = st->beta_prev;
+      xa = st->alpha_prev;
+      xr = st->ratio;
+    } else if constexpr (PREC == PREC_DD) {
+      alpha_m = dd{st->sc[0], st->sc[1]};
+      beta_t = dd{st->sc[2], st->sc[3]};
+      xa = dd{st->sc[4], st->sc[5]};
+      xr = dd{st->sc[6], st->sc[7]};
+    } else {
+      alpha_m = st->sc[0];
+      beta_t = st->sc[2];
+      xa = st->sc[4];
+      xr = st->sc[6];
+    }
   }
 
   const int64_t tile = blockIdx.x;
@@ -540,37 +655,101 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a, const 
   T* V = U + Bmax;
   T* S = U + 2 * Bmax;
 
+  // Node loops.  A tile's brick = its owned block (contiguous in the
+  // tile-blocked vector: index base + o) plus the "+" faces owned by the next
+  // tiles.  Dirichlet tests only in tiles that touch the domain boundary.
+  const bool bnd_tile = tx == 0 || ty == 0 || tz == 0 || lastx || lasty || lastz;
+  const int n_own = ox * oy * oz;
+  const FastDiv fox = make_fastdiv((uint32_t)ox), foxy = make_fastdiv((uint32_t)(ox * oy));
+  const FastDiv fby = make_fastdiv((uint32_t)by);
+  const int nfx = lastx ? 0 : by * bz, nfy = lasty ? 0 : ox * bz, nfz = lastz ? 0 : ox * oy;
+  const int n_face = nfx + nfy + nfz;
+  // (li, lj, lk) of owned node o
+  auto own_coords = [&](int o, int& li, int& lj, int& lk) {
+    lk = (int)fdiv((uint32_t)o, foxy);
+    const int rem = o - lk * ox * oy;
+    lj = (int)fdiv((uint32_t)rem, fox);
+    li = rem - lj * ox;
+  };
+  // (li, lj, lk) of "+" face node f
+  auto face_coords = [&](int f, int& li, int& lj, int& lk) {
+    if (f < nfx) {
+      li = ox;
+      lk = (int)fdiv((uint32_t)f, fby);
+      lj = f - lk * by;
+    } else if (f < nfx + nfy) {
+      f -= nfx;
+      lj = oy;
+      lk = (int)fdiv((uint32_t)f, fox);
+      li = f - lk * ox;
+    } else {
+      f -= nfx + nfy;
+      lk = oz;
+      lj = (int)fdiv((uint32_t)f, fox);
+      li = f - lj * ox;
+    }
+  };
+
   // ---------------- phase 1: pre ----------------
-  for (int n = threadIdx.x; n < bsize; n += kThreads) {
-    const int lk = (int)fdiv((uint32_t)n, fbxy);
-    const int rem = n - lk * bx * by;
-    const int lj = (int)fdiv((uint32_t)rem, fbx);
-    const int li = rem - lj * bx;
-    const int i = gi0 + li, j = gj0 + lj, k = gk0 + lk;
+  // NB nodes per thread are loaded before any is used, so that each thread
+  // keeps several independent global loads in flight.
+  constexpr int NB = PREC == PREC_F32 ? 4 : 2;
+  for (int n0 = threadIdx.x; n0 < n_own + n_face; n0 += NB * kThreads) {
+    int64_t gi[NB];
+    int sidx[NB];
+    bool ok[NB], own[NB], dir[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const int n = n0 + b * kThreads;
+      ok[b] = n < n_own + n_face;
+      own[b] = n < n_own;
+      int li, lj, lk;
+      if (own[b]) {
+        own_coords(n, li, lj, lk);
+        gi[b] = base + n;
+      } else {
+        face_coords(ok[b] ? n - n_own : 0, li, lj, lk);
+        gi[b] = ok[b] ? brick_global_index(g, tx, ty, tz, li, lj, lk, ox, oy, oz, base) : base;
+      }
+      sidx[b] = li + bx * (lj + by * lk);
+      dir[b] = bnd_tile && is_dirichlet(g, gi0 + li, gj0 + lj, gk0 + lk);
+    }
     if constexpr (MODE == MODE_OPERATOR) {
-      const bool dir = is_dirichlet(g, i, j, k);
-      const int64_t gi = brick_global_index(g, tx, ty, tz, li, lj, lk, ox, oy, oz, base);
-      U[n] = dir ? t_zero<PREC>() : t_from_double<PREC>(static_cast<const double*>(a.in0)[gi]);
+      double src[NB];
+#pragma unroll
+      for (int b = 0; b < NB; ++b) src[b] = static_cast<const double*>(a.in0)[gi[b]];
+#pragma unroll
+      for (int b = 0; b < NB; ++b)
+        if (ok[b]) U[sidx[b]] = dir[b] ? t_zero<PREC>() : t_from_double<PREC>(src[b]);
     } else if constexpr (MODE == MODE_CG) {
-      const bool dir = is_dirichlet(g, i, j, k);
-      const int64_t gi = brick_global_index(g, tx, ty, tz, li, lj, lk, ox, oy, oz, base);
-      const T r_o = static_cast<const T*>(a.in0)[gi], v_o = static_cast<const T*>(a.in1)[gi];
-      const T p_o = static_cast<const T*>(a.in2)[gi], dinv = static_cast<const T*>(a.diag_inv)[gi];
-      const T rk = t_axpy<PREC>(alpha_m, v_o, r_o);       // r_{k-1} - alpha_{k-1} v_{k-1}
-      const T pk = t_axby<PREC>(dinv, rk, beta_t, p_o);   // M^{-1} r_k + beta_{k-1} p_{k-1}
-      U[n] = dir ? t_zero<PREC>() : pk;
-      const bool owned = li < ox && lj < oy && lk < oz;
-      if (owned) {
-        static_cast<T*>(a.out0)[gi] = rk;
-        static_cast<T*>(a.out2)[gi] = pk;
-        if (xupd) {
-          T* x = static_cast<T*>(a.x);
-          const T dp = t_sub<PREC>(p_o, t_mul<PREC>(dinv, r_o));  // p_{k-1} - M^{-1} r_{k-1}
-          x[gi] = t_add<PREC>(x[gi], t_axby<PREC>(xa, p_o, xr, dp));
+      T r_o[NB], v_o[NB], p_o[NB], dinv[NB];
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        r_o[b] = static_cast<const T*>(a.in0)[gi[b]];
+        v_o[b] = static_cast<const T*>(a.in1)[gi[b]];
+        p_o[b] = static_cast<const T*>(a.in2)[gi[b]];
+        dinv[b] = static_cast<const T*>(a.diag_inv)[gi[b]];
+      }
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        if (!ok[b]) continue;
+        const T rk = t_axpy<PREC>(alpha_m, v_o[b], r_o[b]);          // r_{k-1} - alpha_{k-1} v_{k-1}
+        const T pk = t_axby<PREC>(dinv[b], rk, beta_t, p_o[b]);      // M^{-1} r_k + beta_{k-1} p_{k-1}
+        U[sidx[b]] = dir[b] ? t_zero<PREC>() : pk;
+        if (own[b]) {
+          static_cast<T*>(a.out0)[gi[b]] = rk;
+          static_cast<T*>(a.out2)[gi[b]] = pk;
+          if (xupd) {
+            T* x = static_cast<T*>(a.x);
+            const T dp = t_sub<PREC>(p_o[b], t_mul<PREC>(dinv[b], r_o[b]));  // p_{k-1} - M^{-1} r_{k-1}
+            x[gi[b]] = t_add<PREC>(x[gi[b]], t_axby<PREC>(xa, p_o[b], xr, dp));
+          }
         }
       }
     }
-    V[n] = t_zero<PREC>();
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+      if (ok[b]) V[sidx[b]] = t_zero<PREC>();
   }
 
   // ---------------- phase 2: cell integrals, one colour at a time ----------------
@@ -588,9 +767,9 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a, const 
     __syncthreads();
     const ColorCells cc{nc, s_org, s_cell};
     if constexpr (MODE == MODE_RHS) {
-      cell_rhs<P>(c, V, S, bx, by, cc, g, (GEOM == GEOM_AFFINE ? 2 : 4) * N3);
+      cell_rhs<P>(c, V, S, bx, by, cc, g, cell_stride(P, GEOM == GEOM_AFFINE ? 2 : 4));
     } else if constexpr (MODE == MODE_DIAG) {
-      cell_diag<P, GEOM>(c, V, S, bx, by, cc, static_cast<const double*>(a.geo), (GEOM == GEOM_AFFINE ? 2 : 4) * N3);
+      cell_diag<P, GEOM>(c, V, S, bx, by, cc, static_cast<const double*>(a.geo), cell_stride(P, GEOM == GEOM_AFFINE ? 2 : 4));
     } else if constexpr (GEOM == GEOM_AFFINE) {
       cell_op_affine<PREC, P>(c, U, V, S, bx, by, cc);
     } else {
@@ -599,49 +778,70 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a, const 
   }
 
   // ---------------- phase 3: post ----------------
+  // Owned nodes on the "-" faces of a tile with a lower neighbour, and all
+  // non-Dirichlet "+" face nodes, are shared: their partial sums go to the
+  // shell; the other owned nodes are final.
   DotAcc<PREC> sm[7];
   T* shell = static_cast<T*>(a.shell);
-  for (int n = threadIdx.x; n < bsize; n += kThreads) {
-    const int lk = (int)fdiv((uint32_t)n, fbxy);
-    const int rem = n - lk * bx * by;
-    const int lj = (int)fdiv((uint32_t)rem, fbx);
-    const int li = rem - lj * bx;
-    const int i = gi0 + li, j = gj0 + lj, k = gk0 + lk;
-    const bool dir = is_dirichlet(g, i, j, k);
-    const bool shared = !dir && ((li == 0 && tx > 0) || (li == bx - 1 && !lastx) || (lj == 0 && ty > 0) ||
-                                 (lj == by - 1 && !lasty) || (lk == 0 && tz > 0) || (lk == bz - 1 && !lastz));
-    if (shared) {
-      shell[tile * g.face_stride + shell_slot(g, li, lj, lk, bx, by, bz)] = V[n];
-      continue;
+  for (int n0 = threadIdx.x; n0 < n_own + n_face; n0 += NB * kThreads) {
+    int64_t gi[NB];
+    int sidx[NB];
+    bool fin[NB], dir[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const int n = n0 + b * kThreads;
+      fin[b] = false;
+      gi[b] = base;
+      sidx[b] = 0;
+      dir[b] = false;
+      if (n >= n_own + n_face) continue;
+      int li, lj, lk;
+      const bool own = n < n_own;
+      if (own)
+        own_coords(n, li, lj, lk);
+      else
+        face_coords(n - n_own, li, lj, lk);
+      sidx[b] = li + bx * (lj + by * lk);
+      dir[b] = bnd_tile && is_dirichlet(g, gi0 + li, gj0 + lj, gk0 + lk);
+      const bool shared = !dir[b] && (!own || (li == 0 && tx > 0) || (lj == 0 && ty > 0) || (lk == 0 && tz > 0));
+      if (shared) {
+        shell[tile * g.face_stride + shell_slot(g, li, lj, lk, bx, by, bz)] = V[sidx[b]];
+      } else if (own) {
+        fin[b] = true;
+        gi[b] = base + n;
+      }
     }
-    const bool owned = li < ox && lj < oy && lk < oz;
-    if (!owned) continue;
-    const int64_t gi = base + li + (int64_t)ox * (lj + (int64_t)oy * lk);
-    if constexpr (MODE == MODE_OPERATOR) {
-      const double* src = static_cast<const double*>(a.in0);
-      static_cast<double*>(a.out0)[gi] = dir ? src[gi] : t_to_double<PREC>(V[n]);
-    } else if constexpr (MODE == MODE_RHS) {
-      static_cast<double*>(a.out0)[gi] = dir ? 0.0 : t_to_double<PREC>(V[n]);
-    } else if constexpr (MODE == MODE_DIAG) {
-      static_cast<double*>(a.out0)[gi] = dir ? 1.0 : t_to_double<PREC>(V[n]);
+    if constexpr (MODE == MODE_CG) {
+      T rk[NB], dv[NB], pd[NB];
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        rk[b] = static_cast<const T*>(a.out0)[gi[b]];
+        dv[b] = static_cast<const T*>(a.diag_inv)[gi[b]];
+        pd[b] = static_cast<const T*>(a.out2)[gi[b]];
+      }
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        if (!fin[b]) continue;
+        const T pk = dir[b] ? pd[b] : U[sidx[b]];
+        const T v = dir[b] ? pk : V[sidx[b]];
+        static_cast<T*>(a.out1)[gi[b]] = v;
+        post_sums<PREC>(sm, rk[b], pk, v, dv[b]);
+      }
     } else {
-      const T pk = dir ? static_cast<const T*>(a.out2)[gi] : U[n];
-      const T v = dir ? pk : V[n];
-      const T rk = static_cast<const T*>(a.out0)[gi];
-      static_cast<T*>(a.out1)[gi] = v;
-      post_sums<PREC>(sm, rk, pk, v, static_cast<const T*>(a.diag_inv)[gi]);
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        if (!fin[b]) continue;
+        double* out = static_cast<double*>(a.out0);
+        if constexpr (MODE == MODE_OPERATOR)
+          out[gi[b]] = dir[b] ? static_cast<const double*>(a.in0)[gi[b]] : t_to_double<PREC>(V[sidx[b]]);
+        else if constexpr (MODE == MODE_RHS)
+          out[gi[b]] = dir[b] ? 0.0 : t_to_double<PREC>(V[sidx[b]]);
+        else
+          out[gi[b]] = dir[b] ? 1.0 : t_to_double<PREC>(V[sidx[b]]);
+      }
     }
   }
-  if constexpr (MODE == MODE_CG) {
-    double s[7];
-#pragma unroll
-    for (int m = 0; m < 7; ++m) s[m] = sm[m].get();
-    block_reduce<7>(s, red);
-    if (threadIdx.x == 0) {
-#pragma unroll
-      for (int m = 0; m < 7; ++m) a.partial[tile * 8 + m] = s[m];
-    }
-  }
+  if constexpr (MODE == MODE_CG) store_cta_sums<PREC>(sm, red, a.partial, tile);
 }
 
 // ------------------------------------------------------------------------------------
@@ -682,6 +882,7 @@ __device__ inline void cg_scalar_step(CGState* st, const double (&s)[7]) {
   st->alpha_prev = alpha;
   st->beta_prev = beta;
   st->k = k + 1;
+  prepare_iteration_scalars(st);
 }
 
 template <int P, int MODE, int PREC>
@@ -719,13 +920,8 @@ __global__ void __launch_bounds__(kThreads) tail_kernel(const TileArgs a) {
     }
   }
   if constexpr (MODE == MODE_CG) {
-    double s7[7];
-#pragma unroll
-    for (int m = 0; m < 7; ++m) s7[m] = sm[m].get();
-    block_reduce<7>(s7, red);
-    double* tail_partial = a.partial + a.g.n_tiles * 8;
+    store_cta_sums<PREC>(sm, red, a.partial, a.g.n_tiles + blockIdx.x);
     if (threadIdx.x == 0) {
-      for (int m = 0; m < 7; ++m) tail_partial[blockIdx.x * 8 + m] = s7[m];
       __threadfence();
       const unsigned prev = atomicAdd(&a.state->ticket, 1u);
       is_last = (prev == gridDim.x - 1);
@@ -733,14 +929,9 @@ __global__ void __launch_bounds__(kThreads) tail_kernel(const TileArgs a) {
     __syncthreads();
     if (!is_last) return;
     __threadfence();
-    // last CTA: fixed-order reduction of all per-CTA sums
-    const int64_t nparts = a.g.n_tiles + gridDim.x;
-    double s[7] = {0, 0, 0, 0, 0, 0, 0};
-    for (int64_t t = threadIdx.x; t < nparts; t += kThreads) {
-#pragma unroll
-      for (int m = 0; m < 7; ++m) s[m] += __ldcg(a.partial + t * 8 + m);
-    }
-    block_reduce<7>(s, red);
+    // last CTA: fixed-order reduction of all per-CTA sums, then the scalar step
+    double s[7];
+    reduce_partials<PREC>(a.partial, a.g.n_tiles + gridDim.x, red, s);
     if (threadIdx.x == 0) {
       cg_scalar_step(a.state, s);
       a.state->ticket = 0u;
@@ -754,8 +945,7 @@ __global__ void __launch_bounds__(kThreads) tail_kernel(const TileArgs a) {
 inline size_t tile_smem_elems(int P, int geom, const TileGeom& g) {
   const size_t Bmax = (size_t)(P * g.T[0] + 1) * (P * g.T[1] + 1) * (P * g.T[2] + 1);
   const size_t cpc = (size_t)((g.T[0] + 1) / 2) * ((g.T[1] + 1) / 2) * ((g.T[2] + 1) / 2);
-  const size_t n3 = (size_t)(P + 1) * (P + 1) * (P + 1);
-  return 2 * Bmax + cpc * (geom == GEOM_AFFINE ? 2 : 4) * n3;
+  return 2 * Bmax + cpc * (size_t)cell_stride(P, geom == GEOM_AFFINE ? 2 : 4);
 }
 
 template <int P>
