@@ -589,6 +589,19 @@ __device__ __forceinline__ void post_sums(DotAcc<PREC> (&sm)[7], typename Num<PR
 // ------------------------------------------------------------------------------------
 // The tile kernel
 // ------------------------------------------------------------------------------------
+// 16-byte loads and stores of VN = 16 / sizeof(T) consecutive values
+template <typename T>
+__device__ __forceinline__ void ld16(const T* p, T (&v)[16 / sizeof(T)]) {
+  const float4 raw = *reinterpret_cast<const float4*>(p);
+  memcpy(&v[0], &raw, 16);
+}
+template <typename T>
+__device__ __forceinline__ void st16(T* p, const T (&v)[16 / sizeof(T)]) {
+  float4 raw;
+  memcpy(&raw, &v[0], 16);
+  *reinterpret_cast<float4*>(p) = raw;
+}
+
 // position in the tile-blocked vector of brick node (li, lj, lk) of tile
 // (tx, ty, tz) whose own block starts at `base` with extents (ox, oy, oz);
 // nodes past the owned extent belong to the next tile along that direction
@@ -608,7 +621,6 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a, const 
   __shared__ double red[8 * (kThreads / 32)];
   __shared__ int s_org[kMaxColorCells];
   __shared__ int s_cell[kMaxColorCells];
-  constexpr int N1 = P + 1, N3 = N1 * N1 * N1;
   const TileGeom& g = a.g;
 
   T alpha_m = t_zero<PREC>(), beta_t = t_zero<PREC>(), xa = t_zero<PREC>(), xr = t_zero<PREC>();
@@ -643,13 +655,11 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a, const 
   const int cx0 = tx * g.T[0], cy0 = ty * g.T[1], cz0 = tz * g.T[2];
   const int ncx = min(g.T[0], g.N[0] - cx0), ncy = min(g.T[1], g.N[1] - cy0), ncz = min(g.T[2], g.N[2] - cz0);
   const int bx = P * ncx + 1, by = P * ncy + 1, bz = P * ncz + 1;
-  const int bsize = bx * by * bz;
   const int Bmax = (P * g.T[0] + 1) * (P * g.T[1] + 1) * (P * g.T[2] + 1);
   const int gi0 = P * cx0, gj0 = P * cy0, gk0 = P * cz0;
   const bool lastx = tx == g.nt[0] - 1, lasty = ty == g.nt[1] - 1, lastz = tz == g.nt[2] - 1;
   const int ox = owned_count(g, 0, tx), oy = owned_count(g, 1, ty), oz = owned_count(g, 2, tz);
   const int64_t base = tile_base(g, tx, ty, tz);
-  const FastDiv fbx = make_fastdiv((uint32_t)bx), fbxy = make_fastdiv((uint32_t)(bx * by));
 
   T* U = reinterpret_cast<T*>(smem_raw);
   T* V = U + Bmax;
@@ -691,10 +701,72 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a, const 
   };
 
   // ---------------- phase 1: pre ----------------
-  // NB nodes per thread are loaded before any is used, so that each thread
-  // keeps several independent global loads in flight.
+  // CG mode: the owned block is processed in 16-byte chunks of VN nodes (it is
+  // contiguous and, when base and n_own are multiples of VN, aligned), two
+  // chunks per thread in flight; the remaining owned nodes and the "+" face
+  // nodes take the scalar path with NB nodes per thread in flight.
   constexpr int NB = PREC == PREC_F32 ? 4 : 2;
-  for (int n0 = threadIdx.x; n0 < n_own + n_face; n0 += NB * kThreads) {
+  constexpr int VN = 16 / sizeof(T);
+  const bool vec_ok = MODE == MODE_CG && (base % VN) == 0 && (n_own % VN) == 0;
+  const int n_chunks = vec_ok ? n_own / VN : 0;
+  const int scalar_begin = vec_ok ? n_own : 0;
+  if constexpr (MODE == MODE_CG) {
+    const T* r_old = static_cast<const T*>(a.in0) + base;
+    const T* v_old = static_cast<const T*>(a.in1) + base;
+    const T* p_old = static_cast<const T*>(a.in2) + base;
+    const T* dinv_o = static_cast<const T*>(a.diag_inv) + base;
+    T* r_new = static_cast<T*>(a.out0) + base;
+    T* p_new = static_cast<T*>(a.out2) + base;
+    T* x_o = static_cast<T*>(a.x) + base;
+    for (int c0 = threadIdx.x; c0 < n_chunks; c0 += 2 * kThreads) {
+      T r4[2][VN], v4[2][VN], p4[2][VN], d4[2][VN];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int c = min(c0 + h * kThreads, n_chunks - 1);
+        ld16(r_old + c * VN, r4[h]);
+        ld16(v_old + c * VN, v4[h]);
+        ld16(p_old + c * VN, p4[h]);
+        ld16(dinv_o + c * VN, d4[h]);
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int c = c0 + h * kThreads;
+        if (c >= n_chunks) continue;
+        T rk[VN], pk[VN];
+        int li, lj, lk;
+        own_coords(c * VN, li, lj, lk);
+#pragma unroll
+        for (int e = 0; e < VN; ++e) {
+          if (e > 0 && ++li == ox) {
+            li = 0;
+            if (++lj == oy) {
+              lj = 0;
+              ++lk;
+            }
+          }
+          rk[e] = t_axpy<PREC>(alpha_m, v4[h][e], r4[h][e]);        // r_{k-1} - alpha_{k-1} v_{k-1}
+          pk[e] = t_axby<PREC>(d4[h][e], rk[e], beta_t, p4[h][e]);  // M^{-1} r_k + beta_{k-1} p_{k-1}
+          const int sidx = li + bx * (lj + by * lk);
+          const bool dir = bnd_tile && is_dirichlet(g, gi0 + li, gj0 + lj, gk0 + lk);
+          U[sidx] = dir ? t_zero<PREC>() : pk[e];
+          V[sidx] = t_zero<PREC>();
+        }
+        st16(r_new + c * VN, rk);
+        st16(p_new + c * VN, pk);
+        if (xupd) {
+          T xv[VN];
+          ld16(x_o + c * VN, xv);
+#pragma unroll
+          for (int e = 0; e < VN; ++e) {
+            const T dp = t_sub<PREC>(p4[h][e], t_mul<PREC>(d4[h][e], r4[h][e]));  // p_{k-1} - M^{-1} r_{k-1}
+            xv[e] = t_add<PREC>(xv[e], t_axby<PREC>(xa, p4[h][e], xr, dp));
+          }
+          st16(x_o + c * VN, xv);
+        }
+      }
+    }
+  }
+  for (int n0 = scalar_begin + threadIdx.x; n0 < n_own + n_face; n0 += NB * kThreads) {
     int64_t gi[NB];
     int sidx[NB];
     bool ok[NB], own[NB], dir[NB];
@@ -780,10 +852,59 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a, const 
   // ---------------- phase 3: post ----------------
   // Owned nodes on the "-" faces of a tile with a lower neighbour, and all
   // non-Dirichlet "+" face nodes, are shared: their partial sums go to the
-  // shell; the other owned nodes are final.
+  // shell; the other owned nodes are final.  In the chunked path the value
+  // stored for a shared owned node is a placeholder that the tail kernel
+  // overwrites with the complete sum.
   DotAcc<PREC> sm[7];
   T* shell = static_cast<T*>(a.shell);
-  for (int n0 = threadIdx.x; n0 < n_own + n_face; n0 += NB * kThreads) {
+  if constexpr (MODE == MODE_CG) {
+    const T* r_k = static_cast<const T*>(a.out0) + base;
+    const T* p_k = static_cast<const T*>(a.out2) + base;
+    const T* dinv_o = static_cast<const T*>(a.diag_inv) + base;
+    T* v_new = static_cast<T*>(a.out1) + base;
+    for (int c0 = threadIdx.x; c0 < n_chunks; c0 += 2 * kThreads) {
+      T r4[2][VN], p4[2][VN], d4[2][VN];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int c = min(c0 + h * kThreads, n_chunks - 1);
+        ld16(r_k + c * VN, r4[h]);
+        ld16(p_k + c * VN, p4[h]);
+        ld16(dinv_o + c * VN, d4[h]);
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int c = c0 + h * kThreads;
+        if (c >= n_chunks) continue;
+        T vv[VN];
+        int li, lj, lk;
+        own_coords(c * VN, li, lj, lk);
+#pragma unroll
+        for (int e = 0; e < VN; ++e) {
+          if (e > 0 && ++li == ox) {
+            li = 0;
+            if (++lj == oy) {
+              lj = 0;
+              ++lk;
+            }
+          }
+          const int sidx = li + bx * (lj + by * lk);
+          const bool dir = bnd_tile && is_dirichlet(g, gi0 + li, gj0 + lj, gk0 + lk);
+          const bool shared = !dir && ((li == 0 && tx > 0) || (lj == 0 && ty > 0) || (lk == 0 && tz > 0));
+          const T vs = V[sidx];
+          if (shared) {
+            shell[tile * g.face_stride + shell_slot(g, li, lj, lk, bx, by, bz)] = vs;
+            vv[e] = vs;
+          } else {
+            const T pk = dir ? p4[h][e] : U[sidx];
+            vv[e] = dir ? pk : vs;
+            post_sums<PREC>(sm, r4[h][e], pk, vv[e], d4[h][e]);
+          }
+        }
+        st16(v_new + c * VN, vv);
+      }
+    }
+  }
+  for (int n0 = scalar_begin + threadIdx.x; n0 < n_own + n_face; n0 += NB * kThreads) {
     int64_t gi[NB];
     int sidx[NB];
     bool fin[NB], dir[NB];
