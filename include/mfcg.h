@@ -42,7 +42,9 @@ typedef enum mfcg_status {
   MFCG_CUDA_ERROR = 4,           /* a CUDA runtime call failed                        */
   MFCG_NOT_CONVERGED = 5,        /* maxit reached before the tolerance               */
   MFCG_BREAKDOWN = 6,            /* p^T A p <= 0, r^T M^-1 r <= 0 or a non-finite sum */
-  MFCG_DEVICE_TIMEOUT = 7        /* a bounded device-side wait gave up               */
+  MFCG_DEVICE_TIMEOUT = 7,       /* a bounded device-side wait gave up               */
+  MFCG_SCRATCH_TOO_SMALL = 8     /* the mesh needs more scratch than the fixed array of
+                                    mfcg_apply_operator_static holds                    */
 } mfcg_status;
 
 /* Mesh of Nx x Ny x Nz box cells on [0,1]^3.  amplitude A deforms the mesh by
@@ -175,6 +177,30 @@ int mfcg_from_lexicographic(mfcg_problem* prob, const double* in, double* out);
 
 /* mfcg_destroy -- frees every buffer the library owns; NULL is accepted. */
 int mfcg_destroy(mfcg_problem* prob);
+
+/* mfcg_apply_operator_static -- dst = A src like mfcg_apply_operator, for
+ * callers that cannot allocate device memory: programs whose device memory is
+ * handed to their own pool allocator at start-up, and loops that must not call
+ * cudaMalloc/cudaFree because those calls can synchronise the whole device.
+ * The paper has no counterpart; this is a service of the library.
+ *   mesh    in: Cartesian mesh only (amplitude 0, coefficient 1), any Nx, Ny, Nz.
+ *   degree  in: 1..8.
+ *   src, dst: device, n doubles in the tile-blocked order that mfcg_setup uses
+ *            with default options for the same mesh and degree (FP64); no overlap.
+ *   cuda_stream: stream of the launch (NULL = legacy default stream).
+ * The call allocates nothing: its only scratch, the partial sums of the nodes
+ * shared between tiles, lives in one fixed 16 MiB array of device memory that
+ * every GPU loading the library holds until the process exits.  Meshes whose
+ * scratch exceeds it (for example Q4 beyond about 42^3 cells, Q2 beyond 84^3)
+ * are rejected with MFCG_SCRATCH_TOO_SMALL before any GPU work.  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress) and
+ * sets the kernel's shared-memory limit; make that first call before any
+ * stream capture.  All calls share the array: calls that overlap on the GPU
+ * (concurrent streams, other host threads) race and give wrong results; every
+ * value read from the array is written earlier in the same call, so nothing
+ * needs clearing between calls.  Asynchronous on cuda_stream.  Errors:
+ * INVALID_ARG, UNSUPPORTED_DEGREE, SCRATCH_TOO_SMALL, CUDA_ERROR. */
+int mfcg_apply_operator_static(const mfcg_mesh* mesh, int degree, const double* src, double* dst, void* cuda_stream);
 
 /* mfcg_status_string -- static description of a status code. */
 const char* mfcg_status_string(int status);

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(PKG, "_lib", "libmfcg.so")
 HEADER = os.path.join(os.path.dirname(PKG), "include", "mfcg.h")
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED_DEGREE", 3: "OUT_OF_MEMORY", 4: "CUDA_ERROR",
-          5: "NOT_CONVERGED", 6: "BREAKDOWN", 7: "DEVICE_TIMEOUT"}
+          5: "NOT_CONVERGED", 6: "BREAKDOWN", 7: "DEVICE_TIMEOUT", 8: "SCRATCH_TOO_SMALL"}
 OK, NOT_CONVERGED, BREAKDOWN = 0, 5, 6
 
 GEOM = {"affine": 0, "deformed": 1}

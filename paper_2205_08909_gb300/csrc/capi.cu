@@ -471,6 +471,7 @@ const char* mfcg_status_string(int status) {
     case MFCG_NOT_CONVERGED: return "maximum number of iterations reached";
     case MFCG_BREAKDOWN: return "CG breakdown (non-positive or non-finite inner product)";
     case MFCG_DEVICE_TIMEOUT: return "bounded device wait expired";
+    case MFCG_SCRATCH_TOO_SMALL: return "mesh too large for the fixed scratch array of mfcg_apply_operator_static";
     default: return "unknown status";
   }
 }
