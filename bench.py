@@ -262,9 +262,14 @@ def run_ours(args, world, rank, local):
     main_prec = args.precision
 
     tile = tuple(int(t) for t in args.tile.split(",")) if args.tile else None
+    geometry = w.geometry
+    if args.geometry:
+        if w.geometry == "affine":
+            raise SystemExit("--geometry applies to deformed workloads only")
+        geometry = args.geometry
 
     def make(mode, precision, instrument=False):
-        return mfcg.Problem(w.degree, w.cells, amplitude=w.amplitude, geometry=w.geometry,
+        return mfcg.Problem(w.degree, w.cells, amplitude=w.amplitude, geometry=geometry,
                             coefficient=w.coefficient, mode=mode, precision=precision, instrument=instrument,
                             tile=tile)
 
@@ -363,7 +368,7 @@ def run_ours(args, world, rank, local):
         achieved = hbm_gbs / 2  # FP32 storage: 32 B per unknown
         roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                     "frac": round(achieved / hbm, 4), "traffic": traffic, "peak_kind": peak_kind}
-    roofline.update({"kernel": f"tile_kernel<{w.degree}, MODE_CG, GEOM_{w.geometry.upper()}, {main_prec}>",
+    roofline.update({"kernel": f"tile_kernel<{w.degree}, MODE_CG, GEOM_{ {'affine': 'AFFINE', 'deformed': 'DEFORMED', 'deformed_tensor': 'TENSOR'}[geometry]}, {main_prec}>",
                      "kernel_ms": round(kernel_ms, 4),
                      "hbm_view": {"achieved_gbs": round(hbm_gbs, 1), "peak_gbs": hbm, "peak_kind": peak_kind,
                                   "frac": round(hbm_gbs / hbm, 4)}})
@@ -394,7 +399,7 @@ def run_ours(args, world, rank, local):
         "dtype": dtype,
         "data": "synthetic: manufactured right-hand side of u = sin(pi x) sin(pi y) sin(pi z), x0 = 0",
         "config": {"workload": w.name, "degree": w.degree, "cells": list(w.cells), "n_dofs": w.n_dofs,
-                   "geometry": w.geometry, "precision": main_prec, "iterations_per_step": iters,
+                   "geometry": geometry, "precision": main_prec, "iterations_per_step": iters,
                    "tile": list(tile) if tile else "default",
                    "parallelism": f"replicas x{world}",
                    "l2": f"inputs larger than L2: {8 * w.n_dofs / 1e6:.0f} MB per vector, 8 vectors"},
@@ -432,6 +437,8 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-dc", action="store_true", help="skip the FP32-inner defect-correction solve")
     ap.add_argument("--skip-variants", action="store_true", help="skip the FP64 comparators")
+    ap.add_argument("--geometry", default="", choices=["", "deformed", "deformed_tensor"],
+                    help="storage of the deformed map: J^{-1} and JxW (10 values per point) or the final tensor (6)")
     ap.add_argument("--tile", default="", help="cells per tile, e.g. 4,4,2 (default: chosen from the degree)")
     ap.add_argument("--precision", default="double_float", choices=["fp64", "double_float", "fp32_inner"],
                     help="arithmetic of the headline fused path")

@@ -57,8 +57,10 @@ typedef struct mfcg_mesh {
 
 typedef enum mfcg_geometry_kind {
   MFCG_GEOM_AFFINE = 0,     /* constant Jacobian per cell (Cartesian box cells), Sec. 2.2 "affine" variant */
-  MFCG_GEOM_DEFORMED = 1    /* per-quadrature-point inverse Jacobian and JxW stored in FP64, Sec. 2.2
-                               "inverse Jacobian load" variant                                             */
+  MFCG_GEOM_DEFORMED = 1,   /* per-quadrature-point inverse Jacobian and JxW stored in FP64, Sec. 2.2
+                               "inverse Jacobian load" variant (10 values per point)                        */
+  MFCG_GEOM_DEFORMED_TENSOR = 2  /* the same mesh with the symmetric tensor J^{-1} (w det J a) J^{-T}
+                               stored per point, Sec. 2.2 "final tensor load" variant (6 values per point) */
 } mfcg_geometry_kind;
 
 typedef enum mfcg_coefficient_kind {
@@ -73,8 +75,15 @@ typedef struct mfcg_geometry {
 
 typedef enum mfcg_mode {
   MFCG_MODE_FUSED = 0,      /* Algorithm 5 with pre/post inside the operator pass (Sec. 5)        */
-  MFCG_MODE_UNFUSED = 1     /* Algorithm 1 with a separate operator, axpy, Jacobi and dot kernel   */
+  MFCG_MODE_UNFUSED = 1,    /* Algorithm 1 with a separate operator, axpy, Jacobi and dot kernel   */
+  MFCG_MODE_SEMI_FUSED = 2  /* Algorithm 5 as separate "pre", operator and "post" kernels, the GPU
+                               form of Sec. 6.4; FP64 vectors                                      */
 } mfcg_mode;
+
+typedef enum mfcg_preconditioner {
+  MFCG_PRECOND_JACOBI = 0,  /* M = diag(A) (Sec. 3, Algorithm 5)                                   */
+  MFCG_PRECOND_NONE = 1     /* M = I: Algorithm 5 reduces to the merged CG of Algorithm 4 (Sec. 4.1) */
+} mfcg_preconditioner;
 
 /* Arithmetic of the operator and of the CG vectors.  The ABI is FP64 in every case. */
 typedef enum mfcg_precision {
@@ -94,7 +103,7 @@ typedef struct mfcg_options {
                                CUDA events (mfcg_solve_info.main_kernel_ms); 0: graphs, no timing      */
   int32_t tile[3];          /* cells per tile and direction; 0 = chosen from the degree               */
   int32_t precision;        /* mfcg_precision                                                       */
-  int32_t reserved;         /* must be zero                                                          */
+  int32_t preconditioner;   /* mfcg_preconditioner                                                  */
   double inner_rtol;        /* MFCG_PREC_FP32_INNER: residual reduction of each inner solve (0 = 1e-3) */
 } mfcg_options;
 
@@ -122,7 +131,7 @@ typedef struct mfcg_problem mfcg_problem;
  *   cuda_stream   in: cudaStream_t (NULL = legacy default stream) used by every call.
  *   out           out: new handle; release with mfcg_destroy.
  * Errors: INVALID_ARG (cells < 1, |amplitude| >= 0.1, affine kind with A != 0 or
- * a != 1, bad enums, FP32_INNER with UNFUSED), UNSUPPORTED_DEGREE,
+ * a != 1, bad enums, FP32_INNER without FUSED, SEMI_FUSED with FP32_INNER), UNSUPPORTED_DEGREE,
  * OUT_OF_MEMORY, CUDA_ERROR. */
 int mfcg_setup(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, const mfcg_options* opt,
                void* cuda_stream, mfcg_problem** out);
@@ -147,7 +156,7 @@ int mfcg_diagonal(mfcg_problem* prob, double* diag);
 int mfcg_rhs(mfcg_problem* prob, double* b);
 
 /* mfcg_cg_solve -- Jacobi-preconditioned CG from the initial guess in x
- * (Algorithm 5 in FUSED mode, Algorithm 1 in UNFUSED mode) until
+ * (Algorithm 5 in FUSED and SEMI_FUSED modes, Algorithm 1 in UNFUSED mode) until
  * ||r_k|| < rtol ||b|| (unpreconditioned residual, Sec. 3.1) or maxit products
  * A p.  rtol == 0 runs exactly maxit iterations and returns MFCG_OK.  With
  * MFCG_PREC_FP32_INNER the solve stops on the true residual ||b - A x|| <

@@ -32,9 +32,13 @@ class Problem:
     """One Q_p Poisson problem on the unit cube, set up on the current CUDA device.
 
     degree: 1..8; cells: (Nx, Ny, Nz); amplitude: sine deformation of the mesh
-    (needs geometry="deformed"); coefficient: "constant" (a = 1) or "sin_x"
+    (needs geometry="deformed", which stores J^{-1} and JxW per quadrature
+    point, or "deformed_tensor", which stores the symmetric J^{-1} JxW a J^{-T});
+    coefficient: "constant" (a = 1) or "sin_x"
     (a = 1 + 0.5 sin(pi x)); mode: "fused" (Algorithm 5 inside the operator
-    pass) or "unfused" (Algorithm 1, one kernel per vector operation);
+    pass), "unfused" (Algorithm 1, one kernel per vector operation) or
+    "semi_fused" (Algorithm 5 as separate pre / operator / post kernels);
+    preconditioner: "jacobi" or "none" (Algorithm 4);
     precision: "fp64", "double_float" (FP32 pairs, ~48 bits) or "fp32_inner"
     (FP64 defect correction around an FP32 fused CG, inner_rtol per cycle).
     Vectors are float64 CUDA tensors in the library's tile-blocked order.
@@ -42,8 +46,8 @@ class Problem:
 
     def __init__(self, degree: int, cells, amplitude: float = 0.0, geometry: str = "affine",
                  coefficient: str = "constant", mode: str = "fused", precision: str = "fp64",
-                 inner_rtol: float = 0.0, graph_iterations: int = 0, instrument: bool = False, tile=None,
-                 stream: torch.cuda.Stream | None = None):
+                 preconditioner: str = "jacobi", inner_rtol: float = 0.0, graph_iterations: int = 0,
+                 instrument: bool = False, tile=None, stream: torch.cuda.Stream | None = None):
         if not torch.cuda.is_available():
             raise RuntimeError("paper_2205_08909_gb300 needs a CUDA device (no CPU fallback)")
         self._lib = _binding.load()
@@ -56,6 +60,7 @@ class Problem:
         opt = _binding.Options()
         opt.mode = _binding.MODE[mode]
         opt.precision = _binding.PRECISION[precision]
+        opt.preconditioner = _binding.PRECONDITIONER[preconditioner]
         opt.inner_rtol = float(inner_rtol)
         opt.graph_iterations = int(graph_iterations)
         opt.instrument = 1 if instrument else 0

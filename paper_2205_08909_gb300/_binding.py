@@ -19,9 +19,10 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED_DEGREE", 3: "OUT_OF_MEMORY"
           5: "NOT_CONVERGED", 6: "BREAKDOWN", 7: "DEVICE_TIMEOUT", 8: "SCRATCH_TOO_SMALL"}
 OK, NOT_CONVERGED, BREAKDOWN = 0, 5, 6
 
-GEOM = {"affine": 0, "deformed": 1}
+GEOM = {"affine": 0, "deformed": 1, "deformed_tensor": 2}
 COEF = {"constant": 0, "sin_x": 1}
-MODE = {"fused": 0, "unfused": 1}
+MODE = {"fused": 0, "unfused": 1, "semi_fused": 2}
+PRECONDITIONER = {"jacobi": 0, "none": 1}
 PRECISION = {"fp64": 0, "double_float": 1, "fp32_inner": 2}
 
 
@@ -35,7 +36,7 @@ class Geometry(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("graph_iterations", ctypes.c_int32), ("instrument", ctypes.c_int32),
-                ("tile", ctypes.c_int32 * 3), ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("tile", ctypes.c_int32 * 3), ("precision", ctypes.c_int32), ("preconditioner", ctypes.c_int32),
                 ("inner_rtol", ctypes.c_double)]
 
 

@@ -72,6 +72,7 @@ struct mfcg_problem {
   int graph_iters = 16;
   cudaGraphExec_t graph_fused = nullptr;
   cudaGraphExec_t graph_unfused = nullptr;
+  cudaGraphExec_t graph_semi = nullptr;
   int64_t launches = 0;
   std::vector<void*> owned;  // every device allocation
 };
@@ -185,16 +186,36 @@ int enqueue_unfused_iteration(mfcg_problem* P, cudaEvent_t t0, cudaEvent_t t1) {
   return MFCG_OK;
 }
 
-constexpr int kFusedLaunchesPerIter = 2;
-constexpr int kUnfusedLaunchesPerIter = 9;
+// semi-fused Algorithm 5: "pre" kernel, operator (tile + tail), "post" kernel
+int enqueue_semi_iteration(mfcg_problem* P, cudaEvent_t t0, cudaEvent_t t1) {
+  const int64_t n = P->g.n_dofs;
+  CK(launch_semi_pre(n, P->state, P->x, P->ur, P->up, P->uv, P->diag_inv, P->exec));
+  TileArgs a = base_args(P, P->op_prec, P->geo_op);
+  a.in0 = P->up;
+  a.out0 = P->uv;
+  if (t0) CK(cudaEventRecord(t0, P->exec));
+  CK(launch_tile(P->degree, MODE_OPERATOR, a, P->c, P->exec));
+  if (t1) CK(cudaEventRecord(t1, P->exec));
+  CK(launch_tail(P->degree, MODE_OPERATOR, a, P->exec));
+  CK(launch_semi_post(n, P->state, P->ur, P->up, P->uv, P->diag_inv, P->partial, P->exec));
+  return MFCG_OK;
+}
 
-int capture_graph(mfcg_problem* P, int fused, cudaGraphExec_t* out) {
+enum IterKind { ITER_FUSED = 0, ITER_UNFUSED = 1, ITER_SEMI = 2 };
+constexpr int kLaunchesPerIter[3] = {2, 9, 4};
+
+int enqueue_iteration(mfcg_problem* P, int kind, int odd, cudaEvent_t t0, cudaEvent_t t1) {
+  if (kind == ITER_FUSED) return enqueue_fused_iteration(P, odd, t0, t1);
+  if (kind == ITER_UNFUSED) return enqueue_unfused_iteration(P, t0, t1);
+  return enqueue_semi_iteration(P, t0, t1);
+}
+
+int capture_graph(mfcg_problem* P, int kind, cudaGraphExec_t* out) {
   cudaGraph_t graph;
   CK(cudaStreamBeginCapture(P->exec, cudaStreamCaptureModeThreadLocal));
   int st = MFCG_OK;
   for (int it = 0; it < P->graph_iters && st == MFCG_OK; ++it)
-    st = fused ? enqueue_fused_iteration(P, (it & 1) == 0, nullptr, nullptr)
-               : enqueue_unfused_iteration(P, nullptr, nullptr);
+    st = enqueue_iteration(P, kind, (it & 1) == 0, nullptr, nullptr);
   cudaError_t e = cudaStreamEndCapture(P->exec, &graph);
   if (st != MFCG_OK || e != cudaSuccess) return MFCG_CUDA_ERROR;
   e = cudaGraphInstantiate(out, graph, 0);
@@ -223,9 +244,9 @@ struct IterStats {
 // Runs CG iterations until the device flag is set or maxit is reached: graphs
 // of G iterations (no per-iteration host synchronisation), or direct launches
 // with CUDA events around every operator-pass kernel when instrumenting.
-int run_iterations(mfcg_problem* P, int fused, int maxit, IterStats& stats) {
+int run_iterations(mfcg_problem* P, int kind, int maxit, IterStats& stats) {
   int st;
-  const int per_iter = fused ? kFusedLaunchesPerIter : kUnfusedLaunchesPerIter;
+  const int per_iter = kLaunchesPerIter[kind];
   if (P->opt.instrument) {
     std::vector<cudaEvent_t> ev;
     int done_it = 0;
@@ -235,8 +256,7 @@ int run_iterations(mfcg_problem* P, int fused, int maxit, IterStats& stats) {
       for (auto& e : ev) CK(cudaEventCreate(&e));
       for (int i = 0; i < chunk; ++i) {
         const int k = done_it + i + 1;
-        st = fused ? enqueue_fused_iteration(P, k & 1, ev[2 * i], ev[2 * i + 1])
-                   : enqueue_unfused_iteration(P, ev[2 * i], ev[2 * i + 1]);
+        st = enqueue_iteration(P, kind, k & 1, ev[2 * i], ev[2 * i + 1]);
         if (st != MFCG_OK) return st;
       }
       P->launches += (int64_t)chunk * per_iter;
@@ -255,8 +275,8 @@ int run_iterations(mfcg_problem* P, int fused, int maxit, IterStats& stats) {
     }
     return MFCG_OK;
   }
-  cudaGraphExec_t* gexec = fused ? &P->graph_fused : &P->graph_unfused;
-  if (!*gexec && (st = capture_graph(P, fused, gexec)) != MFCG_OK) return st;
+  cudaGraphExec_t* gexec = kind == ITER_FUSED ? &P->graph_fused : (kind == ITER_UNFUSED ? &P->graph_unfused : &P->graph_semi);
+  if (!*gexec && (st = capture_graph(P, kind, gexec)) != MFCG_OK) return st;
   const int G = P->graph_iters;
   const int n_graphs = (maxit + G - 1) / G;
   cudaEvent_t evs[2];
@@ -296,7 +316,7 @@ int fused_core(mfcg_problem* P, const double* b, const double* r0, double rtol, 
   CK(cudaMemsetAsync(P->p[0], 0, n * es, P->exec));
   CK(cudaMemsetAsync(P->v[0], 0, n * es, P->exec));
   P->launches += 2;
-  int st = run_iterations(P, 1, maxit, stats);
+  int st = run_iterations(P, ITER_FUSED, maxit, stats);
   if (st != MFCG_OK) return st;
   CK(launch_finalize_fused(P->cg_prec, n, P->state, P->xs, P->p[0], P->p[1], P->r[0], P->r[1], P->dinv_s, P->exec));
   P->launches += 1;
@@ -335,6 +355,17 @@ int solve_direct(mfcg_problem* P, const double* b, double* x_user, double rtol, 
     if ((st = fused_core(P, b, P->work, rtol, maxit, fixed, stats)) != MFCG_OK) return st;
     CK(launch_from_prec(P->cg_prec, P->xs, x_user, n, 0, P->exec));
     P->launches += 2;
+  } else if (P->opt.mode == MFCG_MODE_SEMI_FUSED) {
+    CK(cudaMemcpyAsync(P->x, x_user, n * sizeof(double), cudaMemcpyDeviceToDevice, P->exec));
+    CK(cudaMemcpyAsync(P->ur, P->work, n * sizeof(double), cudaMemcpyDeviceToDevice, P->exec));
+    CK(cudaMemsetAsync(P->up, 0, n * sizeof(double), P->exec));
+    CK(cudaMemsetAsync(P->uv, 0, n * sizeof(double), P->exec));
+    CK(launch_cg_init(P->state, b, P->ur, n, rtol, maxit, fixed, P->partial, 0, P->exec));
+    P->launches += 1;
+    if ((st = run_iterations(P, ITER_SEMI, maxit, stats)) != MFCG_OK) return st;
+    CK(launch_finalize_fused(PREC_F64, n, P->state, P->x, P->up, P->up, P->ur, P->ur, P->diag_inv, P->exec));
+    CK(cudaMemcpyAsync(x_user, P->x, n * sizeof(double), cudaMemcpyDeviceToDevice, P->exec));
+    P->launches += 1;
   } else {
     CK(cudaMemcpyAsync(P->x, x_user, n * sizeof(double), cudaMemcpyDeviceToDevice, P->exec));
     CK(cudaMemcpyAsync(P->ur, P->work, n * sizeof(double), cudaMemcpyDeviceToDevice, P->exec));
@@ -343,7 +374,7 @@ int solve_direct(mfcg_problem* P, const double* b, double* x_user, double rtol, 
     UnfusedArgs u = unfused_args(P);
     CK(launch_unfused_dot(3, u, P->exec));  // z0 = M^-1 r0, p0 = z0, e0 = r0.z0
     P->launches += 2;
-    if ((st = run_iterations(P, 0, maxit, stats)) != MFCG_OK) return st;
+    if ((st = run_iterations(P, ITER_UNFUSED, maxit, stats)) != MFCG_OK) return st;
     CK(cudaMemcpyAsync(x_user, P->x, n * sizeof(double), cudaMemcpyDeviceToDevice, P->exec));
   }
   CK(cudaMemcpyAsync(P->h_state, P->state, sizeof(CGState), cudaMemcpyDeviceToHost, P->exec));
@@ -402,7 +433,7 @@ int solve_defect_correction(mfcg_problem* P, const double* b, double* x_user, do
     CK(cudaMemsetAsync(P->v[0], 0, n * es, P->exec));
     CK(cudaMemsetAsync(P->xs, 0, n * es, P->exec));
     P->launches += 1;
-    if ((st = run_iterations(P, 1, maxit - total_it, stats)) != MFCG_OK) return st;
+    if ((st = run_iterations(P, ITER_FUSED, maxit - total_it, stats)) != MFCG_OK) return st;
     CK(launch_finalize_fused(P->cg_prec, n, P->state, P->xs, P->p[0], P->p[1], P->r[0], P->r[1], P->dinv_s,
                              P->exec));
     CK(launch_from_prec(P->cg_prec, P->xs, P->x, n, 1, P->exec));  // x += d in FP64
@@ -482,6 +513,7 @@ int mfcg_destroy(mfcg_problem* P) {
   if (P->exec) cudaStreamSynchronize(P->exec);
   if (P->graph_fused) cudaGraphExecDestroy(P->graph_fused);
   if (P->graph_unfused) cudaGraphExecDestroy(P->graph_unfused);
+  if (P->graph_semi) cudaGraphExecDestroy(P->graph_semi);
   for (void* q : P->owned) cudaFree(q);
   if (P->h_state) cudaFreeHost(P->h_state);
   if (P->ev_in) cudaEventDestroy(P->ev_in);
@@ -498,13 +530,16 @@ int mfcg_setup(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, con
   if (degree < 1 || degree > kMaxDegree) return MFCG_UNSUPPORTED_DEGREE;
   if (mesh->nx < 1 || mesh->ny < 1 || mesh->nz < 1) return MFCG_INVALID_ARG;
   if (!(std::fabs(mesh->amplitude) < 0.1)) return MFCG_INVALID_ARG;
-  if (geom->kind != MFCG_GEOM_AFFINE && geom->kind != MFCG_GEOM_DEFORMED) return MFCG_INVALID_ARG;
+  if (geom->kind != MFCG_GEOM_AFFINE && geom->kind != MFCG_GEOM_DEFORMED && geom->kind != MFCG_GEOM_DEFORMED_TENSOR)
+    return MFCG_INVALID_ARG;
   if (geom->coefficient != MFCG_COEF_CONSTANT && geom->coefficient != MFCG_COEF_SIN_X) return MFCG_INVALID_ARG;
   if (geom->kind == MFCG_GEOM_AFFINE && (mesh->amplitude != 0.0 || geom->coefficient != MFCG_COEF_CONSTANT))
     return MFCG_INVALID_ARG;
   mfcg_options o{};
   if (opt) o = *opt;
-  if (o.mode != MFCG_MODE_FUSED && o.mode != MFCG_MODE_UNFUSED) return MFCG_INVALID_ARG;
+  if (o.mode != MFCG_MODE_FUSED && o.mode != MFCG_MODE_UNFUSED && o.mode != MFCG_MODE_SEMI_FUSED)
+    return MFCG_INVALID_ARG;
+  if (o.preconditioner != MFCG_PRECOND_JACOBI && o.preconditioner != MFCG_PRECOND_NONE) return MFCG_INVALID_ARG;
   if (o.graph_iterations < 0 || (o.graph_iterations & 1)) return MFCG_INVALID_ARG;
   if (o.precision < MFCG_PREC_FP64 || o.precision > MFCG_PREC_FP32_INNER) return MFCG_INVALID_ARG;
   if (o.precision == MFCG_PREC_FP32_INNER && o.mode != MFCG_MODE_FUSED) return MFCG_INVALID_ARG;
@@ -527,7 +562,8 @@ int mfcg_setup(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, con
   P->mesh = *mesh;
   P->geom = *geom;
   P->opt = o;
-  P->geom_kind = geom->kind == MFCG_GEOM_AFFINE ? GEOM_AFFINE : GEOM_DEFORMED;
+  P->geom_kind = geom->kind == MFCG_GEOM_AFFINE ? GEOM_AFFINE
+                  : (geom->kind == MFCG_GEOM_DEFORMED_TENSOR ? GEOM_TENSOR : GEOM_DEFORMED);
   // the defect correction forms its outer residual with the native FP64
   // operator: its true-residual floor is 2^5 lower than the double-float one
   P->op_prec = o.precision == MFCG_PREC_DOUBLE_FLOAT ? PREC_DD : PREC_F64;
@@ -585,15 +621,16 @@ int mfcg_setup(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, con
   if (st == MFCG_OK) st = alloc_bytes(P, &P->shell, g.n_tiles * g.face_stride * 8);
   const int64_t nparts = std::max<int64_t>(g.n_tiles + P->tail_ctas, 152 * 8);
   if (st == MFCG_OK) st = alloc_bytes(P, &P->partial, nparts * 8 * 8);
-  const int64_t ngeo = (int64_t)N[0] * N[1] * N[2] * 10 * (degree + 1) * (degree + 1) * (degree + 1);
-  if (st == MFCG_OK && P->geom_kind == GEOM_DEFORMED) {
+  const int64_t ngeo =
+      (int64_t)N[0] * N[1] * N[2] * geo_values(P->geom_kind) * (degree + 1) * (degree + 1) * (degree + 1);
+  if (st == MFCG_OK && P->geom_kind != GEOM_AFFINE) {
     st = alloc_bytes(P, &P->geo, ngeo * 8);
     if (st == MFCG_OK && P->op_prec != PREC_F64) st = alloc_bytes(P, &P->geo_op, ngeo * 8);
     if (st == MFCG_OK && P->cg_prec != PREC_F64 && P->cg_prec != P->op_prec)
       st = alloc_bytes(P, &P->geo_cg, ngeo * prec_bytes(P->cg_prec));
   }
   if (st != MFCG_OK) return fail(st);
-  if (P->geom_kind == GEOM_DEFORMED) {
+  if (P->geom_kind != GEOM_AFFINE) {
     if (!P->geo_op) P->geo_op = P->geo;
     if (!P->geo_cg) P->geo_cg = P->cg_prec == PREC_F64 ? (void*)P->geo : P->geo_op;
   }
@@ -601,8 +638,8 @@ int mfcg_setup(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, con
   if (cudaMallocHost(&P->h_state, 2 * sizeof(CGState)) != cudaSuccess) return fail(MFCG_OUT_OF_MEMORY);
   if (cudaMemsetAsync(P->state, 0, sizeof(CGState), P->exec) != cudaSuccess) return fail(MFCG_CUDA_ERROR);
   if (enter(P) != MFCG_OK) return fail(MFCG_CUDA_ERROR);
-  if (P->geom_kind == GEOM_DEFORMED) {
-    if (launch_geometry(g, P->c, P->geo, P->exec) != cudaSuccess) return fail(MFCG_CUDA_ERROR);
+  if (P->geom_kind != GEOM_AFFINE) {
+    if (launch_geometry(g, P->c, P->geom_kind, P->geo, P->exec) != cudaSuccess) return fail(MFCG_CUDA_ERROR);
     if (P->geo_op != P->geo && launch_to_prec(P->op_prec, P->geo, P->geo_op, ngeo, P->exec) != cudaSuccess)
       return fail(MFCG_CUDA_ERROR);
     if (P->geo_cg != P->geo && P->geo_cg != P->geo_op &&
@@ -611,7 +648,11 @@ int mfcg_setup(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, con
   }
   // Jacobi preconditioner: exact diagonal and its inverse (FP64, converted for the fused CG)
   if ((st = run_pass(P, MODE_DIAG, nullptr, P->diag)) != MFCG_OK) return fail(st);
-  if (launch_invert(P->diag, P->diag_inv, n, P->exec) != cudaSuccess) return fail(MFCG_CUDA_ERROR);
+  if (o.preconditioner == MFCG_PRECOND_NONE) {
+    if (launch_fill(P->diag_inv, 1.0, n, P->exec) != cudaSuccess) return fail(MFCG_CUDA_ERROR);
+  } else if (launch_invert(P->diag, P->diag_inv, n, P->exec) != cudaSuccess) {
+    return fail(MFCG_CUDA_ERROR);
+  }
   if (fused && launch_to_prec(P->cg_prec, P->diag_inv, P->dinv_s, n, P->exec) != cudaSuccess)
     return fail(MFCG_CUDA_ERROR);
   if (cudaStreamSynchronize(P->exec) != cudaSuccess) return fail(MFCG_CUDA_ERROR);

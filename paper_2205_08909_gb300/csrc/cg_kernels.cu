@@ -95,10 +95,12 @@ __global__ void reorder_kernel(const TileGeom g, const double* in, double* out, 
 // Per-point data of the deformed map x = X + A s(X) (1,1,1), X = h (c + xhat):
 // J = (I + A 1 grad s^T) diag(h), so by Sherman-Morrison
 // J^{-1}_{rc} = (delta_rc - A ds/dX_c / (1 + A sum grad s)) / h_r and
-// det J = h_x h_y h_z (1 + A sum grad s).  Stored [cell][10][nq]: J^{-1}
-// row-major, then w_q det J a(x_q).
-__global__ void geometry_kernel(const TileGeom g, const OperatorCoeffs c, double* geo) {
+// det J = h_x h_y h_z (1 + A sum grad s).  GEOM_DEFORMED stores [cell][10][nq]:
+// J^{-1} row-major, then w_q det J a(x_q); GEOM_TENSOR stores [cell][6][nq]:
+// the upper triangle of C = (w_q det J a) J^{-1} J^{-T}.
+__global__ void geometry_kernel(const TileGeom g, const OperatorCoeffs c, int geom, double* geo) {
   const int n1 = g.p + 1, nq = n1 * n1 * n1;
+  const int nv = geo_values(geom);
   const int64_t total = (int64_t)g.N[0] * g.N[1] * g.N[2] * nq;
   const double twopi = 6.28318530717958647692, pi = 3.14159265358979323846;
   for (int64_t t = blockIdx.x * (int64_t)kVecThreads + threadIdx.x; t < total; t += (int64_t)gridDim.x * kVecThreads) {
@@ -112,12 +114,24 @@ __global__ void geometry_kernel(const TileGeom g, const OperatorCoeffs c, double
                           twopi * sx * sy * cos(twopi * Z)};
     const double A = c.amplitude;
     const double den = 1.0 + A * (gs[0] + gs[1] + gs[2]);
-    double* out = geo + cell * 10 * nq + q;
+    double Ji[9];
     for (int r = 0; r < 3; ++r)
-      for (int cc = 0; cc < 3; ++cc) out[(3 * r + cc) * nq] = ((r == cc ? 1.0 : 0.0) - A * gs[cc] / den) / c.h[r];
+      for (int cc = 0; cc < 3; ++cc) Ji[3 * r + cc] = ((r == cc ? 1.0 : 0.0) - A * gs[cc] / den) / c.h[r];
     const double xphys = X + A * sx * sy * sz;
     const double coef = c.coef == MFCG_COEF_SIN_X ? 1.0 + 0.5 * sin(pi * xphys) : 1.0;
-    out[9 * nq] = c.w[qa] * c.w[qb] * c.w[qc] * c.h[0] * c.h[1] * c.h[2] * den * coef;
+    const double jxw = c.w[qa] * c.w[qb] * c.w[qc] * c.h[0] * c.h[1] * c.h[2] * den * coef;
+    double* out = geo + cell * nv * nq + q;
+    if (geom == GEOM_TENSOR) {
+      const int rr[6] = {0, 0, 0, 1, 1, 2}, ccn[6] = {0, 1, 2, 1, 2, 2};
+      for (int m = 0; m < 6; ++m) {
+        double s = 0.0;
+        for (int l = 0; l < 3; ++l) s += Ji[3 * rr[m] + l] * Ji[3 * ccn[m] + l];
+        out[m * nq] = jxw * s;
+      }
+    } else {
+      for (int m = 0; m < 9; ++m) out[m * nq] = Ji[m];
+      out[9 * nq] = jxw;
+    }
   }
 }
 
@@ -283,9 +297,9 @@ cudaError_t launch_reorder(const TileGeom& g, const double* in, double* out, int
   return cudaGetLastError();
 }
 
-cudaError_t launch_geometry(const TileGeom& g, const OperatorCoeffs& c, double* geo, cudaStream_t s) {
+cudaError_t launch_geometry(const TileGeom& g, const OperatorCoeffs& c, int geom, double* geo, cudaStream_t s) {
   const int64_t total = (int64_t)g.N[0] * g.N[1] * g.N[2] * (g.p + 1) * (g.p + 1) * (g.p + 1);
-  geometry_kernel<<<grid_for(total), kVecThreads, 0, s>>>(g, c, geo);
+  geometry_kernel<<<grid_for(total), kVecThreads, 0, s>>>(g, c, geom, geo);
   return cudaGetLastError();
 }
 

@@ -258,7 +258,10 @@ __host__ __device__ inline void prepare_iteration_scalars(CGState* st) {
 
 enum TileMode { MODE_OPERATOR = 0, MODE_CG = 1, MODE_RHS = 2, MODE_DIAG = 3 };
 
-enum GeomKind { GEOM_AFFINE = 0, GEOM_DEFORMED = 1 };
+enum GeomKind { GEOM_AFFINE = 0, GEOM_DEFORMED = 1, GEOM_TENSOR = 2 };
+
+// values stored per quadrature point by the deformed geometry kinds
+__host__ __device__ constexpr int geo_values(int geom) { return geom == GEOM_TENSOR ? 6 : 10; }
 
 enum MatId { MAT_M = 0, MAT_K0 = 1, MAT_K1 = 2, MAT_K2 = 3, MAT_S = 4, MAT_DC = 5, NMAT = 6 };
 constexpr int kMat = (kMaxDegree + 1) * (kMaxDegree + 1);
@@ -297,7 +300,8 @@ struct TileArgs {
   void* x;
   void* shell;           // partial sums of shared-face nodes, arithmetic type of the precision
   double* partial;       // [n_tiles][8] (main) and [tail CTAs][8] (tail)
-  const void* geo;       // deformed: [cell][10][nq] = J^{-1} row-major, JxW*a (precision's type)
+  const void* geo;       // deformed: [cell][10][nq] = J^{-1} row-major, JxW*a; tensor: [cell][6][nq]
+                         // = C00 C01 C02 C11 C12 C22 of J^{-1} (JxW a) J^{-T} (precision's type)
   CGState* state;
   int64_t tail_nodes;    // number of shared-face nodes handled by the tail kernel
   int64_t fam[3];        // tail enumeration: nodes in the x / y / z boundary-plane families
@@ -317,7 +321,7 @@ cudaError_t prepare_tile(int degree, int geom, int prec, size_t smem);
 cudaError_t launch_fill(double* v, double value, int64_t n, cudaStream_t s);
 cudaError_t launch_invert(const double* in, double* out, int64_t n, cudaStream_t s);
 cudaError_t launch_reorder(const TileGeom& g, const double* in, double* out, int to_lex, cudaStream_t s);
-cudaError_t launch_geometry(const TileGeom& g, const OperatorCoeffs& c, double* geo, cudaStream_t s);
+cudaError_t launch_geometry(const TileGeom& g, const OperatorCoeffs& c, int geom, double* geo, cudaStream_t s);
 
 // CG drivers (cg_kernels.cu)
 struct UnfusedArgs {
@@ -340,6 +344,10 @@ cudaError_t launch_residual(const double* b, const double* ax, double* r, int64_
 cudaError_t launch_finalize_fused(int prec, int64_t n, CGState* st, void* x, const void* p0, const void* p1,
                                   const void* r0, const void* r1, const void* diag_inv, cudaStream_t s);
 cudaError_t launch_to_prec(int prec, const double* in, void* out, int64_t n, cudaStream_t s);
+cudaError_t launch_semi_pre(int64_t n, const CGState* st, double* x, double* r, double* p, const double* v,
+                            const double* dinv, cudaStream_t s);
+cudaError_t launch_semi_post(int64_t n, CGState* st, const double* r, const double* p, const double* v,
+                             const double* dinv, double* partial, cudaStream_t s);
 cudaError_t launch_from_prec(int prec, const void* in, double* out, int64_t n, int accumulate, cudaStream_t s);
 
 }  // namespace mfcg

@@ -280,7 +280,7 @@ __device__ void cell_op_affine(const OperatorCoeffs& c, const typename Num<PREC>
 // Gauss points by three sweeps with the interpolation matrix S, reference
 // gradients by three sweeps with the Gauss collocation derivative Dc, the
 // per-point metric J^{-1} (JxW a) J^{-T}, and the transposed sweeps back.
-template <int PREC, int P>
+template <int PREC, int P, int GEOM>
 __device__ void cell_op_deformed(const OperatorCoeffs& c, const typename Num<PREC>::T* U, typename Num<PREC>::T* V,
                                  typename Num<PREC>::T* S, int bx, int by, const ColorCells& cc,
                                  const typename Num<PREC>::T* __restrict__ geo) {
@@ -315,20 +315,29 @@ __device__ void cell_op_deformed(const OperatorCoeffs& c, const typename Num<PRE
   // metric at each point: flux = J^{-1} (JxW a) J^{-T} grad_ref
   for (int t = threadIdx.x; t < nc * N3; t += kThreads) {
     const int ci = t / N3, q = t - ci * N3;
-    const T* gq = geo + (int64_t)cc.cell[ci] * 10 * N3 + q;
-    T Ji[9];
-#pragma unroll
-    for (int m = 0; m < 9; ++m) Ji[m] = gq[m * N3];
-    const T jxw = gq[9 * N3];
     T* s = S + ci * stride;
     const T g0 = s[N3 + q], g1 = s[2 * N3 + q], g2 = s[3 * N3 + q];
-    // physical gradient (J^{-T} g)_m = sum_n Ji[n][m] g_n, scaled by JxW a
-    const T f0 = t_mul<PREC>(jxw, dot3<PREC>(Ji[0], g0, Ji[3], g1, Ji[6], g2));
-    const T f1 = t_mul<PREC>(jxw, dot3<PREC>(Ji[1], g0, Ji[4], g1, Ji[7], g2));
-    const T f2 = t_mul<PREC>(jxw, dot3<PREC>(Ji[2], g0, Ji[5], g1, Ji[8], g2));
-    s[N3 + q] = dot3<PREC>(Ji[0], f0, Ji[1], f1, Ji[2], f2);
-    s[2 * N3 + q] = dot3<PREC>(Ji[3], f0, Ji[4], f1, Ji[5], f2);
-    s[3 * N3 + q] = dot3<PREC>(Ji[6], f0, Ji[7], f1, Ji[8], f2);
+    if constexpr (GEOM == GEOM_TENSOR) {
+      // stored symmetric tensor C = J^{-1} (JxW a) J^{-T}: flux = C grad_ref
+      const T* gq = geo + (int64_t)cc.cell[ci] * 6 * N3 + q;
+      const T c00 = gq[0], c01 = gq[N3], c02 = gq[2 * N3], c11 = gq[3 * N3], c12 = gq[4 * N3], c22 = gq[5 * N3];
+      s[N3 + q] = dot3<PREC>(c00, g0, c01, g1, c02, g2);
+      s[2 * N3 + q] = dot3<PREC>(c01, g0, c11, g1, c12, g2);
+      s[3 * N3 + q] = dot3<PREC>(c02, g0, c12, g1, c22, g2);
+    } else {
+      const T* gq = geo + (int64_t)cc.cell[ci] * 10 * N3 + q;
+      T Ji[9];
+#pragma unroll
+      for (int m = 0; m < 9; ++m) Ji[m] = gq[m * N3];
+      const T jxw = gq[9 * N3];
+      // physical gradient (J^{-T} g)_m = sum_n Ji[n][m] g_n, scaled by JxW a
+      const T f0 = t_mul<PREC>(jxw, dot3<PREC>(Ji[0], g0, Ji[3], g1, Ji[6], g2));
+      const T f1 = t_mul<PREC>(jxw, dot3<PREC>(Ji[1], g0, Ji[4], g1, Ji[7], g2));
+      const T f2 = t_mul<PREC>(jxw, dot3<PREC>(Ji[2], g0, Ji[5], g1, Ji[8], g2));
+      s[N3 + q] = dot3<PREC>(Ji[0], f0, Ji[1], f1, Ji[2], f2);
+      s[2 * N3 + q] = dot3<PREC>(Ji[3], f0, Ji[4], f1, Ji[5], f2);
+      s[3 * N3 + q] = dot3<PREC>(Ji[6], f0, Ji[7], f1, Ji[8], f2);
+    }
   }
   __syncthreads();
   // transposed derivative sweeps, summed into s0
@@ -420,6 +429,9 @@ __device__ void cell_diag(const OperatorCoeffs& c, double* V, double* S, int bx,
       if (GEOM == GEOM_AFFINE) {
         const int qa = q % N1, qb = (q / N1) % N1, qc = q / N2;
         C = c.w[qa] * c.w[qb] * c.w[qc] * c.h[0] * c.h[1] * c.h[2] / (c.h[d0] * c.h[d0]);
+      } else if (GEOM == GEOM_TENSOR) {
+        const int m = d0 == d1 ? (d0 == 0 ? 0 : (d0 == 1 ? 3 : 5)) : (d0 + d1 == 1 ? 1 : (d0 + d1 == 2 ? 2 : 4));
+        C = __ldg(geo + (int64_t)cc.cell[ci] * 6 * N3 + m * N3 + q);
       } else {
         const double* gq = geo + (int64_t)cc.cell[ci] * 10 * N3 + q;
         double s = 0.0;
@@ -845,7 +857,7 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a, const 
     } else if constexpr (GEOM == GEOM_AFFINE) {
       cell_op_affine<PREC, P>(c, U, V, S, bx, by, cc);
     } else {
-      cell_op_deformed<PREC, P>(c, U, V, S, bx, by, cc, static_cast<const T*>(a.geo));
+      cell_op_deformed<PREC, P, GEOM>(c, U, V, S, bx, by, cc, static_cast<const T*>(a.geo));
     }
   }
 
@@ -1091,7 +1103,9 @@ TileFn<P> tile_fn_g(int mode, int prec) {
 
 template <int P>
 TileFn<P> tile_fn(int mode, int geom, int prec) {
-  return geom == GEOM_AFFINE ? tile_fn_g<P, GEOM_AFFINE>(mode, prec) : tile_fn_g<P, GEOM_DEFORMED>(mode, prec);
+  if (geom == GEOM_AFFINE) return tile_fn_g<P, GEOM_AFFINE>(mode, prec);
+  if (geom == GEOM_TENSOR) return tile_fn_g<P, GEOM_TENSOR>(mode, prec);
+  return tile_fn_g<P, GEOM_DEFORMED>(mode, prec);
 }
 
 // once per problem (outside any stream capture): allow the dynamic shared memory

@@ -35,8 +35,9 @@ def _oracle_problem(p, cells, amp=0.0, coef="constant"):
     return fem.Problem(p, tuple(cells), amp, fem.COEF_SIN_X if coef == "sin_x" else fem.COEF_CONSTANT)
 
 
-def _gpu_problem(mfcg, p, cells, amp=0.0, coef="constant", **kw):
-    geometry = "deformed" if (amp != 0.0 or coef != "constant") else "affine"
+def _gpu_problem(mfcg, p, cells, amp=0.0, coef="constant", geometry=None, **kw):
+    if geometry is None:
+        geometry = "deformed" if (amp != 0.0 or coef != "constant") else "affine"
     return mfcg.Problem(p, cells, amplitude=amp, geometry=geometry, coefficient=coef, **kw)
 
 
@@ -85,6 +86,25 @@ def test_operator_diagonal_rhs_match_oracle(mfcg, p, cells, amp, coef, tile, pre
     prob.close()
 
 
+DEFORMED_OPERATOR_CASES = [c for c in OPERATOR_CASES if c[2] != 0.0 or c[3] != "constant"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "double_float"])
+@pytest.mark.parametrize("p,cells,amp,coef,tile", DEFORMED_OPERATOR_CASES)
+def test_final_tensor_geometry_matches_oracle(mfcg, p, cells, amp, coef, tile, precision):
+    # Sec. 2.2 "final tensor" storage: the same operator as the inverse-Jacobian
+    # storage, from 6 instead of 10 values per quadrature point
+    op = _oracle_problem(p, cells, amp, coef)
+    A = fem.assemble(op)
+    prob = _gpu_problem(mfcg, p, cells, amp, coef, geometry="deformed_tensor", tile=tile, precision=precision)
+    u = inputs.random_vector(op.n_dofs, salt=p)
+    got = _to_host(prob, prob.apply_operator(_to_dev(prob, u)))
+    assert _rel(got, A @ u) <= OP_TOL
+    assert _rel(_to_host(prob, prob.diagonal()), A.diagonal()) <= OP_TOL
+    assert _rel(_to_host(prob, prob.rhs()), fem.rhs(op)) <= 1e-12
+    prob.close()
+
+
 def test_reordering_is_a_permutation(mfcg):
     prob = mfcg.Problem(3, (5, 4, 3), tile=(2, 3, 2))
     lex = torch.arange(prob.n_dofs, dtype=torch.float64, device="cuda")
@@ -103,7 +123,8 @@ CG_CASES = [
 
 
 SOLVER_VARIANTS = [("fused", "fp64"), ("unfused", "fp64"), ("fused", "double_float"), ("unfused", "double_float"),
-                   ("fused", "fp32_inner")]
+                   ("fused", "fp32_inner"), ("semi_fused", "fp64"), ("semi_fused", "double_float")]
+FIXED_VARIANTS = [v for v in SOLVER_VARIANTS if v[1] != "fp32_inner"]
 
 
 @pytest.mark.parametrize("mode,precision", SOLVER_VARIANTS)
@@ -127,7 +148,24 @@ def test_cg_solution_matches_oracle(mfcg, mode, precision, p, cells, amp, coef):
     prob.close()
 
 
-@pytest.mark.parametrize("mode,precision", SOLVER_VARIANTS[:4])
+@pytest.mark.parametrize("mode,precision", [("fused", "fp64"), ("unfused", "fp64"), ("fused", "double_float"),
+                                            ("fused", "fp32_inner")])
+@pytest.mark.parametrize("p,cells,amp,coef", [c for c in CG_CASES if c[2] != 0.0])
+def test_cg_with_final_tensor_geometry_matches_oracle(mfcg, mode, precision, p, cells, amp, coef):
+    op = _oracle_problem(p, cells, amp, coef)
+    A = fem.assemble(op)
+    b = fem.rhs(op)
+    ref = ocg.pcg_algorithm1(lambda v: A @ v, b, 1.0 / A.diagonal(), 1e-10, 5000)
+    prob = _gpu_problem(mfcg, p, cells, amp, coef, geometry="deformed_tensor", mode=mode, precision=precision)
+    x, info = prob.cg_solve(_to_dev(prob, b), rtol=1e-10, maxit=5000)
+    assert info["converged"] == 1
+    if precision != "fp32_inner":
+        assert abs(info["iterations"] - ref.iterations) <= 1
+    assert _rel(_to_host(prob, x), ref.x) <= SOL_TOL
+    prob.close()
+
+
+@pytest.mark.parametrize("mode,precision", FIXED_VARIANTS)
 @pytest.mark.parametrize("maxit", [1, 2, 3, 6, 7])
 def test_fixed_iterations_match_algorithm1_iterates(mfcg, mode, precision, maxit):
     # rtol = 0 runs exactly maxit iterations: checks the delayed x update and
@@ -141,6 +179,24 @@ def test_fixed_iterations_match_algorithm1_iterates(mfcg, mode, precision, maxit
     x, info = prob.cg_solve(_to_dev(prob, b), rtol=0.0, maxit=maxit)
     assert info["iterations"] == maxit
     assert _rel(_to_host(prob, x), ref.x) <= 1e-11
+    prob.close()
+
+
+@pytest.mark.parametrize("mode,precision", FIXED_VARIANTS)
+@pytest.mark.parametrize("p,cells,amp,coef", [(2, (6, 5, 7), 0.0, "constant"), (3, (3, 4, 3), 0.05, "sin_x")])
+def test_no_preconditioner_is_merged_cg_of_algorithm4(mfcg, mode, precision, p, cells, amp, coef):
+    # M = I: Algorithm 5 reduces to Algorithm 4; the oracle is Algorithm 1 with M = I
+    op = _oracle_problem(p, cells, amp, coef)
+    A = fem.assemble(op)
+    b = fem.rhs(op)
+    ref = ocg.pcg_algorithm1(lambda v: A @ v, b, np.ones(op.n_dofs), 1e-10, 5000)
+    prob = _gpu_problem(mfcg, p, cells, amp, coef, mode=mode, precision=precision, preconditioner="none")
+    x, info = prob.cg_solve(_to_dev(prob, b), rtol=1e-10, maxit=5000)
+    assert info["converged"] == 1
+    assert abs(info["iterations"] - ref.iterations) <= 1
+    assert _rel(_to_host(prob, x), ref.x) <= SOL_TOL
+    # the diagonal entry point still returns diag(A)
+    assert _rel(_to_host(prob, prob.diagonal()), A.diagonal()) <= OP_TOL
     prob.close()
 
 
@@ -227,11 +283,13 @@ def test_full_size_q4_64cube_solve(mfcg, mode, precision):
     prob.close()
 
 
+@pytest.mark.parametrize("geometry", ["deformed", "deformed_tensor"])
 @pytest.mark.parametrize("precision", ["fp64", "double_float"])
-def test_full_size_q6_48cube_deformed_operator_sampled_rows(mfcg, precision):
+def test_full_size_q6_48cube_deformed_operator_sampled_rows(mfcg, precision, geometry):
     w = inputs.WORKLOADS["q6_48cube_deformed"]
     op = _oracle_problem(w.degree, w.cells, w.amplitude, w.coefficient)
-    prob = _gpu_problem(mfcg, w.degree, w.cells, w.amplitude, w.coefficient, precision=precision)
+    prob = _gpu_problem(mfcg, w.degree, w.cells, w.amplitude, w.coefficient, geometry=geometry,
+                        precision=precision)
     u = inputs.random_vector(op.n_dofs, salt=48)
     got = _to_host(prob, prob.apply_operator(_to_dev(prob, u)))
     diag = _to_host(prob, prob.diagonal())

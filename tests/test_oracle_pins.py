@@ -335,3 +335,17 @@ def test_kronecker_apply_matches_assembled_matrix():
         ref = A @ u
         np.testing.assert_allclose(fastdiag.apply(prob, u), ref, atol=1e-13 * np.abs(ref).max())
 
+
+
+def test_algorithm5_with_identity_is_algorithm4_exact_rationals():
+    # M = I: Algorithm 5 becomes the merged CG of Algorithm 4 and must reproduce
+    # plain CG (Algorithm 1 with M = I) exactly
+    A = _exact_q2_system((2, 2, 2))
+    n = A.shape[0]
+    b = np.array([Fraction((5 * i) % 9 - 4) for i in range(n)], dtype=object)
+    ones = np.array([Fraction(1)] * n, dtype=object)
+    r1 = cg.pcg_algorithm1(lambda x: A.dot(x), b, ones, Fraction(1, 10 ** 9), 100)
+    r5 = cg.pcg_algorithm5(lambda x: A.dot(x), b, ones, Fraction(1, 10 ** 9), 100)
+    assert r1.iterations == r5.iterations
+    assert r1.alphas == r5.alphas and r1.betas == r5.betas
+    assert list(r1.x) == list(r5.x)
