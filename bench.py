@@ -73,12 +73,24 @@ def stored_traffic(workload: str, precision: str):
 
 # ------------------------------------------------------------------------------ algorithmic counts
 
-def algorithmic_flops_per_iteration(degree: int, n_cells: int, n_dofs: int) -> float:
-    """FP64 flops of one fused iteration: seven 1D sweeps of (p+1)^4 FMAs per
-    cell (Kronecker form of the affine cell operator) plus the vector work per
-    unknown (r, z, p updates 5, x update 5 every other iteration, seven sums
-    with M^-1 r and M^-1 v 16)."""
-    return 2.0 * 7 * (degree + 1) ** 4 * n_cells + 23.5 * n_dofs
+def geometry_values(geometry: str) -> int:
+    """Values stored per quadrature point: J^{-1} and JxW a (10) or the final tensor (6)."""
+    return {"affine": 0, "deformed": 10, "deformed_tensor": 6}[geometry]
+
+
+def algorithmic_flops_per_iteration(degree: int, n_cells: int, n_dofs: int, geometry: str = "affine") -> float:
+    """FP64 flops of one fused iteration.  Affine cells: seven 1D sweeps of
+    (p+1)^4 FMAs per cell (Kronecker form); deformed cells: twelve sweeps
+    (interpolation, collocation derivative and their transposes) plus the
+    per-point metric (42 flops from J^{-1} and JxW a, 18 from the final
+    tensor).  Plus the vector work per unknown (r, z, p updates 5, x update 5
+    every other iteration, seven sums with M^-1 r and M^-1 v 16)."""
+    n1 = degree + 1
+    if geometry == "affine":
+        per_cell = 2.0 * 7 * n1 ** 4
+    else:
+        per_cell = 2.0 * 12 * n1 ** 4 + (42 if geometry == "deformed" else 18) * n1 ** 3
+    return per_cell * n_cells + 23.5 * n_dofs
 
 
 ALGORITHMIC_BYTES_PER_DOF = 64.0  # r, p, v read+write, D^-1 read, x read+write every other iteration
@@ -224,17 +236,26 @@ def run_reference(args, world, rank):
     }
 
 
-def dd_ops_per_dof(degree: int, n_cells: int, n_dofs: int) -> float:
+def dd_ops_per_dof(degree: int, n_cells: int, n_dofs: int, geometry: str = "affine") -> float:
     """FP32-pipe operations of one fused double-float iteration per unknown,
     counted from the error-free transformations: a product accumulated into a
     (s, t) pair costs 12 (TwoProduct 2, cross terms 2, TwoSum 6, error sum 2),
     the first product of a sum 4, a normalisation 3, a pair addition 11, a pair
-    product 7.  Operator: per cell and pencil the z sweep (M, K_z), the y sweep
-    (M; K_y + M) and the x sweep (K_x + M, added into the node brick)."""
+    product 7.  Affine operator: per cell and pencil the z sweep (M, K_z), the
+    y sweep (M; K_y + M) and the x sweep (K_x + M, added into the node brick).
+    Deformed operator: twelve single-matrix sweeps, two accumulating
+    transposed-derivative sweeps, the metric (3 three-term sums from the final
+    tensor; 6 sums and 3 pair products from J^{-1} and JxW a) and the
+    node gather (one pair addition per cell node)."""
     n1 = degree + 1
     mv = n1 * (4 + 12 * (n1 - 1) + 3)
     mv2 = n1 * (4 + 12 * (2 * n1 - 1) + 3)
-    per_cell = n1 * n1 * (2 * mv + (mv + mv2) + (mv2 + 11 * n1))
+    dot3 = 4 + 12 * 2 + 3
+    if geometry == "affine":
+        per_cell = n1 * n1 * (2 * mv + (mv + mv2) + (mv2 + 11 * n1))
+    else:
+        metric = 3 * dot3 if geometry == "deformed_tensor" else 6 * dot3 + 3 * 7
+        per_cell = 12 * n1 * n1 * mv + 2 * 11 * n1 ** 3 + metric * n1 ** 3 + 11 * n1 ** 3
     pre = 34.0 * 1.2                                  # r and p updates on the tile brick (~1.2x the owned nodes)
     x_update = 48.0 / 2                               # every other iteration
     post = 2 * 7 + 7 * 12                             # M^-1 r, M^-1 v and seven accumulations
@@ -303,6 +324,10 @@ def run_ours(args, world, rank, local):
                 "converged": info["converged"], "outer_cycles": info["outer_cycles"]}
 
     dof_its = w.n_dofs * iters * K * world
+    # algorithmic bytes per unknown: the vectors, plus the stored geometry of deformed meshes
+    n_qp = n_cells * (w.degree + 1) ** 3
+    geo_bytes_per_dof = geometry_values(geometry) * 8.0 * n_qp / w.n_dofs
+    bytes_per_dof = ALGORITHMIC_BYTES_PER_DOF + geo_bytes_per_dof
 
     # ---------------- headline: fused CG in the requested precision
     fused = make("fused", main_prec)
@@ -325,10 +350,10 @@ def run_ours(args, world, rank, local):
         prob = make(mode, prec)
         ms_v, _ = timed_steps(prob, b, K, W)
         v = dof_its / (ms_v / 1e3) / 1e9
-        bytes_per_dof = 64 if mode == "fused" else 152
+        vb = (64 if mode == "fused" else 152) + geo_bytes_per_dof
         variants[f"{mode}_{prec}"] = {"value": round(v, 4), "ms_per_step": round(ms_v / K, 3),
-                                      "hbm_roofline_frac": round(v / world * bytes_per_dof / hbm, 4),
-                                      "algorithmic_bytes_per_dof": bytes_per_dof,
+                                      "hbm_roofline_frac": round(v / world * vb / hbm, 4),
+                                      "algorithmic_bytes_per_dof": round(vb, 2),
                                       "solve_rtol_1e-10": converged_solve(prob, b)}
         prob.close()
     unf_key = f"unfused_{main_prec}"
@@ -349,23 +374,23 @@ def run_ours(args, world, rank, local):
     _, info_i = inst.cg_solve(b, xi.zero_(), rtol=0.0, maxit=iters)
     kernel_ms = info_i["main_kernel_ms"] / max(info_i["main_kernel_launches"], 1)
     inst.close()
-    hbm_gbs = ALGORITHMIC_BYTES_PER_DOF * w.n_dofs / (kernel_ms / 1e3) / 1e9
+    hbm_gbs = bytes_per_dof * w.n_dofs / (kernel_ms / 1e3) / 1e9
     traffic = stored_traffic(w.name, main_prec)
     if main_prec == "fp64":
-        flops = algorithmic_flops_per_iteration(w.degree, n_cells, w.n_dofs)
+        flops = algorithmic_flops_per_iteration(w.degree, n_cells, w.n_dofs, geometry)
         achieved = flops / (kernel_ms / 1e3) / 1e12
         roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
                     "peak_kind": "nominal FP64 (recipe table)", "algorithmic_flops_per_launch": flops}
     elif main_prec == "double_float":
-        ops = dd_ops_per_dof(w.degree, n_cells, w.n_dofs) * w.n_dofs
+        ops = dd_ops_per_dof(w.degree, n_cells, w.n_dofs, geometry) * w.n_dofs
         achieved = ops / (kernel_ms / 1e3) / 1e12
         peak = fp32_pipe_peak_tops()
         roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 2),
                     "unit": "T FP32-pipe ops/s", "frac": round(achieved / peak, 4), "traffic": traffic,
                     "peak_kind": "152 SMs x 128 FP32 lanes x 2.07 GHz", "algorithmic_ops_per_launch": ops}
     else:
-        achieved = hbm_gbs / 2  # FP32 storage: 32 B per unknown
+        achieved = hbm_gbs / 2  # FP32 storage: half the FP64 bytes
         roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                     "frac": round(achieved / hbm, 4), "traffic": traffic, "peak_kind": peak_kind}
     roofline.update({"kernel": f"tile_kernel<{w.degree}, MODE_CG, GEOM_{ {'affine': 'AFFINE', 'deformed': 'DEFORMED', 'deformed_tensor': 'TENSOR'}[geometry]}, {main_prec}>",
@@ -403,8 +428,8 @@ def run_ours(args, world, rank, local):
                    "tile": list(tile) if tile else "default",
                    "parallelism": f"replicas x{world}",
                    "l2": f"inputs larger than L2: {8 * w.n_dofs / 1e6:.0f} MB per vector, 8 vectors"},
-        "hbm_roofline_frac": round(value / world * ALGORITHMIC_BYTES_PER_DOF / hbm, 4),
-        "algorithmic_bytes_per_dof": ALGORITHMIC_BYTES_PER_DOF,
+        "hbm_roofline_frac": round(value / world * bytes_per_dof / hbm, 4),
+        "algorithmic_bytes_per_dof": round(bytes_per_dof, 2),
         "fused_over_unfused": fused_over_unfused,
         "solve_rtol_1e-10": solve_main,
         "variants": variants,

@@ -61,7 +61,7 @@ cudaError_t prepare_tile(int degree, int geom, int prec, size_t smem) {
 }
 
 size_t tile_smem_bytes(int degree, int geom, int prec, const TileGeom& g) {
-  return tile_smem_elems(degree, geom, g) * prec_bytes(prec);
+  return tile_smem_elems(degree, geom, prec_bytes(prec), g) * prec_bytes(prec);
 }
 
 }  // namespace mfcg

@@ -22,6 +22,8 @@
 // the arithmetic precision (precision.cuh): FP64, double-float or FP32.
 #pragma once
 
+#include <algorithm>
+
 #include "mfcg_internal.h"
 #include "precision.cuh"
 
@@ -36,6 +38,22 @@ constexpr int kMaxColorCells = 512;
 __host__ __device__ constexpr int cell_stride(int P, int ns) {
   return ns * (P + 1) * (P + 1) * (P + 1) +
          ((((P + 1) * (P + 1) - ns * (P + 1) * (P + 1) * (P + 1)) % 32) + 32) % 32;
+}
+
+// Cells of a tile that the deformed cell operator processes at once: as many
+// as fit next to the two node bricks in kDeformedSmemBytes of shared memory
+// (two CTAs per SM), balanced over the batches of a full tile.
+constexpr int kDeformedSmemBytes = 110 * 1024;
+
+__host__ __device__ inline int deformed_batch_cells(int P, int elem_bytes, const TileGeom& g) {
+  const int ncell = g.T[0] * g.T[1] * g.T[2];
+  const int64_t bricks = 2LL * (P * g.T[0] + 1) * (P * g.T[1] + 1) * (P * g.T[2] + 1) * elem_bytes;
+  int64_t nb = (kDeformedSmemBytes - bricks) / ((int64_t)cell_stride(P, 4) * elem_bytes);
+  if (nb < 1) nb = 1;
+  if (nb > ncell) nb = ncell;
+  if (nb > kMaxColorCells) nb = kMaxColorCells;
+  const int nbatch = (int)((ncell + nb - 1) / nb);
+  return (ncell + nbatch - 1) / nbatch;
 }
 
 // ------------------------------------------------------------------------------------
@@ -280,10 +298,11 @@ __device__ void cell_op_affine(const OperatorCoeffs& c, const typename Num<PREC>
 // Gauss points by three sweeps with the interpolation matrix S, reference
 // gradients by three sweeps with the Gauss collocation derivative Dc, the
 // per-point metric J^{-1} (JxW a) J^{-T}, and the transposed sweeps back.
+// The results of the cells stay in their scratch (element (a,b,c) of cell ci
+// at S[ci*stride + cidx(a,b,c)]); gather_cell_results sums them into V.
 template <int PREC, int P, int GEOM>
-__device__ void cell_op_deformed(const OperatorCoeffs& c, const typename Num<PREC>::T* U, typename Num<PREC>::T* V,
-                                 typename Num<PREC>::T* S, int bx, int by, const ColorCells& cc,
-                                 const typename Num<PREC>::T* __restrict__ geo) {
+__device__ void cell_op_deformed(const OperatorCoeffs& c, const typename Num<PREC>::T* U, typename Num<PREC>::T* S,
+                                 int bx, int by, const ColorCells& cc, const typename Num<PREC>::T* __restrict__ geo) {
   using T = typename Num<PREC>::T;
   constexpr int N1 = P + 1, N2 = N1 * N1, N3 = N2 * N1;
   const int nc = cc.count();
@@ -346,19 +365,48 @@ __device__ void cell_op_deformed(const OperatorCoeffs& c, const typename Num<PRE
   sweep_copy<PREC, P, true, true>(S + 3 * N3, S, stride, nc, 2, c, MAT_DC);
   sweep_inplace<PREC, P, true>(S, stride, nc, 0, c, MAT_S);
   sweep_inplace<PREC, P, true>(S, stride, nc, 1, c, MAT_S);
-  // last sweep writes straight into the node brick
-  for (int t = threadIdx.x; t < nc * N2; t += kThreads) {
-    const int ci = t / N2, e = t - ci * N2, a = e % N1, b = e / N1;
-    const T* s0 = S + ci * stride;
-    T x[N1], y[N1];
-#pragma unroll
-    for (int s = 0; s < N1; ++s) x[s] = s0[cidx<N1>(a, b, s)];
-    mv<PREC, N1, true>(c, MAT_S, x, y);
-    T* v0 = V + cc.org[ci] + a + bx * b;
-#pragma unroll
-    for (int s = 0; s < N1; ++s) v0[s * bx * by] = t_add<PREC>(v0[s * bx * by], y[s]);
+  sweep_inplace<PREC, P, true>(S, stride, nc, 2, c, MAT_S);
+}
+
+// Sum of the cell results of a batch of cells [c0, c0 + nb) (tile-local
+// lexicographic cell order) into the node brick: every node of the slab of
+// node planes the batch touches adds the results of the batch's cells that
+// contain it, in a fixed (z, y, x) cell order -- deterministic without colours.
+template <int PREC, int P>
+__device__ void gather_cell_results(typename Num<PREC>::T* V, const typename Num<PREC>::T* S, int stride, int c0,
+                                    int nb, int ncx, int ncy, int bx, int by, const FastDiv& fbx,
+                                    const FastDiv& fby) {
+  using T = typename Num<PREC>::T;
+  constexpr int N1 = P + 1;
+  const int nxy = ncx * ncy;
+  const int cz_lo = c0 / nxy, cz_hi = (c0 + nb - 1) / nxy;
+  const int k_lo = P * cz_lo;
+  const int n = bx * by * (P * (cz_hi - cz_lo + 1) + 1);
+  for (int t = threadIdx.x; t < n; t += kThreads) {
+    const int r = (int)fdiv((uint32_t)t, fbx);
+    const int li = t - r * bx;
+    const int q = (int)fdiv((uint32_t)r, fby);
+    const int lj = r - q * by, lk = k_lo + q;
+    // cells containing the node along each direction: [lo, hi]
+    const int xh = min(li / P, ncx - 1), xl = li > 0 ? (li - 1) / P : 0;
+    const int yh = min(lj / P, ncy - 1), yl = lj > 0 ? (lj - 1) / P : 0;
+    const int zh = min(lk / P, cz_hi), zl = max(lk > 0 ? (lk - 1) / P : 0, cz_lo);
+    T acc = t_zero<PREC>();
+    bool any = false;
+    for (int cz = zl; cz <= zh; ++cz)
+      for (int cy = yl; cy <= yh; ++cy)
+        for (int cx = xl; cx <= xh; ++cx) {
+          const int cid = cx + ncx * (cy + ncy * cz) - c0;
+          if (cid < 0 || cid >= nb) continue;
+          const T val = S[cid * stride + cidx<N1>(li - P * cx, lj - P * cy, lk - P * cz)];
+          acc = any ? t_add<PREC>(acc, val) : val;
+          any = true;
+        }
+    if (any) {
+      T* v = V + li + bx * (lj + by * lk);
+      *v = t_add<PREC>(*v, acc);
+    }
   }
-  __syncthreads();
 }
 
 // Right-hand side b_e = sum_q w_q det J_q f(x_q) phi(xhat_q): forcing at the
@@ -836,7 +884,30 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a, const 
       if (ok[b]) V[sidx[b]] = t_zero<PREC>();
   }
 
-  // ---------------- phase 2: cell integrals, one colour at a time ----------------
+  // ---------------- phase 2: cell integrals ----------------
+  if constexpr (GEOM != GEOM_AFFINE && (MODE == MODE_CG || MODE == MODE_OPERATOR)) {
+    // deformed cells: batches of consecutive cells, all cells of a batch at
+    // once with their results in the scratch, then a fixed-order node gather
+    const int ncell = ncx * ncy * ncz;
+    const int nbmax = deformed_batch_cells(P, (int)sizeof(T), g);
+    const int stride = cell_stride(P, 4);
+    const FastDiv fbx = make_fastdiv((uint32_t)bx);
+    for (int c0 = 0; c0 < ncell; c0 += nbmax) {
+      const int nb = min(nbmax, ncell - c0);
+      __syncthreads();  // previous batch gathered (and phase 1 finished with U, V)
+      for (int ci = threadIdx.x; ci < nb; ci += kThreads) {
+        const int cid = c0 + ci;
+        const int cx = cid % ncx, cy = (cid / ncx) % ncy, cz = cid / (ncx * ncy);
+        s_org[ci] = P * cx + bx * (P * cy + by * P * cz);
+        s_cell[ci] = (cx0 + cx) + g.N[0] * ((cy0 + cy) + g.N[1] * (cz0 + cz));
+      }
+      __syncthreads();
+      const ColorCells cc{nb, s_org, s_cell};
+      cell_op_deformed<PREC, P, GEOM>(c, U, S, bx, by, cc, static_cast<const T*>(a.geo));
+      gather_cell_results<PREC, P>(V, S, stride, c0, nb, ncx, ncy, bx, by, fbx, fby);
+    }
+    __syncthreads();
+  } else
   for (int color = 0; color < 8; ++color) {
     const int px = color & 1, py = (color >> 1) & 1, pz = color >> 2;
     const int mx = (ncx - px + 1) / 2, my = (ncy - py + 1) / 2, mz = (ncz - pz + 1) / 2;
@@ -856,8 +927,6 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a, const 
       cell_diag<P, GEOM>(c, V, S, bx, by, cc, static_cast<const double*>(a.geo), cell_stride(P, GEOM == GEOM_AFFINE ? 2 : 4));
     } else if constexpr (GEOM == GEOM_AFFINE) {
       cell_op_affine<PREC, P>(c, U, V, S, bx, by, cc);
-    } else {
-      cell_op_deformed<PREC, P, GEOM>(c, U, V, S, bx, by, cc, static_cast<const T*>(a.geo));
     }
   }
 
@@ -1075,10 +1144,13 @@ __global__ void __launch_bounds__(kThreads) tail_kernel(const TileArgs a) {
 // ------------------------------------------------------------------------------------
 // launch helpers
 // ------------------------------------------------------------------------------------
-inline size_t tile_smem_elems(int P, int geom, const TileGeom& g) {
+// elements of dynamic shared memory: node bricks U and V, and the cell scratch
+// (one colour of cells, or one batch of deformed cells)
+inline size_t tile_smem_elems(int P, int geom, int elem_bytes, const TileGeom& g) {
   const size_t Bmax = (size_t)(P * g.T[0] + 1) * (P * g.T[1] + 1) * (P * g.T[2] + 1);
-  const size_t cpc = (size_t)((g.T[0] + 1) / 2) * ((g.T[1] + 1) / 2) * ((g.T[2] + 1) / 2);
-  return 2 * Bmax + cpc * (size_t)cell_stride(P, geom == GEOM_AFFINE ? 2 : 4);
+  size_t cells = (size_t)((g.T[0] + 1) / 2) * ((g.T[1] + 1) / 2) * ((g.T[2] + 1) / 2);
+  if (geom != GEOM_AFFINE) cells = std::max(cells, (size_t)deformed_batch_cells(P, elem_bytes, g));
+  return 2 * Bmax + cells * (size_t)cell_stride(P, geom == GEOM_AFFINE ? 2 : 4);
 }
 
 template <int P>
@@ -1124,7 +1196,7 @@ template <int P>
 cudaError_t launch_tile_p(int mode, const TileArgs& a, const OperatorCoeffs& c, cudaStream_t s) {
   TileFn<P> fn = tile_fn<P>(mode, a.geom, a.prec);
   if (!fn) return cudaErrorInvalidValue;
-  const size_t smem = tile_smem_elems(P, a.geom, a.g) * prec_bytes(a.prec);
+  const size_t smem = tile_smem_elems(P, a.geom, prec_bytes(a.prec), a.g) * prec_bytes(a.prec);
   fn<<<(unsigned)a.g.n_tiles, kThreads, smem, s>>>(a, c);
   return cudaGetLastError();
 }

@@ -332,3 +332,22 @@ def test_defect_correction_on_deformed_mesh(mfcg):
     assert (x - xr).abs().max().item() <= SOL_TOL * xr.abs().max().item()
     prob.close()
     ref.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32_inner", "double_float"])
+def test_full_size_q4_128cube_solve(mfcg, precision):
+    # FP32-inner defect correction (and the double-float CG) at 135M unknowns
+    # against the exact discrete solution by fast diagonalisation
+    w = inputs.WORKLOADS["q4_128cube"]
+    op = _oracle_problem(w.degree, w.cells)
+    prob = mfcg.Problem(w.degree, w.cells, precision=precision)
+    b = prob.rhs()
+    x, info = prob.cg_solve(b, rtol=1e-10, maxit=20000)
+    assert info["converged"]
+    bh = _to_host(prob, b)
+    xh = _to_host(prob, x)
+    prob.close()
+    xs = fastdiag.solve(op, bh)
+    assert _rel(xh, xs) <= SOL_TOL
+    r = bh - fastdiag.apply(op, xh)
+    assert np.linalg.norm(r) <= 1.5e-10 * np.linalg.norm(bh)
