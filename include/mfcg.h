@@ -85,6 +85,13 @@ typedef enum mfcg_preconditioner {
   MFCG_PRECOND_NONE = 1     /* M = I: Algorithm 5 reduces to the merged CG of Algorithm 4 (Sec. 4.1) */
 } mfcg_preconditioner;
 
+/* The operator of the problem (the CEED bake-off family of Sec. 2). */
+typedef enum mfcg_operator {
+  MFCG_OP_LAPLACE = 0,      /* a(grad phi_i, grad phi_j) (Eq. 5): BP3, or BP4 with components = 3      */
+  MFCG_OP_MASS = 1          /* (a phi_i, phi_j), same Gauss rule: BP1, or BP2 with components = 3;
+                               affine meshes or MFCG_GEOM_DEFORMED (which stores JxW a)             */
+} mfcg_operator;
+
 /* Arithmetic of the operator and of the CG vectors.  The ABI is FP64 in every case. */
 typedef enum mfcg_precision {
   MFCG_PREC_FP64 = 0,         /* native FP64 everywhere                                                 */
@@ -101,10 +108,18 @@ typedef struct mfcg_options {
   int32_t graph_iterations; /* CG iterations per captured CUDA graph (even; 0 = 16)                   */
   int32_t instrument;       /* 1: launch without graphs and time every operator-pass kernel with
                                CUDA events (mfcg_solve_info.main_kernel_ms); 0: graphs, no timing      */
-  int32_t tile[3];          /* cells per tile and direction; 0 = chosen from the degree               */
+  int32_t tile[3];          /* cells per tile and direction; 0 = chosen from the degree; all three -1 =
+                               autotune: mfcg_setup times short fixed-iteration solves with a few
+                               candidate tiles around the default and keeps the fastest              */
   int32_t precision;        /* mfcg_precision                                                       */
   int32_t preconditioner;   /* mfcg_preconditioner                                                  */
   double inner_rtol;        /* MFCG_PREC_FP32_INNER: residual reduction of each inner solve (0 = 1e-3) */
+  int32_t components;       /* 0 or 1: scalar Laplacian; 2 or 3: vector-valued Laplacian (the BP4 form
+                               of Sec. 2): every component is the scalar operator, one CG runs on the
+                               coupled system, the Jacobi diagonal and the geometry are shared by the
+                               components.  Vectors hold the components one after another (each in
+                               the tile-blocked order); FUSED mode only                               */
+  int32_t operator_kind;    /* mfcg_operator                                                        */
 } mfcg_options;
 
 typedef struct mfcg_solve_info {
@@ -152,7 +167,9 @@ int mfcg_diagonal(mfcg_problem* prob, double* diag);
 
 /* mfcg_rhs -- right-hand side b_i = int f phi_i for the manufactured solution
  * u = sin(pi x) sin(pi y) sin(pi z) (f = -div(a grad u)), same Gauss rule,
- * 0 on Dirichlet nodes.  b: device, n doubles.  Asynchronous. */
+ * 0 on Dirichlet nodes; for MFCG_OP_MASS the right-hand side of the same u
+ * (f = a u).  b: device, n doubles.  With components > 1, component c holds the
+ * right-hand side of u_c = (c + 1) u.  Asynchronous. */
 int mfcg_rhs(mfcg_problem* prob, double* b);
 
 /* mfcg_cg_solve -- Jacobi-preconditioned CG from the initial guess in x
@@ -210,6 +227,46 @@ int mfcg_destroy(mfcg_problem* prob);
  * needs clearing between calls.  Asynchronous on cuda_stream.  Errors:
  * INVALID_ARG, UNSUPPORTED_DEGREE, SCRATCH_TOO_SMALL, CUDA_ERROR. */
 int mfcg_apply_operator_static(const mfcg_mesh* mesh, int degree, const double* src, double* dst, void* cuda_stream);
+
+/* ---------------------------------------------------------------------------
+ * Batches of independent problems.  Small problems cannot fill the GPU and are
+ * bound by launch latency (Sec. 6: the GPU needs millions of unknowns for its
+ * best throughput); a batch solves many independent problems of any degree and
+ * mesh together: the fused iterations of all members are one CUDA graph with
+ * one branch per member, so their kernels run concurrently and the host
+ * synchronises once per graph for the whole batch.
+ * --------------------------------------------------------------------------- */
+typedef struct mfcg_batch mfcg_batch;
+
+/* mfcg_setup_batch -- sets up `count` problems as mfcg_setup would, member i
+ * with meshes[i], degrees[i] and geoms[i], all with the options *opt (mode
+ * FUSED, precision FP64 or DOUBLE_FLOAT; NULL = defaults) on cuda_stream.
+ *   count   in: 1..4096.
+ *   meshes, degrees, geoms: host arrays of count entries, read during the call.
+ *   out     out: new handle; release with mfcg_destroy_batch.
+ * Errors: those of mfcg_setup for any member (nothing is left allocated),
+ * INVALID_ARG for a mode or precision a batch does not support. */
+int mfcg_setup_batch(int count, const mfcg_mesh* meshes, const int* degrees, const mfcg_geometry* geoms,
+                     const mfcg_options* opt, void* cuda_stream, mfcg_batch** out);
+
+/* mfcg_batch_member -- the problem handle of member i, owned by the batch (valid
+ * until mfcg_destroy_batch; do not destroy it), for mfcg_n_dofs, mfcg_rhs,
+ * mfcg_apply_operator and the reordering helpers. */
+int mfcg_batch_member(mfcg_batch* batch, int i, mfcg_problem** prob);
+
+/* mfcg_cg_solve_batch -- solves A_i x_i = b_i for every member i with the
+ * fused Algorithm 5, each with its own convergence test ||r_k|| <= rtol ||b_i||
+ * (rtol = 0: exactly maxit iterations each), like mfcg_cg_solve.
+ *   b, x    in: host arrays of count DEVICE pointers (n_i doubles each, the
+ *           member's tile-blocked order); x_i in: initial guess, out: solution.
+ *   infos   out: host array of count records (may be NULL).
+ * Returns OK when every member converged (or rtol = 0), else the first
+ * non-OK member status (per-member status in infos[i].status). */
+int mfcg_cg_solve_batch(mfcg_batch* batch, const double* const* b, double* const* x, double rtol, int maxit,
+                        mfcg_solve_info* infos);
+
+/* mfcg_destroy_batch -- destroys every member and the batch; NULL is accepted. */
+int mfcg_destroy_batch(mfcg_batch* batch);
 
 /* mfcg_status_string -- static description of a status code. */
 const char* mfcg_status_string(int status);

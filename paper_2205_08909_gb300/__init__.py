@@ -21,7 +21,7 @@ import torch
 from . import _binding
 from ._binding import MfcgError, SolveInfo  # noqa: F401
 
-__all__ = ["Problem", "MfcgError", "SolveInfo"]
+__all__ = ["Problem", "Batch", "MfcgError", "SolveInfo"]
 
 
 def _ptr(t: torch.Tensor) -> ctypes.c_void_p:
@@ -40,14 +40,18 @@ class Problem:
     "semi_fused" (Algorithm 5 as separate pre / operator / post kernels);
     preconditioner: "jacobi" or "none" (Algorithm 4);
     precision: "fp64", "double_float" (FP32 pairs, ~48 bits) or "fp32_inner"
-    (FP64 defect correction around an FP32 fused CG, inner_rtol per cycle).
+    (FP64 defect correction around an FP32 fused CG, inner_rtol per cycle);
+    components: 1 (scalar) or 2..3 (vector-valued operator, components stored
+    one after another; fused mode); operator: "laplace" (BP3/BP4) or "mass"
+    (BP1/BP2; affine or geometry="deformed").
     Vectors are float64 CUDA tensors in the library's tile-blocked order.
     """
 
     def __init__(self, degree: int, cells, amplitude: float = 0.0, geometry: str = "affine",
                  coefficient: str = "constant", mode: str = "fused", precision: str = "fp64",
                  preconditioner: str = "jacobi", inner_rtol: float = 0.0, graph_iterations: int = 0,
-                 instrument: bool = False, tile=None, stream: torch.cuda.Stream | None = None):
+                 instrument: bool = False, tile=None, components: int = 1, operator: str = "laplace",
+                 stream: torch.cuda.Stream | None = None):
         if not torch.cuda.is_available():
             raise RuntimeError("paper_2205_08909_gb300 needs a CUDA device (no CPU fallback)")
         self._lib = _binding.load()
@@ -64,6 +68,9 @@ class Problem:
         opt.inner_rtol = float(inner_rtol)
         opt.graph_iterations = int(graph_iterations)
         opt.instrument = 1 if instrument else 0
+        opt.components = int(components)
+        opt.operator_kind = _binding.OPERATOR[operator]
+        self.components = int(components)
         if tile is not None:
             for d in range(3):
                 opt.tile[d] = int(tile[d])
@@ -141,8 +148,102 @@ class Problem:
         return out
 
     def close(self) -> None:
-        if getattr(self, "_h", None):
+        if getattr(self, "_h", None) and not getattr(self, "_borrowed", False):
             self._lib.mfcg_destroy(self._h)
+        self._h = None
+
+    @classmethod
+    def _member(cls, lib, handle, degree: int, cells, stream) -> "Problem":
+        """View of a batch member (owned by the batch)."""
+        self = cls.__new__(cls)
+        self._lib, self._h, self._borrowed = lib, handle, True
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream
+        self.degree, self.cells = int(degree), tuple(cells)
+        self.components = 1
+        n = ctypes.c_int64()
+        _binding.check("mfcg_n_dofs", lib.mfcg_n_dofs(handle, ctypes.byref(n)))
+        self.n_dofs = int(n.value)
+        return self
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Batch:
+    """Independent problems solved together: the fused iterations of all members
+    run as one CUDA graph with one branch per member (mfcg_setup_batch).
+
+    specs: list of dicts with keys degree, cells and optionally amplitude,
+    geometry, coefficient; precision: "fp64" or "double_float".
+    members[i] is a Problem view for rhs / apply_operator / reordering.
+    """
+
+    def __init__(self, specs, precision: str = "fp64", graph_iterations: int = 0,
+                 stream: torch.cuda.Stream | None = None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("paper_2205_08909_gb300 needs a CUDA device (no CPU fallback)")
+        self._lib = _binding.load()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        count = len(specs)
+        meshes = (_binding.Mesh * count)()
+        geoms = (_binding.Geometry * count)()
+        degrees = (ctypes.c_int * count)()
+        cells_list = []
+        for i, sp in enumerate(specs):
+            c = sp["cells"]
+            c = tuple(int(v) for v in (c if hasattr(c, "__len__") else (c,) * 3))
+            cells_list.append(c)
+            amp = float(sp.get("amplitude", 0.0))
+            geometry = sp.get("geometry", "deformed" if amp != 0.0 else "affine")
+            meshes[i] = _binding.Mesh(c[0], c[1], c[2], amp)
+            geoms[i] = _binding.Geometry(_binding.GEOM[geometry], _binding.COEF[sp.get("coefficient", "constant")])
+            degrees[i] = int(sp["degree"])
+        opt = _binding.Options()
+        opt.mode = _binding.MODE["fused"]
+        opt.precision = _binding.PRECISION[precision]
+        opt.graph_iterations = int(graph_iterations)
+        handle = ctypes.c_void_p()
+        _binding.check("mfcg_setup_batch", self._lib.mfcg_setup_batch(
+            count, meshes, degrees, geoms, ctypes.byref(opt), ctypes.c_void_p(self.stream.cuda_stream),
+            ctypes.byref(handle)))
+        self._h = handle
+        self.members = []
+        for i in range(count):
+            mh = ctypes.c_void_p()
+            _binding.check("mfcg_batch_member", self._lib.mfcg_batch_member(self._h, i, ctypes.byref(mh)))
+            self.members.append(Problem._member(self._lib, mh, degrees[i], cells_list[i], self.stream))
+
+    def cg_solve(self, bs, xs=None, rtol: float = 1e-10, maxit: int = 100000, allow_not_converged: bool = False):
+        """Solves every member; xs (if given) are the initial guesses and are
+        overwritten.  Returns (xs, list of info dicts)."""
+        count = len(self.members)
+        if xs is None:
+            xs = [torch.zeros(m.n_dofs, dtype=torch.float64, device=m.device) for m in self.members]
+        if len(bs) != count or len(xs) != count:
+            raise ValueError(f"expected {count} right-hand sides and solutions")
+        bp = (ctypes.c_void_p * count)(*[_ptr(m._vec(b, "b")).value for m, b in zip(self.members, bs)])
+        xp = (ctypes.c_void_p * count)(*[_ptr(m._vec(x, "x")).value for m, x in zip(self.members, xs)])
+        infos = (SolveInfo * count)()
+        allowed = (_binding.OK, _binding.NOT_CONVERGED) if allow_not_converged else (_binding.OK,)
+        st = self._lib.mfcg_cg_solve_batch(self._h, bp, xp, float(rtol), int(maxit), infos)
+        _binding.check("mfcg_cg_solve_batch", st, allowed)
+        return xs, [infos[i].as_dict() for i in range(count)]
+
+    def close(self) -> None:
+        for m in getattr(self, "members", []):
+            m._h = None
+        if getattr(self, "_h", None):
+            self._lib.mfcg_destroy_batch(self._h)
             self._h = None
 
     def __del__(self):

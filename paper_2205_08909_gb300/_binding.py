@@ -24,6 +24,7 @@ COEF = {"constant": 0, "sin_x": 1}
 MODE = {"fused": 0, "unfused": 1, "semi_fused": 2}
 PRECONDITIONER = {"jacobi": 0, "none": 1}
 PRECISION = {"fp64": 0, "double_float": 1, "fp32_inner": 2}
+OPERATOR = {"laplace": 0, "mass": 1}
 
 
 class Mesh(ctypes.Structure):
@@ -37,7 +38,7 @@ class Geometry(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("graph_iterations", ctypes.c_int32), ("instrument", ctypes.c_int32),
                 ("tile", ctypes.c_int32 * 3), ("precision", ctypes.c_int32), ("preconditioner", ctypes.c_int32),
-                ("inner_rtol", ctypes.c_double)]
+                ("inner_rtol", ctypes.c_double), ("components", ctypes.c_int32), ("operator_kind", ctypes.c_int32)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -86,6 +87,11 @@ def load() -> ctypes.CDLL:
         "mfcg_to_lexicographic": [vp, vp, vp],
         "mfcg_from_lexicographic": [vp, vp, vp],
         "mfcg_destroy": [vp],
+        "mfcg_setup_batch": [i32, ctypes.POINTER(Mesh), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(Geometry),
+                             ctypes.POINTER(Options), vp, ctypes.POINTER(vp)],
+        "mfcg_batch_member": [vp, i32, ctypes.POINTER(vp)],
+        "mfcg_cg_solve_batch": [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), f64, i32, ctypes.POINTER(SolveInfo)],
+        "mfcg_destroy_batch": [vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)

@@ -11,6 +11,8 @@
 // the host replays it and reads the device-side convergence flag only once per
 // graph, one graph behind, so there is no per-iteration host synchronisation.
 #include <algorithm>
+#include <array>
+#include <chrono>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -39,6 +41,8 @@ struct mfcg_problem {
   TileGeom g{};
   OperatorCoeffs c{};
   int geom_kind = GEOM_AFFINE;
+  int ncomp = 1;           // components of the vector-valued operator
+  int op_kind = OP_LAPLACE;
   int op_prec = PREC_F64;  // apply_operator and FP64-accurate residuals
   int cg_prec = PREC_F64;  // fused CG iterations
   // fused CG vectors in the storage type of cg_prec (ping-pong r, p, v), x, M^{-1}
@@ -75,6 +79,23 @@ struct mfcg_problem {
   cudaGraphExec_t graph_semi = nullptr;
   int64_t launches = 0;
   std::vector<void*> owned;  // every device allocation
+  int64_t nv() const { return ncomp * g.n_dofs; }  // length of every vector of the ABI
+};
+
+// A batch: independent member problems whose fused iterations are captured
+// as one graph with one branch per member.
+struct mfcg_batch {
+  int device = 0;
+  cudaStream_t user = nullptr;
+  cudaStream_t exec = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_fork = nullptr;
+  std::vector<mfcg_problem*> members;
+  std::vector<cudaEvent_t> ev_join;  // one per member
+  int graph_iters = 16;
+  cudaGraphExec_t graph = nullptr;
+  CGState** d_states = nullptr;      // device array of the members' state pointers
+  int* d_done = nullptr;             // device: done flag per member
+  int* h_done = nullptr;             // pinned: two slots of count flags
 };
 
 namespace {
@@ -118,6 +139,10 @@ TileArgs base_args(const mfcg_problem* P, int prec, const void* geo) {
   a.geom = P->geom_kind;
   a.prec = prec;
   a.tail_ctas = P->tail_ctas;
+  a.ncomp = P->ncomp;
+  a.op_kind = P->op_kind;
+  a.comp_stride = P->g.n_dofs;
+  a.shell_comp_stride = P->g.n_tiles * P->g.face_stride;
   return a;
 }
 
@@ -125,6 +150,7 @@ TileArgs base_args(const mfcg_problem* P, int prec, const void* geo) {
 int run_pass(mfcg_problem* P, int mode, const double* src, double* dst) {
   const int prec = mode == MODE_OPERATOR ? P->op_prec : PREC_F64;
   TileArgs a = base_args(P, prec, mode == MODE_OPERATOR ? P->geo_op : P->geo);
+  if (mode != MODE_OPERATOR) a.ncomp = 1;  // diagonal and right-hand side of the scalar operator
   a.in0 = src;
   a.out0 = dst;
   CK(launch_tile(P->degree, mode, a, P->c, P->exec));
@@ -154,7 +180,7 @@ int enqueue_fused_iteration(mfcg_problem* P, int odd, cudaEvent_t t0, cudaEvent_
 
 UnfusedArgs unfused_args(mfcg_problem* P) {
   UnfusedArgs u{};
-  u.n = P->g.n_dofs;
+  u.n = P->nv();
   u.diag_inv = P->diag_inv;
   u.x = P->x;
   u.r = P->ur;
@@ -188,7 +214,7 @@ int enqueue_unfused_iteration(mfcg_problem* P, cudaEvent_t t0, cudaEvent_t t1) {
 
 // semi-fused Algorithm 5: "pre" kernel, operator (tile + tail), "post" kernel
 int enqueue_semi_iteration(mfcg_problem* P, cudaEvent_t t0, cudaEvent_t t1) {
-  const int64_t n = P->g.n_dofs;
+  const int64_t n = P->nv();
   CK(launch_semi_pre(n, P->state, P->x, P->ur, P->up, P->uv, P->diag_inv, P->exec));
   TileArgs a = base_args(P, P->op_prec, P->geo_op);
   a.in0 = P->up;
@@ -307,19 +333,42 @@ int run_iterations(mfcg_problem* P, int kind, int maxit, IterStats& stats) {
 
 // Fused CG (Algorithm 5) in P->cg_prec on the system A x = b with the FP64
 // initial residual r0 and the initial guess already in P->xs.
-int fused_core(mfcg_problem* P, const double* b, const double* r0, double rtol, int maxit, int fixed,
-               IterStats& stats) {
-  const int64_t n = P->g.n_dofs;
+// start-up of the fused CG: scalars from (b, r0), r_0 in the CG precision, p and v zero
+int fused_start(mfcg_problem* P, const double* b, const double* r0, double rtol, int maxit, int fixed) {
+  const int64_t n = P->nv();
   const size_t es = prec_bytes(P->cg_prec);
   CK(launch_cg_init(P->state, b, r0, n, rtol, maxit, fixed, P->partial, 0, P->exec));
   CK(launch_to_prec(P->cg_prec, r0, P->r[0], n, P->exec));
   CK(cudaMemsetAsync(P->p[0], 0, n * es, P->exec));
   CK(cudaMemsetAsync(P->v[0], 0, n * es, P->exec));
   P->launches += 2;
-  int st = run_iterations(P, ITER_FUSED, maxit, stats);
-  if (st != MFCG_OK) return st;
-  CK(launch_finalize_fused(P->cg_prec, n, P->state, P->xs, P->p[0], P->p[1], P->r[0], P->r[1], P->dinv_s, P->exec));
+  return MFCG_OK;
+}
+
+// parity-dependent finalisation of x (Algorithm 5)
+int fused_finish(mfcg_problem* P) {
+  CK(launch_finalize_fused(P->cg_prec, P->nv(), P->state, P->xs, P->p[0], P->p[1], P->r[0], P->r[1], P->dinv_s,
+                           P->exec));
   P->launches += 1;
+  return MFCG_OK;
+}
+
+int fused_core(mfcg_problem* P, const double* b, const double* r0, double rtol, int maxit, int fixed,
+               IterStats& stats) {
+  int st = fused_start(P, b, r0, rtol, maxit, fixed);
+  if (st == MFCG_OK) st = run_iterations(P, ITER_FUSED, maxit, stats);
+  if (st == MFCG_OK) st = fused_finish(P);
+  return st;
+}
+
+// r0 = b - A x0 in FP64 (operator in the operator precision) and x0 in the CG precision
+int fused_initial_residual(mfcg_problem* P, const double* b, const double* x_user) {
+  const int64_t n = P->nv();
+  int st = run_pass(P, MODE_OPERATOR, x_user, P->work);
+  if (st != MFCG_OK) return st;
+  CK(launch_residual(b, P->work, P->work, n, P->exec));
+  CK(launch_to_prec(P->cg_prec, x_user, P->xs, n, P->exec));
+  P->launches += 2;
   return MFCG_OK;
 }
 
@@ -340,7 +389,7 @@ void fill_info(mfcg_problem* P, mfcg_solve_info* info, int status, int iteration
 }
 
 int solve_direct(mfcg_problem* P, const double* b, double* x_user, double rtol, int maxit, mfcg_solve_info* info) {
-  const int64_t n = P->g.n_dofs;
+  const int64_t n = P->nv();
   const int fused = P->opt.mode == MFCG_MODE_FUSED;
   const int64_t launches0 = P->launches;
   const int fixed = rtol == 0.0;
@@ -352,9 +401,10 @@ int solve_direct(mfcg_problem* P, const double* b, double* x_user, double rtol, 
   P->launches += 1;
   if (fused) {
     CK(launch_to_prec(P->cg_prec, x_user, P->xs, n, P->exec));
+    P->launches += 1;
     if ((st = fused_core(P, b, P->work, rtol, maxit, fixed, stats)) != MFCG_OK) return st;
     CK(launch_from_prec(P->cg_prec, P->xs, x_user, n, 0, P->exec));
-    P->launches += 2;
+    P->launches += 1;
   } else if (P->opt.mode == MFCG_MODE_SEMI_FUSED) {
     CK(cudaMemcpyAsync(P->x, x_user, n * sizeof(double), cudaMemcpyDeviceToDevice, P->exec));
     CK(cudaMemcpyAsync(P->ur, P->work, n * sizeof(double), cudaMemcpyDeviceToDevice, P->exec));
@@ -392,7 +442,7 @@ int solve_direct(mfcg_problem* P, const double* b, double* x_user, double rtol, 
 // formed with the FP64 operator and FP64 vectors.
 int solve_defect_correction(mfcg_problem* P, const double* b, double* x_user, double rtol, int maxit,
                             mfcg_solve_info* info) {
-  const int64_t n = P->g.n_dofs;
+  const int64_t n = P->nv();
   const int64_t launches0 = P->launches;
   const double inner = P->opt.inner_rtol > 0.0 ? P->opt.inner_rtol : 1e-3;
   IterStats stats;
@@ -461,7 +511,7 @@ int solve_defect_correction(mfcg_problem* P, const double* b, double* x_user, do
 // rtol == 0 with the FP32 inner form: one correction x += d with exactly maxit
 // inner FP32 iterations on A d = b - A x (benchmark mode of the inner kernel).
 int solve_fixed_inner(mfcg_problem* P, const double* b, double* x_user, int maxit, mfcg_solve_info* info) {
-  const int64_t n = P->g.n_dofs;
+  const int64_t n = P->nv();
   const int64_t launches0 = P->launches;
   const size_t es = prec_bytes(P->cg_prec);
   IterStats stats;
@@ -488,9 +538,274 @@ int solve_impl(mfcg_problem* P, const double* b, double* x_user, double rtol, in
   return solve_direct(P, b, x_user, rtol, maxit, info);
 }
 
+// ------------------------------------------------------------------ tile autotuning
+
+// Candidate tiles around the default edge T of the degree: T^3, T^2 (T-1),
+// T (T-1)^2, (T-1)^3 and (T+1)^3 -- smaller tiles trade halo work for more
+// CTAs per SM, larger ones the reverse.
+std::vector<std::array<int, 3>> tile_candidates(int degree, int geom_kind) {
+  const int T = default_tile(degree, geom_kind);
+  const int lo = degree == 1 ? 2 : 1;
+  std::vector<std::array<int, 3>> c;
+  auto add = [&](int a, int b, int d) {
+    if (a < lo || b < lo || d < lo || a > 16 || b > 16 || d > 16) return;
+    const std::array<int, 3> t{a, b, d};
+    if (std::find(c.begin(), c.end(), t) == c.end()) c.push_back(t);
+  };
+  add(T, T, T);
+  add(T, T, T - 1);
+  add(T, T - 1, T - 1);
+  add(T - 1, T - 1, T - 1);
+  add(T + 1, T + 1, T + 1);
+  return c;
+}
+
+int setup_autotuned(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, mfcg_options o,
+                    void* cuda_stream, mfcg_problem** out) {
+  const int kind = geom->kind == MFCG_GEOM_AFFINE ? GEOM_AFFINE
+                   : (geom->kind == MFCG_GEOM_DEFORMED_TENSOR ? GEOM_TENSOR : GEOM_DEFORMED);
+  std::array<int, 3> best{0, 0, 0};
+  double best_s = 1e300;
+  for (const auto& t : tile_candidates(degree, kind)) {
+    mfcg_options oc = o;
+    oc.instrument = 0;
+    for (int d = 0; d < 3; ++d) oc.tile[d] = t[d];
+    mfcg_problem* Q = nullptr;
+    if (mfcg_setup(mesh, degree, geom, &oc, cuda_stream, &Q) != MFCG_OK) continue;  // e.g. too much shared memory
+    double* b = nullptr;
+    double* x = nullptr;
+    const size_t bytes = (size_t)Q->nv() * sizeof(double);
+    double secs = 1e300;
+    if (cudaMalloc(&b, bytes) == cudaSuccess && cudaMalloc(&x, bytes) == cudaSuccess &&
+        mfcg_rhs(Q, b) == MFCG_OK && cudaMemsetAsync(x, 0, bytes, Q->user) == cudaSuccess &&
+        mfcg_cg_solve(Q, b, x, 0.0, 2 * Q->graph_iters, nullptr) == MFCG_OK) {
+      for (int rep = 0; rep < 2; ++rep) {
+        if (cudaStreamSynchronize(Q->user) != cudaSuccess) break;
+        const auto t0 = std::chrono::steady_clock::now();
+        if (mfcg_cg_solve(Q, b, x, 0.0, 2 * Q->graph_iters, nullptr) != MFCG_OK) break;
+        if (cudaStreamSynchronize(Q->user) != cudaSuccess) break;
+        secs = std::min(secs, std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
+      }
+    }
+    cudaGetLastError();
+    if (b) cudaFree(b);
+    if (x) cudaFree(x);
+    mfcg_destroy(Q);
+    if (secs < best_s) {
+      best_s = secs;
+      best = t;
+    }
+  }
+  if (best[0] == 0) return MFCG_INVALID_ARG;
+  for (int d = 0; d < 3; ++d) o.tile[d] = best[d];
+  return mfcg_setup(mesh, degree, geom, &o, cuda_stream, out);
+}
+
+// ------------------------------------------------------------------ batches
+
+int batch_capture(mfcg_batch* B) {
+  const int count = (int)B->members.size();
+  cudaGraph_t graph;
+  CK(cudaStreamBeginCapture(B->exec, cudaStreamCaptureModeThreadLocal));
+  int st = MFCG_OK;
+  if (cudaEventRecord(B->ev_fork, B->exec) != cudaSuccess) st = MFCG_CUDA_ERROR;
+  for (int i = 0; i < count && st == MFCG_OK; ++i) {
+    mfcg_problem* P = B->members[i];
+    if (cudaStreamWaitEvent(P->exec, B->ev_fork, 0) != cudaSuccess) st = MFCG_CUDA_ERROR;
+    for (int it = 0; it < B->graph_iters && st == MFCG_OK; ++it)
+      st = enqueue_fused_iteration(P, (it & 1) == 0, nullptr, nullptr);
+    if (st == MFCG_OK && (cudaEventRecord(B->ev_join[i], P->exec) != cudaSuccess ||
+                          cudaStreamWaitEvent(B->exec, B->ev_join[i], 0) != cudaSuccess))
+      st = MFCG_CUDA_ERROR;
+  }
+  if (st == MFCG_OK && launch_gather_done(B->d_states, count, B->d_done, B->exec) != cudaSuccess)
+    st = MFCG_CUDA_ERROR;
+  const cudaError_t e = cudaStreamEndCapture(B->exec, &graph);
+  if (st != MFCG_OK || e != cudaSuccess) return MFCG_CUDA_ERROR;
+  const cudaError_t e2 = cudaGraphInstantiate(&B->graph, graph, 0);
+  cudaGraphDestroy(graph);
+  return e2 == cudaSuccess ? MFCG_OK : MFCG_CUDA_ERROR;
+}
+
+// every member's stream waits for the batch stream
+int batch_fork(mfcg_batch* B) {
+  CK(cudaEventRecord(B->ev_fork, B->exec));
+  for (mfcg_problem* P : B->members) CK(cudaStreamWaitEvent(P->exec, B->ev_fork, 0));
+  return MFCG_OK;
+}
+
+// the batch stream waits for every member's stream
+int batch_join(mfcg_batch* B) {
+  for (size_t i = 0; i < B->members.size(); ++i) {
+    CK(cudaEventRecord(B->ev_join[i], B->members[i]->exec));
+    CK(cudaStreamWaitEvent(B->exec, B->ev_join[i], 0));
+  }
+  return MFCG_OK;
+}
+
+// graphs of G iterations of every member until all done flags are set or maxit
+int batch_run_iterations(mfcg_batch* B, int maxit) {
+  const int count = (int)B->members.size();
+  int st;
+  if (!B->graph && (st = batch_capture(B)) != MFCG_OK) return st;
+  const int G = B->graph_iters;
+  const int n_graphs = (maxit + G - 1) / G;
+  cudaEvent_t evs[2];
+  CK(cudaEventCreateWithFlags(&evs[0], cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&evs[1], cudaEventDisableTiming));
+  int launched = 0, checked = 0;
+  bool finished = n_graphs == 0;
+  while (!finished) {
+    while (launched < n_graphs && launched < checked + 2) {
+      CK(cudaGraphLaunch(B->graph, B->exec));
+      CK(cudaMemcpyAsync(B->h_done + (launched & 1) * count, B->d_done, count * sizeof(int), cudaMemcpyDeviceToHost,
+                         B->exec));
+      CK(cudaEventRecord(evs[launched & 1], B->exec));
+      for (mfcg_problem* P : B->members) P->launches += 2LL * G;
+      ++launched;
+    }
+    if (checked >= launched) break;
+    CK(cudaEventSynchronize(evs[checked & 1]));
+    const int* f = B->h_done + (checked & 1) * count;
+    bool all = true;
+    for (int i = 0; i < count && all; ++i) all = f[i] != 0;
+    if (all) finished = true;
+    ++checked;
+    if (checked >= n_graphs) finished = true;
+  }
+  CK(cudaStreamSynchronize(B->exec));
+  cudaEventDestroy(evs[0]);
+  cudaEventDestroy(evs[1]);
+  return MFCG_OK;
+}
+
+int batch_solve(mfcg_batch* B, const double* const* b, double* const* x, double rtol, int maxit,
+                mfcg_solve_info* infos) {
+  const int count = (int)B->members.size();
+  const int fixed = rtol == 0.0;
+  std::vector<int64_t> launches0(count);
+  for (int i = 0; i < count; ++i) launches0[i] = B->members[i]->launches;
+  int st;
+  // start-up of every member on its own stream
+  if ((st = batch_fork(B)) != MFCG_OK) return st;
+  for (int i = 0; i < count; ++i) {
+    mfcg_problem* P = B->members[i];
+    if ((st = fused_initial_residual(P, b[i], x[i])) != MFCG_OK) return st;
+    if ((st = fused_start(P, b[i], P->work, rtol, maxit, fixed)) != MFCG_OK) return st;
+  }
+  if ((st = batch_join(B)) != MFCG_OK) return st;
+  if ((st = batch_run_iterations(B, maxit)) != MFCG_OK) return st;
+  // finalisation of every member on its own stream
+  if ((st = batch_fork(B)) != MFCG_OK) return st;
+  for (int i = 0; i < count; ++i) {
+    mfcg_problem* P = B->members[i];
+    if ((st = fused_finish(P)) != MFCG_OK) return st;
+    CK(launch_from_prec(P->cg_prec, P->xs, x[i], P->nv(), 0, P->exec));
+    CK(cudaMemcpyAsync(P->h_state, P->state, sizeof(CGState), cudaMemcpyDeviceToHost, P->exec));
+    P->launches += 1;
+  }
+  if ((st = batch_join(B)) != MFCG_OK) return st;
+  CK(cudaStreamSynchronize(B->exec));
+  int status = MFCG_OK;
+  for (int i = 0; i < count; ++i) {
+    mfcg_problem* P = B->members[i];
+    const CGState& S = *P->h_state;
+    int si = MFCG_OK;
+    if (S.done == 3) si = MFCG_BREAKDOWN;
+    else if (S.done != 1 && !fixed) si = MFCG_NOT_CONVERGED;
+    if (status == MFCG_OK) status = si;
+    if (infos) fill_info(P, &infos[i], si, S.iterations, IterStats{}, launches0[i], 0);
+  }
+  return status;
+}
+
 }  // namespace
 
 extern "C" {
+
+int mfcg_setup_batch(int count, const mfcg_mesh* meshes, const int* degrees, const mfcg_geometry* geoms,
+                     const mfcg_options* opt, void* cuda_stream, mfcg_batch** out) {
+  if (!out) return MFCG_INVALID_ARG;
+  *out = nullptr;
+  if (count < 1 || count > 4096 || !meshes || !degrees || !geoms) return MFCG_INVALID_ARG;
+  mfcg_options o{};
+  if (opt) o = *opt;
+  if (o.mode != MFCG_MODE_FUSED || (o.precision != MFCG_PREC_FP64 && o.precision != MFCG_PREC_DOUBLE_FLOAT) ||
+      o.instrument)
+    return MFCG_INVALID_ARG;
+  mfcg_batch* B = new (std::nothrow) mfcg_batch();
+  if (!B) return MFCG_OUT_OF_MEMORY;
+  auto fail = [&](int code) {
+    mfcg_destroy_batch(B);
+    return code;
+  };
+  if (cudaGetDevice(&B->device) != cudaSuccess) return fail(MFCG_CUDA_ERROR);
+  B->user = (cudaStream_t)cuda_stream;
+  B->graph_iters = o.graph_iterations ? o.graph_iterations : 16;
+  if (B->graph_iters < 0 || (B->graph_iters & 1)) return fail(MFCG_INVALID_ARG);
+  B->members.reserve(count);
+  for (int i = 0; i < count; ++i) {
+    mfcg_problem* P = nullptr;
+    const int st = mfcg_setup(&meshes[i], degrees[i], &geoms[i], &o, cuda_stream, &P);
+    if (st != MFCG_OK) return fail(st);
+    B->members.push_back(P);
+  }
+  if (cudaStreamCreateWithFlags(&B->exec, cudaStreamNonBlocking) != cudaSuccess) return fail(MFCG_CUDA_ERROR);
+  if (cudaEventCreateWithFlags(&B->ev_in, cudaEventDisableTiming) != cudaSuccess) return fail(MFCG_CUDA_ERROR);
+  if (cudaEventCreateWithFlags(&B->ev_out, cudaEventDisableTiming) != cudaSuccess) return fail(MFCG_CUDA_ERROR);
+  if (cudaEventCreateWithFlags(&B->ev_fork, cudaEventDisableTiming) != cudaSuccess) return fail(MFCG_CUDA_ERROR);
+  B->ev_join.assign(count, nullptr);
+  for (auto& e : B->ev_join)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return fail(MFCG_CUDA_ERROR);
+  if (cudaMalloc(&B->d_states, count * sizeof(CGState*)) != cudaSuccess) return fail(MFCG_OUT_OF_MEMORY);
+  if (cudaMalloc(&B->d_done, count * sizeof(int)) != cudaSuccess) return fail(MFCG_OUT_OF_MEMORY);
+  if (cudaMallocHost(&B->h_done, 2 * count * sizeof(int)) != cudaSuccess) return fail(MFCG_OUT_OF_MEMORY);
+  std::vector<CGState*> states(count);
+  for (int i = 0; i < count; ++i) states[i] = B->members[i]->state;
+  if (cudaMemcpy(B->d_states, states.data(), count * sizeof(CGState*), cudaMemcpyHostToDevice) != cudaSuccess)
+    return fail(MFCG_CUDA_ERROR);
+  *out = B;
+  return MFCG_OK;
+}
+
+int mfcg_batch_member(mfcg_batch* B, int i, mfcg_problem** prob) {
+  if (!B || !prob || i < 0 || i >= (int)B->members.size()) return MFCG_INVALID_ARG;
+  *prob = B->members[i];
+  return MFCG_OK;
+}
+
+int mfcg_cg_solve_batch(mfcg_batch* B, const double* const* b, double* const* x, double rtol, int maxit,
+                        mfcg_solve_info* infos) {
+  if (!B || !b || !x || maxit < 0 || !(rtol >= 0.0)) return MFCG_INVALID_ARG;
+  for (size_t i = 0; i < B->members.size(); ++i)
+    if (!b[i] || !x[i] || b[i] == x[i]) return MFCG_INVALID_ARG;
+  CK(cudaSetDevice(B->device));
+  CK(cudaEventRecord(B->ev_in, B->user));
+  CK(cudaStreamWaitEvent(B->exec, B->ev_in, 0));
+  const int st = batch_solve(B, b, x, rtol, maxit, infos);
+  CK(cudaEventRecord(B->ev_out, B->exec));
+  CK(cudaStreamWaitEvent(B->user, B->ev_out, 0));
+  return st;
+}
+
+int mfcg_destroy_batch(mfcg_batch* B) {
+  if (!B) return MFCG_OK;
+  cudaSetDevice(B->device);
+  if (B->exec) cudaStreamSynchronize(B->exec);
+  if (B->graph) cudaGraphExecDestroy(B->graph);
+  for (mfcg_problem* P : B->members) mfcg_destroy(P);
+  for (cudaEvent_t e : B->ev_join)
+    if (e) cudaEventDestroy(e);
+  if (B->ev_in) cudaEventDestroy(B->ev_in);
+  if (B->ev_out) cudaEventDestroy(B->ev_out);
+  if (B->ev_fork) cudaEventDestroy(B->ev_fork);
+  if (B->d_states) cudaFree(B->d_states);
+  if (B->d_done) cudaFree(B->d_done);
+  if (B->h_done) cudaFreeHost(B->h_done);
+  if (B->exec) cudaStreamDestroy(B->exec);
+  delete B;
+  return MFCG_OK;
+}
 
 const char* mfcg_status_string(int status) {
   switch (status) {
@@ -544,6 +859,11 @@ int mfcg_setup(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, con
   if (o.precision < MFCG_PREC_FP64 || o.precision > MFCG_PREC_FP32_INNER) return MFCG_INVALID_ARG;
   if (o.precision == MFCG_PREC_FP32_INNER && o.mode != MFCG_MODE_FUSED) return MFCG_INVALID_ARG;
   if (!(o.inner_rtol >= 0.0 && o.inner_rtol < 1.0)) return MFCG_INVALID_ARG;
+  if (o.components < 0 || o.components > 3 || (o.components > 1 && o.mode != MFCG_MODE_FUSED))
+    return MFCG_INVALID_ARG;
+  if (o.operator_kind != MFCG_OP_LAPLACE && o.operator_kind != MFCG_OP_MASS) return MFCG_INVALID_ARG;
+  if (o.operator_kind == MFCG_OP_MASS && geom->kind == MFCG_GEOM_DEFORMED_TENSOR) return MFCG_INVALID_ARG;
+  if (o.tile[0] == -1 && o.tile[1] == -1 && o.tile[2] == -1) return setup_autotuned(mesh, degree, geom, o, cuda_stream, out);
   for (int d = 0; d < 3; ++d)
     if (o.tile[d] < 0 || o.tile[d] > 16) return MFCG_INVALID_ARG;
   const int64_t nn[3] = {(int64_t)degree * mesh->nx + 1, (int64_t)degree * mesh->ny + 1, (int64_t)degree * mesh->nz + 1};
@@ -562,6 +882,8 @@ int mfcg_setup(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, con
   P->mesh = *mesh;
   P->geom = *geom;
   P->opt = o;
+  P->ncomp = o.components ? o.components : 1;
+  P->op_kind = o.operator_kind == MFCG_OP_MASS ? OP_MASS : OP_LAPLACE;
   P->geom_kind = geom->kind == MFCG_GEOM_AFFINE ? GEOM_AFFINE
                   : (geom->kind == MFCG_GEOM_DEFORMED_TENSOR ? GEOM_TENSOR : GEOM_DEFORMED);
   // the defect correction forms its outer residual with the native FP64
@@ -596,8 +918,8 @@ int mfcg_setup(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, con
   const double h[3] = {1.0 / N[0], 1.0 / N[1], 1.0 / N[2]};
   build_coeffs(degree, h, mesh->amplitude, geom->coefficient, P->c);
 
-  const int64_t n = g.n_dofs;
-  const int64_t n8 = n * 8;
+  const int64_t n = g.n_dofs;     // nodes (scalar set-up passes)
+  const int64_t n8 = P->nv() * 8; // bytes of an FP64 vector of the ABI
   const int fused = o.mode == MFCG_MODE_FUSED;
   if (fused) {
     for (int i = 0; i < 2 && st == MFCG_OK; ++i) {
@@ -618,7 +940,7 @@ int mfcg_setup(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, con
   if (st == MFCG_OK) st = alloc_bytes(P, &P->work, n8);
   if (st == MFCG_OK) st = alloc_bytes(P, &P->diag, n8);
   if (st == MFCG_OK) st = alloc_bytes(P, &P->diag_inv, n8);
-  if (st == MFCG_OK) st = alloc_bytes(P, &P->shell, g.n_tiles * g.face_stride * 8);
+  if (st == MFCG_OK) st = alloc_bytes(P, &P->shell, P->ncomp * g.n_tiles * g.face_stride * 8);
   const int64_t nparts = std::max<int64_t>(g.n_tiles + P->tail_ctas, 152 * 8);
   if (st == MFCG_OK) st = alloc_bytes(P, &P->partial, nparts * 8 * 8);
   const int64_t ngeo =
@@ -648,12 +970,19 @@ int mfcg_setup(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, con
   }
   // Jacobi preconditioner: exact diagonal and its inverse (FP64, converted for the fused CG)
   if ((st = run_pass(P, MODE_DIAG, nullptr, P->diag)) != MFCG_OK) return fail(st);
+  // vector-valued operator: every component has the scalar diagonal (the
+  // fused kernels read the first copy for all components)
+  for (int comp = 1; comp < P->ncomp; ++comp)
+    if (cudaMemcpyAsync(P->diag + comp * n, P->diag, n * sizeof(double), cudaMemcpyDeviceToDevice, P->exec) !=
+        cudaSuccess)
+      return fail(MFCG_CUDA_ERROR);
+  const int64_t nvec = P->nv();
   if (o.preconditioner == MFCG_PRECOND_NONE) {
-    if (launch_fill(P->diag_inv, 1.0, n, P->exec) != cudaSuccess) return fail(MFCG_CUDA_ERROR);
-  } else if (launch_invert(P->diag, P->diag_inv, n, P->exec) != cudaSuccess) {
+    if (launch_fill(P->diag_inv, 1.0, nvec, P->exec) != cudaSuccess) return fail(MFCG_CUDA_ERROR);
+  } else if (launch_invert(P->diag, P->diag_inv, nvec, P->exec) != cudaSuccess) {
     return fail(MFCG_CUDA_ERROR);
   }
-  if (fused && launch_to_prec(P->cg_prec, P->diag_inv, P->dinv_s, n, P->exec) != cudaSuccess)
+  if (fused && launch_to_prec(P->cg_prec, P->diag_inv, P->dinv_s, nvec, P->exec) != cudaSuccess)
     return fail(MFCG_CUDA_ERROR);
   if (cudaStreamSynchronize(P->exec) != cudaSuccess) return fail(MFCG_CUDA_ERROR);
   if (leave(P) != MFCG_OK) return fail(MFCG_CUDA_ERROR);
@@ -663,7 +992,7 @@ int mfcg_setup(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, con
 
 int mfcg_n_dofs(const mfcg_problem* P, int64_t* n) {
   if (!P || !n) return MFCG_INVALID_ARG;
-  *n = P->g.n_dofs;
+  *n = P->nv();
   return MFCG_OK;
 }
 
@@ -679,7 +1008,7 @@ int mfcg_diagonal(mfcg_problem* P, double* diag) {
   if (!P || !diag) return MFCG_INVALID_ARG;
   int st;
   if ((st = enter(P)) != MFCG_OK) return st;
-  CK(cudaMemcpyAsync(diag, P->diag, P->g.n_dofs * sizeof(double), cudaMemcpyDeviceToDevice, P->exec));
+  CK(cudaMemcpyAsync(diag, P->diag, P->nv() * sizeof(double), cudaMemcpyDeviceToDevice, P->exec));
   return leave(P);
 }
 
@@ -688,6 +1017,9 @@ int mfcg_rhs(mfcg_problem* P, double* b) {
   int st;
   if ((st = enter(P)) != MFCG_OK) return st;
   if ((st = run_pass(P, MODE_RHS, nullptr, b)) != MFCG_OK) return st;
+  // component c of a vector-valued problem: (c + 1) times the scalar b (u*_c = (c + 1) u*)
+  for (int comp = 1; comp < P->ncomp; ++comp)
+    CK(launch_scale(b, b + comp * P->g.n_dofs, (double)(comp + 1), P->g.n_dofs, P->exec));
   return leave(P);
 }
 
@@ -703,7 +1035,7 @@ int mfcg_cg_solve(mfcg_problem* P, const double* b, double* x, double rtol, int 
 int mfcg_cg_solve_host(mfcg_problem* P, const double* b_host, double* x_host, double rtol, int maxit,
                        mfcg_solve_info* info) {
   if (!P || !b_host || !x_host || maxit < 0 || !(rtol >= 0.0)) return MFCG_INVALID_ARG;
-  const int64_t n = P->g.n_dofs;
+  const int64_t n = P->nv();
   int st;
   if ((st = enter(P)) != MFCG_OK) return st;
   if (!P->bdev && (st = alloc_bytes(P, &P->bdev, n * 8)) != MFCG_OK) return st;
@@ -722,7 +1054,8 @@ int mfcg_to_lexicographic(mfcg_problem* P, const double* in, double* out) {
   if (!P || !in || !out || in == out) return MFCG_INVALID_ARG;
   int st;
   if ((st = enter(P)) != MFCG_OK) return st;
-  CK(launch_reorder(P->g, in, out, 1, P->exec));
+  for (int comp = 0; comp < P->ncomp; ++comp)
+    CK(launch_reorder(P->g, in + comp * P->g.n_dofs, out + comp * P->g.n_dofs, 1, P->exec));
   return leave(P);
 }
 
@@ -730,7 +1063,8 @@ int mfcg_from_lexicographic(mfcg_problem* P, const double* in, double* out) {
   if (!P || !in || !out || in == out) return MFCG_INVALID_ARG;
   int st;
   if ((st = enter(P)) != MFCG_OK) return st;
-  CK(launch_reorder(P->g, in, out, 0, P->exec));
+  for (int comp = 0; comp < P->ncomp; ++comp)
+    CK(launch_reorder(P->g, in + comp * P->g.n_dofs, out + comp * P->g.n_dofs, 0, P->exec));
   return leave(P);
 }
 

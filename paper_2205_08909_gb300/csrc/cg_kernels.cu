@@ -282,6 +282,27 @@ unsigned grid_for(int64_t n) {
 
 int vec_grid(int64_t n) { return (int)grid_for(n); }
 
+// done flags of a batch of CG states into one array (one read-back per batch)
+__global__ void gather_done_kernel(const CGState* const* states, int count, int* done) {
+  for (int i = blockIdx.x * kVecThreads + threadIdx.x; i < count; i += gridDim.x * kVecThreads)
+    done[i] = states[i]->done;
+}
+
+cudaError_t launch_gather_done(const CGState* const* states, int count, int* done, cudaStream_t s) {
+  gather_done_kernel<<<(count + kVecThreads - 1) / kVecThreads, kVecThreads, 0, s>>>(states, count, done);
+  return cudaGetLastError();
+}
+
+__global__ void scale_kernel(const double* in, double* out, double factor, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)kVecThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVecThreads)
+    out[i] = factor * in[i];
+}
+
+cudaError_t launch_scale(const double* in, double* out, double factor, int64_t n, cudaStream_t s) {
+  scale_kernel<<<grid_for(n), kVecThreads, 0, s>>>(in, out, factor, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_fill(double* v, double value, int64_t n, cudaStream_t s) {
   fill_kernel<<<grid_for(n), kVecThreads, 0, s>>>(v, value, n);
   return cudaGetLastError();

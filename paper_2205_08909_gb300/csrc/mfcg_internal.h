@@ -263,14 +263,18 @@ enum GeomKind { GEOM_AFFINE = 0, GEOM_DEFORMED = 1, GEOM_TENSOR = 2 };
 // values stored per quadrature point by the deformed geometry kinds
 __host__ __device__ constexpr int geo_values(int geom) { return geom == GEOM_TENSOR ? 6 : 10; }
 
-enum MatId { MAT_M = 0, MAT_K0 = 1, MAT_K1 = 2, MAT_K2 = 3, MAT_S = 4, MAT_DC = 5, NMAT = 6 };
+enum MatId { MAT_M = 0, MAT_K0 = 1, MAT_K1 = 2, MAT_K2 = 3, MAT_S = 4, MAT_DC = 5, MAT_MV = 6, NMAT = 7 };
+
+// operator of the problem: Laplacian (Eq. 5) or mass matrix
+enum OpKind { OP_LAPLACE = 0, OP_MASS = 1 };
 constexpr int kMat = (kMaxDegree + 1) * (kMaxDegree + 1);
 
 struct OperatorCoeffs {
   // 1D matrices, row-major (P+1)x(P+1): MAT_M the reference mass matrix,
   // MAT_K0..2 the reference stiffness scaled per direction for box cells
   // (h_y h_z / h_x, ...), MAT_S the interpolation from the Gauss-Lobatto
-  // nodes to the Gauss points, MAT_DC the Gauss collocation derivative.
+  // nodes to the Gauss points, MAT_DC the Gauss collocation derivative,
+  // MAT_MV the mass matrix scaled by the cell volume h_x h_y h_z.
   double mat[NMAT][kMat];
   // products of 1D tables used by the exact diagonal: SS = S.*S, DS = D.*S,
   // DD = D.*D with D[q][a] = L_a'(g_q)
@@ -308,6 +312,11 @@ struct TileArgs {
   TailDiv tdiv;          // divisors of the tail enumeration
   int geom;              // GeomKind
   int prec;              // Prec (precision.cuh)
+  int ncomp;             // components of the vector-valued operator (1: scalar); the vectors hold
+                         // them one after another, comp_stride nodes apart; diag_inv is shared
+  int64_t comp_stride;   // nodes per component (= g.n_dofs)
+  int64_t shell_comp_stride;  // shell elements per component (= g.n_tiles * g.face_stride)
+  int op_kind;           // OpKind
   int tail_ctas;
 };
 
@@ -341,6 +350,8 @@ cudaError_t launch_unfused_axpy(int which, const UnfusedArgs& a, cudaStream_t s)
 cudaError_t launch_cg_init(CGState* st, const double* b, const double* r0, int64_t n, double rtol, int maxit,
                            int fixed, double* partial, int n_ctas, cudaStream_t s);
 cudaError_t launch_residual(const double* b, const double* ax, double* r, int64_t n, cudaStream_t s);
+cudaError_t launch_scale(const double* in, double* out, double factor, int64_t n, cudaStream_t s);
+cudaError_t launch_gather_done(const CGState* const* states, int count, int* done, cudaStream_t s);
 cudaError_t launch_finalize_fused(int prec, int64_t n, CGState* st, void* x, const void* p0, const void* p1,
                                   const void* r0, const void* r1, const void* diag_inv, cudaStream_t s);
 cudaError_t launch_to_prec(int prec, const double* in, void* out, int64_t n, cudaStream_t s);

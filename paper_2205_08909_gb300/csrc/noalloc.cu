@@ -44,7 +44,7 @@ int default_affine_tile(int p) {
 template <int P>
 cudaError_t launch_static_operator(const TileArgs& a, const OperatorCoeffs& c, cudaStream_t s, size_t& smem_set) {
   auto tile = tile_kernel<P, MODE_OPERATOR, GEOM_AFFINE, PREC_F64>;
-  const size_t smem = tile_smem_elems(P, GEOM_AFFINE, (int)sizeof(double), a.g) * sizeof(double);
+  const size_t smem = tile_smem_elems(P, GEOM_AFFINE, (int)sizeof(double), a.g, MODE_OPERATOR) * sizeof(double);
   if (smem > smem_set) {
     const cudaError_t e = cudaFuncSetAttribute(tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -91,6 +91,10 @@ extern "C" int mfcg_apply_operator_static(const mfcg_mesh* mesh, int degree, con
   a.out0 = dst;
   a.geom = GEOM_AFFINE;
   a.prec = PREC_F64;
+  a.ncomp = 1;
+  a.op_kind = OP_LAPLACE;
+  a.comp_stride = a.g.n_dofs;
+  a.shell_comp_stride = a.g.n_tiles * a.g.face_stride;
   OperatorCoeffs c{};
   const double h[3] = {1.0 / N[0], 1.0 / N[1], 1.0 / N[2]};
   build_coeffs(degree, h, 0.0, MFCG_COEF_CONSTANT, c);

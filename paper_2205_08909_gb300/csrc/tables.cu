@@ -118,6 +118,7 @@ void build_coeffs(int p, const double h[3], double amplitude, int coef, Operator
     for (int d = 0; d < 3; ++d) c.mat[MAT_K0 + d][i] = scale[d] * K[i];
     c.mat[MAT_S][i] = S[i];
     c.mat[MAT_DC][i] = Dc[i];
+    c.mat[MAT_MV][i] = h[0] * h[1] * h[2] * M[i];
     c.T2[0][i] = S[i] * S[i];
     c.T2[1][i] = D[i] * S[i];
     c.T2[2][i] = D[i] * D[i];

@@ -228,69 +228,89 @@ struct ColorCells {
 // V: accumulated result on the same brick, S: per-cell scratch.
 // ------------------------------------------------------------------------------------
 
-// Affine box cells: the cell matrix of Eq. 5 is the Kronecker sum
-// K_x (x) M (x) M + M (x) K_y (x) M + M (x) M (x) K_z (K_d scaled by the cell
-// sizes), applied in seven 1D sweeps with shared intermediates.
-template <int PREC, int P>
-__device__ void cell_op_affine(const OperatorCoeffs& c, const typename Num<PREC>::T* U, typename Num<PREC>::T* V,
-                               typename Num<PREC>::T* S, int bx, int by, const ColorCells& cc) {
+// Cartesian tile, whole-brick form.  On a box of identical cells the sum over
+// the cells of the Kronecker sums K_x (x) M (x) M + M (x) K_y (x) M + M (x) M (x) K_z
+// is the Kronecker sum of the 1D matrices assembled along the lines of the node
+// brick.  Each sweep therefore runs along whole brick lines, one cell segment
+// of P+1 nodes after the other, and carries the partial result of the node
+// that a segment shares with the next one in registers: no per-cell scratch,
+// no colouring, three barriers per tile.  KIND 0 (first sweep):
+// A <- M A, B <- K A; KIND 1: A <- M A, B <- K A + M B; KIND 2: B <- K A + M B.
+// The mass operator M (x) M (x) M uses KIND 3: A <- Mk A and KIND 4: B <- Mk A.
+// In place is safe: a segment writes its first P nodes after reading them and
+// its last (shared) node only when the next segment has read it.
+//   nlines lines; line t starts at (t % n0) * s0 + (t / n0) * s1; st is the node
+//   stride along the line, ncl the number of cell segments.
+template <int PREC, int P, int KIND>
+__device__ __forceinline__ void brick_line_sweep(const OperatorCoeffs& c, typename Num<PREC>::T* A,
+                                                 typename Num<PREC>::T* B, int nlines, int n0, int s0, int s1,
+                                                 int st, int ncl, int matK) {
   using T = typename Num<PREC>::T;
-  constexpr int N1 = P + 1, N2 = N1 * N1, N3 = N2 * N1, CS = cell_stride(P, 2);
-  const int nc = cc.count();
-  // z direction: s1 = M u, s2 = K_z u
-  for (int t = threadIdx.x; t < nc * N2; t += kThreads) {
-    const int ci = t / N2, e = t - ci * N2, a = e % N1, b = e / N1;
-    const T* u0 = U + cc.org[ci] + a + bx * b;
-    T x[N1], y1[N1], y2[N1];
+  constexpr int N1 = P + 1;
+  for (int t = threadIdx.x; t < nlines; t += kThreads) {
+    const int i1 = t / n0, i0 = t - i1 * n0;
+    T* a0 = A + i0 * s0 + i1 * s1;
+    T* b0 = B + i0 * s0 + i1 * s1;
+    T ca = t_zero<PREC>(), cb = t_zero<PREC>();
+#pragma unroll 1
+    for (int seg = 0; seg < ncl; ++seg) {
+      T* a = a0 + st * P * seg;
+      T* b = b0 + st * P * seg;
+      T x[N1], z[N1], ya[N1], yb[N1];
 #pragma unroll
-    for (int s = 0; s < N1; ++s) x[s] = u0[s * bx * by];
-    mv<PREC, N1, false>(c, MAT_M, x, y1);
-    mv<PREC, N1, false>(c, MAT_K2, x, y2);
-    T* s1 = S + ci * CS;
-    T* s2 = s1 + N3;
+      for (int s = 0; s < N1; ++s) x[s] = a[s * st];
+      if constexpr (KIND == 0) {
+        mv<PREC, N1, false>(c, MAT_M, x, ya);
+        mv<PREC, N1, false>(c, matK, x, yb);
+      } else if constexpr (KIND == 3) {
+        mv<PREC, N1, false>(c, matK, x, ya);
+      } else if constexpr (KIND == 4) {
+        mv<PREC, N1, false>(c, matK, x, yb);
+      } else {
 #pragma unroll
-    for (int s = 0; s < N1; ++s) {
-      s1[cidx<N1>(a, b, s)] = y1[s];
-      s2[cidx<N1>(a, b, s)] = y2[s];
+        for (int s = 0; s < N1; ++s) z[s] = b[s * st];
+        if constexpr (KIND == 1) mv<PREC, N1, false>(c, MAT_M, x, ya);
+        mv2<PREC, N1>(c, matK, x, MAT_M, z, yb);
+      }
+      constexpr bool WA = KIND == 0 || KIND == 1 || KIND == 3;  // writes A
+      constexpr bool WB = KIND != 3;                             // writes B
+      if (seg > 0) {
+        if constexpr (WA) ya[0] = t_add<PREC>(ya[0], ca);
+        if constexpr (WB) yb[0] = t_add<PREC>(yb[0], cb);
+      }
+#pragma unroll
+      for (int s = 0; s < P; ++s) {
+        if constexpr (WA) a[s * st] = ya[s];
+        if constexpr (WB) b[s * st] = yb[s];
+      }
+      if constexpr (WA) ca = ya[P];
+      if constexpr (WB) cb = yb[P];
     }
+    if constexpr (KIND == 0 || KIND == 1 || KIND == 3) a0[st * P * ncl] = ca;
+    if constexpr (KIND != 3) b0[st * P * ncl] = cb;
   }
+}
+
+// The operator on a Cartesian tile: z, y and x sweeps along the brick lines;
+// U (p_k, Dirichlet-masked) is overwritten, the result is left in V.
+template <int PREC, int P>
+__device__ void brick_op_affine(const OperatorCoeffs& c, typename Num<PREC>::T* U, typename Num<PREC>::T* V, int bx,
+                                int by, int bz, int ncx, int ncy, int ncz, int op_kind) {
+  if (op_kind == OP_MASS) {
+    // h_x h_y h_z M (x) M (x) M
+    brick_line_sweep<PREC, P, 3>(c, U, V, bx * by, bx, 1, bx, bx * by, ncz, MAT_M);
+    __syncthreads();
+    brick_line_sweep<PREC, P, 3>(c, U, V, bx * bz, bx, 1, bx * by, bx, ncy, MAT_M);
+    __syncthreads();
+    brick_line_sweep<PREC, P, 4>(c, U, V, by * bz, by, bx, bx * by, 1, ncx, MAT_MV);
+    __syncthreads();
+    return;
+  }
+  brick_line_sweep<PREC, P, 0>(c, U, V, bx * by, bx, 1, bx, bx * by, ncz, MAT_K2);
   __syncthreads();
-  // y direction: s1 <- M s1, s2 <- K_y s1 + M s2
-  for (int t = threadIdx.x; t < nc * N2; t += kThreads) {
-    const int ci = t / N2, e = t - ci * N2, a = e % N1, cz = e / N1;
-    T* s1 = S + ci * CS;
-    T* s2 = s1 + N3;
-    T m[N1], k[N1], y1[N1], y2[N1];
-#pragma unroll
-    for (int s = 0; s < N1; ++s) {
-      m[s] = s1[cidx<N1>(a, s, cz)];
-      k[s] = s2[cidx<N1>(a, s, cz)];
-    }
-    mv<PREC, N1, false>(c, MAT_M, m, y1);
-    mv2<PREC, N1>(c, MAT_K1, m, MAT_M, k, y2);
-#pragma unroll
-    for (int s = 0; s < N1; ++s) {
-      s1[cidx<N1>(a, s, cz)] = y1[s];
-      s2[cidx<N1>(a, s, cz)] = y2[s];
-    }
-  }
+  brick_line_sweep<PREC, P, 1>(c, U, V, bx * bz, bx, 1, bx * by, bx, ncy, MAT_K1);
   __syncthreads();
-  // x direction: out = K_x s1 + M s2, added into V
-  for (int t = threadIdx.x; t < nc * N2; t += kThreads) {
-    const int ci = t / N2, e = t - ci * N2, b = e % N1, cz = e / N1;
-    const T* s1 = S + ci * CS;
-    const T* s2 = s1 + N3;
-    T m[N1], k[N1], y[N1];
-#pragma unroll
-    for (int s = 0; s < N1; ++s) {
-      m[s] = s1[cidx<N1>(s, b, cz)];
-      k[s] = s2[cidx<N1>(s, b, cz)];
-    }
-    mv2<PREC, N1>(c, MAT_K0, m, MAT_M, k, y);
-    T* v0 = V + cc.org[ci] + bx * (b + by * cz);
-#pragma unroll
-    for (int i = 0; i < N1; ++i) v0[i] = t_add<PREC>(v0[i], y[i]);
-  }
+  brick_line_sweep<PREC, P, 2>(c, U, V, by * bz, by, bx, bx * by, 1, ncx, MAT_K0);
   __syncthreads();
 }
 
@@ -302,7 +322,8 @@ __device__ void cell_op_affine(const OperatorCoeffs& c, const typename Num<PREC>
 // at S[ci*stride + cidx(a,b,c)]); gather_cell_results sums them into V.
 template <int PREC, int P, int GEOM>
 __device__ void cell_op_deformed(const OperatorCoeffs& c, const typename Num<PREC>::T* U, typename Num<PREC>::T* S,
-                                 int bx, int by, const ColorCells& cc, const typename Num<PREC>::T* __restrict__ geo) {
+                                 int bx, int by, const ColorCells& cc, const typename Num<PREC>::T* __restrict__ geo,
+                                 int op_kind) {
   using T = typename Num<PREC>::T;
   constexpr int N1 = P + 1, N2 = N1 * N1, N3 = N2 * N1;
   const int nc = cc.count();
@@ -316,6 +337,21 @@ __device__ void cell_op_deformed(const OperatorCoeffs& c, const typename Num<PRE
   sweep_inplace<PREC, P, false>(S, stride, nc, 0, c, MAT_S);
   sweep_inplace<PREC, P, false>(S, stride, nc, 1, c, MAT_S);
   sweep_inplace<PREC, P, false>(S, stride, nc, 2, c, MAT_S);
+  if constexpr (GEOM == GEOM_DEFORMED) {
+    if (op_kind == OP_MASS) {
+      // mass operator: values at the Gauss points times JxW a, transposed interpolation
+      for (int t = threadIdx.x; t < nc * N3; t += kThreads) {
+        const int ci = t / N3, q = t - ci * N3;
+        T* s = S + ci * stride;
+        s[q] = t_mul<PREC>(geo[(int64_t)cc.cell[ci] * 10 * N3 + 9 * N3 + q], s[q]);
+      }
+      __syncthreads();
+      sweep_inplace<PREC, P, true>(S, stride, nc, 0, c, MAT_S);
+      sweep_inplace<PREC, P, true>(S, stride, nc, 1, c, MAT_S);
+      sweep_inplace<PREC, P, true>(S, stride, nc, 2, c, MAT_S);
+      return;
+    }
+  }
   // reference gradients at the Gauss points (single pass over all three directions)
   for (int t = threadIdx.x; t < nc * N2 * 3; t += kThreads) {
     const int dir = t / (nc * N2);
@@ -411,9 +447,10 @@ __device__ void gather_cell_results(typename Num<PREC>::T* V, const typename Num
 
 // Right-hand side b_e = sum_q w_q det J_q f(x_q) phi(xhat_q): forcing at the
 // Gauss points, then three transposed interpolation sweeps (FP64).
-__device__ inline double manufactured_forcing(double x, double y, double z, int coef) {
+__device__ inline double manufactured_forcing(double x, double y, double z, int coef, int op_kind) {
   const double pi = 3.14159265358979323846;
   const double u = sin(pi * x) * sin(pi * y) * sin(pi * z);
+  if (op_kind == OP_MASS) return coef == MFCG_COEF_CONSTANT ? u : (1.0 + 0.5 * sin(pi * x)) * u;
   if (coef == MFCG_COEF_CONSTANT) return 3.0 * pi * pi * u;
   const double a = 1.0 + 0.5 * sin(pi * x);
   const double cx = cos(pi * x);
@@ -422,7 +459,7 @@ __device__ inline double manufactured_forcing(double x, double y, double z, int 
 
 template <int P>
 __device__ void cell_rhs(const OperatorCoeffs& c, double* V, double* S, int bx, int by, const ColorCells& cc,
-                         const TileGeom& g, int stride) {
+                         const TileGeom& g, int stride, int op_kind) {
   constexpr int N1 = P + 1, N2 = N1 * N1, N3 = N2 * N1;
   const int nc = cc.count();
   const double twopi = 6.28318530717958647692;
@@ -438,7 +475,7 @@ __device__ void cell_rhs(const OperatorCoeffs& c, double* V, double* S, int bx, 
     const double s = sx * sy * sz;
     const double dsum = twopi * (cos(twopi * X) * sy * sz + sx * cos(twopi * Y) * sz + sx * sy * cos(twopi * Z));
     const double detJ = c.h[0] * c.h[1] * c.h[2] * (1.0 + A * dsum);
-    const double f = manufactured_forcing(X + A * s, Y + A * s, Z + A * s, c.coef);
+    const double f = manufactured_forcing(X + A * s, Y + A * s, Z + A * s, c.coef, op_kind);
     S[ci * stride + q] = c.w[qa] * c.w[qb] * c.w[qc] * detJ * f;
   }
   __syncthreads();
@@ -459,7 +496,7 @@ __device__ void cell_rhs(const OperatorCoeffs& c, double* V, double* S, int bx, 
 // tables along each direction, i.e. three transposed sweeps.
 template <int P, int GEOM>
 __device__ void cell_diag(const OperatorCoeffs& c, double* V, double* S, int bx, int by, const ColorCells& cc,
-                          const double* __restrict__ geo, int stride) {
+                          const double* __restrict__ geo, int stride, int op_kind) {
   constexpr int N1 = P + 1, N2 = N1 * N1, N3 = N2 * N1;
   const int nc = cc.count();
   for (int t = threadIdx.x; t < nc * N3; t += kThreads) {
@@ -467,14 +504,23 @@ __device__ void cell_diag(const OperatorCoeffs& c, double* V, double* S, int bx,
     S[ci * stride + N3 + e] = 0.0;
   }
   const int combos[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
-  const int ncombo = GEOM == GEOM_AFFINE ? 3 : 6;
+  const bool mass = op_kind == OP_MASS;
+  const int ncombo = mass ? 1 : (GEOM == GEOM_AFFINE ? 3 : 6);
   for (int cb = 0; cb < ncombo; ++cb) {
     const int d0 = combos[cb][0], d1 = combos[cb][1];
     const double factor = d0 == d1 ? 1.0 : 2.0;
     for (int t = threadIdx.x; t < nc * N3; t += kThreads) {
       const int ci = t / N3, q = t - ci * N3;
       double C;
-      if (GEOM == GEOM_AFFINE) {
+      if (mass) {
+        // mass matrix: diag_e(i) = sum_q JxW_q a_q S(q,i)^2
+        if (GEOM == GEOM_AFFINE) {
+          const int qa = q % N1, qb = (q / N1) % N1, qc = q / N2;
+          C = c.w[qa] * c.w[qb] * c.w[qc] * c.h[0] * c.h[1] * c.h[2];
+        } else {
+          C = __ldg(geo + (int64_t)cc.cell[ci] * 10 * N3 + 9 * N3 + q);
+        }
+      } else if (GEOM == GEOM_AFFINE) {
         const int qa = q % N1, qb = (q / N1) % N1, qc = q / N2;
         C = c.w[qa] * c.w[qb] * c.w[qc] * c.h[0] * c.h[1] * c.h[2] / (c.h[d0] * c.h[d0]);
       } else if (GEOM == GEOM_TENSOR) {
@@ -492,7 +538,7 @@ __device__ void cell_diag(const OperatorCoeffs& c, double* V, double* S, int bx,
     __syncthreads();
 #pragma unroll 1
     for (int dim = 0; dim < 3; ++dim) {
-      const int nd = (dim == d0) + (dim == d1);
+      const int nd = mass ? 0 : (dim == d0) + (dim == d1);
       sweep_inplace_table_t<P>(S, stride, nc, dim, c.T2[nd]);
     }
     for (int t = threadIdx.x; t < nc * N3; t += kThreads) {
@@ -675,18 +721,18 @@ __device__ __forceinline__ int64_t brick_global_index(const TileGeom& g, int tx,
 }
 
 template <int P, int MODE, int GEOM, int PREC>
-__global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a, const OperatorCoeffs c) {
+__global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a_all, const OperatorCoeffs c) {
   using T = typename Num<PREC>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[8 * (kThreads / 32)];
   __shared__ int s_org[kMaxColorCells];
   __shared__ int s_cell[kMaxColorCells];
-  const TileGeom& g = a.g;
+  const TileGeom& g = a_all.g;
 
   T alpha_m = t_zero<PREC>(), beta_t = t_zero<PREC>(), xa = t_zero<PREC>(), xr = t_zero<PREC>();
   bool xupd = false;
   if constexpr (MODE == MODE_CG) {
-    const CGState* st = a.state;
+    const CGState* st = a_all.state;
     if (st->done) return;
     const int k = st->k;
     xupd = (k > 1) && (k & 1);
@@ -760,6 +806,46 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a, const 
     }
   };
 
+  // Deformed cells: start streaming the tile's stored geometry into L2 while
+  // phase 1 runs (every prefetched line lies inside the cell's block).
+  if constexpr (GEOM != GEOM_AFFINE && (MODE == MODE_CG || MODE == MODE_OPERATOR)) {
+    constexpr int N3 = (P + 1) * (P + 1) * (P + 1);
+    const int cell_bytes = geo_values(GEOM) * N3 * (int)sizeof(T);
+    const int lines = (cell_bytes + 127) / 128;
+    const int ncell = ncx * ncy * ncz;
+    const char* geo = static_cast<const char*>(a_all.geo);
+    for (int t = threadIdx.x; t < ncell * lines; t += kThreads) {
+      const int ci = t / lines, l = t - ci * lines;
+      const int cx = ci % ncx, cy = (ci / ncx) % ncy, cz = ci / (ncx * ncy);
+      const int64_t cell = (cx0 + cx) + (int64_t)g.N[0] * ((cy0 + cy) + (int64_t)g.N[1] * (cz0 + cz));
+      const size_t ptr = __cvta_generic_to_global(geo + cell * cell_bytes + (int64_t)l * 128);
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
+    }
+  }
+
+  // Vector-valued operator: the components one after another through phases
+  // 1-3, with the per-CTA sums accumulated over all of them; the geometry and
+  // the Jacobi diagonal are shared by the components.
+  DotAcc<PREC> sm[7];
+  const int ncomp = (MODE == MODE_CG || MODE == MODE_OPERATOR) ? a_all.ncomp : 1;
+  for (int comp = 0; comp < ncomp; ++comp) {
+  TileArgs a = a_all;
+  if (comp > 0) {
+    __syncthreads();  // the previous component is finished with U and V
+    const int64_t co = comp * a_all.comp_stride;
+    constexpr int64_t ve = MODE == MODE_CG ? (int64_t)sizeof(T) : (int64_t)sizeof(double);
+    auto shift = [&](const void* ptr, int64_t es) { return (const void*)(static_cast<const char*>(ptr) + co * es); };
+    a.in0 = shift(a_all.in0, ve);
+    a.out0 = const_cast<void*>(shift(a_all.out0, ve));
+    if constexpr (MODE == MODE_CG) {
+      a.in1 = shift(a_all.in1, ve);
+      a.in2 = shift(a_all.in2, ve);
+      a.out1 = const_cast<void*>(shift(a_all.out1, ve));
+      a.out2 = const_cast<void*>(shift(a_all.out2, ve));
+      a.x = const_cast<void*>(shift(a_all.x, ve));
+    }
+    a.shell = static_cast<char*>(a_all.shell) + comp * a_all.shell_comp_stride * (int64_t)sizeof(T);
+  }
   // ---------------- phase 1: pre ----------------
   // CG mode: the owned block is processed in 16-byte chunks of VN nodes (it is
   // contiguous and, when base and n_own are multiples of VN, aligned), two
@@ -767,6 +853,8 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a, const 
   // nodes take the scalar path with NB nodes per thread in flight.
   constexpr int NB = PREC == PREC_F32 ? 4 : 2;
   constexpr int VN = 16 / sizeof(T);
+  // the whole-brick affine operator overwrites V completely; the cell-wise ones accumulate into it
+  constexpr bool kZeroV = !(GEOM == GEOM_AFFINE && (MODE == MODE_CG || MODE == MODE_OPERATOR));
   const bool vec_ok = MODE == MODE_CG && (base % VN) == 0 && (n_own % VN) == 0;
   const int n_chunks = vec_ok ? n_own / VN : 0;
   const int scalar_begin = vec_ok ? n_own : 0;
@@ -809,7 +897,7 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a, const 
           const int sidx = li + bx * (lj + by * lk);
           const bool dir = bnd_tile && is_dirichlet(g, gi0 + li, gj0 + lj, gk0 + lk);
           U[sidx] = dir ? t_zero<PREC>() : pk[e];
-          V[sidx] = t_zero<PREC>();
+          if constexpr (kZeroV) V[sidx] = t_zero<PREC>();
         }
         st16(r_new + c * VN, rk);
         st16(p_new + c * VN, pk);
@@ -881,11 +969,14 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a, const 
     }
 #pragma unroll
     for (int b = 0; b < NB; ++b)
-      if (ok[b]) V[sidx[b]] = t_zero<PREC>();
+      if (kZeroV && ok[b]) V[sidx[b]] = t_zero<PREC>();
   }
 
   // ---------------- phase 2: cell integrals ----------------
-  if constexpr (GEOM != GEOM_AFFINE && (MODE == MODE_CG || MODE == MODE_OPERATOR)) {
+  if constexpr (GEOM == GEOM_AFFINE && (MODE == MODE_CG || MODE == MODE_OPERATOR)) {
+    __syncthreads();  // phase 1 finished with U
+    brick_op_affine<PREC, P>(c, U, V, bx, by, bz, ncx, ncy, ncz, a.op_kind);
+  } else if constexpr (GEOM != GEOM_AFFINE && (MODE == MODE_CG || MODE == MODE_OPERATOR)) {
     // deformed cells: batches of consecutive cells, all cells of a batch at
     // once with their results in the scratch, then a fixed-order node gather
     const int ncell = ncx * ncy * ncz;
@@ -903,7 +994,7 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a, const 
       }
       __syncthreads();
       const ColorCells cc{nb, s_org, s_cell};
-      cell_op_deformed<PREC, P, GEOM>(c, U, S, bx, by, cc, static_cast<const T*>(a.geo));
+      cell_op_deformed<PREC, P, GEOM>(c, U, S, bx, by, cc, static_cast<const T*>(a.geo), a.op_kind);
       gather_cell_results<PREC, P>(V, S, stride, c0, nb, ncx, ncy, bx, by, fbx, fby);
     }
     __syncthreads();
@@ -922,11 +1013,10 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a, const 
     __syncthreads();
     const ColorCells cc{nc, s_org, s_cell};
     if constexpr (MODE == MODE_RHS) {
-      cell_rhs<P>(c, V, S, bx, by, cc, g, cell_stride(P, GEOM == GEOM_AFFINE ? 2 : 4));
+      cell_rhs<P>(c, V, S, bx, by, cc, g, cell_stride(P, GEOM == GEOM_AFFINE ? 2 : 4), a.op_kind);
     } else if constexpr (MODE == MODE_DIAG) {
-      cell_diag<P, GEOM>(c, V, S, bx, by, cc, static_cast<const double*>(a.geo), cell_stride(P, GEOM == GEOM_AFFINE ? 2 : 4));
-    } else if constexpr (GEOM == GEOM_AFFINE) {
-      cell_op_affine<PREC, P>(c, U, V, S, bx, by, cc);
+      cell_diag<P, GEOM>(c, V, S, bx, by, cc, static_cast<const double*>(a.geo),
+                         cell_stride(P, GEOM == GEOM_AFFINE ? 2 : 4), a.op_kind);
     }
   }
 
@@ -936,7 +1026,6 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a, const 
   // shell; the other owned nodes are final.  In the chunked path the value
   // stored for a shared owned node is a placeholder that the tail kernel
   // overwrites with the complete sum.
-  DotAcc<PREC> sm[7];
   T* shell = static_cast<T*>(a.shell);
   if constexpr (MODE == MODE_CG) {
     const T* r_k = static_cast<const T*>(a.out0) + base;
@@ -976,7 +1065,8 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a, const 
             shell[tile * g.face_stride + shell_slot(g, li, lj, lk, bx, by, bz)] = vs;
             vv[e] = vs;
           } else {
-            const T pk = dir ? p4[h][e] : U[sidx];
+            // p_k as stored in phase 1 (the U brick may have been overwritten by the operator)
+            const T pk = p4[h][e];
             vv[e] = dir ? pk : vs;
             post_sums<PREC>(sm, r4[h][e], pk, vv[e], d4[h][e]);
           }
@@ -1024,7 +1114,7 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a, const 
 #pragma unroll
       for (int b = 0; b < NB; ++b) {
         if (!fin[b]) continue;
-        const T pk = dir[b] ? pd[b] : U[sidx[b]];
+        const T pk = pd[b];
         const T v = dir[b] ? pk : V[sidx[b]];
         static_cast<T*>(a.out1)[gi[b]] = v;
         post_sums<PREC>(sm, rk[b], pk, v, dv[b]);
@@ -1043,7 +1133,9 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a, const 
       }
     }
   }
-  if constexpr (MODE == MODE_CG) store_cta_sums<PREC>(sm, red, a.partial, tile);
+  }  // components
+
+  if constexpr (MODE == MODE_CG) store_cta_sums<PREC>(sm, red, a_all.partial, tile);
 }
 
 // ------------------------------------------------------------------------------------
@@ -1095,7 +1187,20 @@ __global__ void __launch_bounds__(kThreads) tail_kernel(const TileArgs a) {
   const TileGeom& g = a.g;
   if (MODE == MODE_CG && a.state->done) return;
   DotAcc<PREC> sm[7];
-  const T* shell = static_cast<const T*>(a.shell);
+  for (int comp = 0; comp < a.ncomp; ++comp) {
+  const int64_t co = comp * a.comp_stride;
+  const T* shell = static_cast<const T*>(a.shell) + comp * a.shell_comp_stride;
+  const T* r_k = nullptr;
+  const T* p_k = nullptr;
+  T* v_k = nullptr;
+  double* dst = nullptr;
+  if constexpr (MODE == MODE_CG) {
+    r_k = static_cast<const T*>(a.out0) + co;
+    p_k = static_cast<const T*>(a.out2) + co;
+    v_k = static_cast<T*>(a.out1) + co;
+  } else {
+    dst = static_cast<double*>(a.out0) + co;
+  }
   for (int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x; t < a.tail_nodes; t += (int64_t)gridDim.x * kThreads) {
     int i, j, k;
     decode_tail_node(g, a.fam, a.tdiv, t, i, j, k);
@@ -1114,13 +1219,14 @@ __global__ void __launch_bounds__(kThreads) tail_kernel(const TileArgs a) {
         }
     const int64_t gi = node_index(g, i, j, k);
     if constexpr (MODE == MODE_CG) {
-      const T rk = static_cast<const T*>(a.out0)[gi], pk = static_cast<const T*>(a.out2)[gi];
-      static_cast<T*>(a.out1)[gi] = v;
+      const T rk = r_k[gi], pk = p_k[gi];
+      v_k[gi] = v;
       post_sums<PREC>(sm, rk, pk, v, static_cast<const T*>(a.diag_inv)[gi]);
     } else {
-      static_cast<double*>(a.out0)[gi] = t_to_double<PREC>(v);
+      dst[gi] = t_to_double<PREC>(v);
     }
   }
+  }  // components
   if constexpr (MODE == MODE_CG) {
     store_cta_sums<PREC>(sm, red, a.partial, a.g.n_tiles + blockIdx.x);
     if (threadIdx.x == 0) {
@@ -1144,12 +1250,22 @@ __global__ void __launch_bounds__(kThreads) tail_kernel(const TileArgs a) {
 // ------------------------------------------------------------------------------------
 // launch helpers
 // ------------------------------------------------------------------------------------
-// elements of dynamic shared memory: node bricks U and V, and the cell scratch
-// (one colour of cells, or one batch of deformed cells)
-inline size_t tile_smem_elems(int P, int geom, int elem_bytes, const TileGeom& g) {
+// elements of dynamic shared memory for a mode (-1: the largest over the
+// modes): node bricks U and V, and the cell scratch -- none for the
+// whole-brick affine operator, one colour of cells for the set-up passes, one
+// batch of cells for the deformed operator
+inline size_t tile_smem_elems(int P, int geom, int elem_bytes, const TileGeom& g, int mode = -1) {
   const size_t Bmax = (size_t)(P * g.T[0] + 1) * (P * g.T[1] + 1) * (P * g.T[2] + 1);
-  size_t cells = (size_t)((g.T[0] + 1) / 2) * ((g.T[1] + 1) / 2) * ((g.T[2] + 1) / 2);
-  if (geom != GEOM_AFFINE) cells = std::max(cells, (size_t)deformed_batch_cells(P, elem_bytes, g));
+  const size_t colour = (size_t)((g.T[0] + 1) / 2) * ((g.T[1] + 1) / 2) * ((g.T[2] + 1) / 2);
+  const bool iter = mode == MODE_CG || mode == MODE_OPERATOR;
+  const bool setup = mode == MODE_RHS || mode == MODE_DIAG;
+  size_t cells;
+  if (geom == GEOM_AFFINE) {
+    cells = iter ? 0 : colour;
+  } else {
+    const size_t batch = (size_t)deformed_batch_cells(P, elem_bytes, g);
+    cells = iter ? batch : (setup ? colour : std::max(colour, batch));
+  }
   return 2 * Bmax + cells * (size_t)cell_stride(P, geom == GEOM_AFFINE ? 2 : 4);
 }
 
@@ -1188,6 +1304,12 @@ cudaError_t prepare_tile_p(int geom, int prec, size_t smem) {
     if (!fn) continue;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    // FP32 kernels fit three CTAs per SM by registers: give them the shared memory for it
+    if (prec == PREC_F32) {
+      e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               (int)cudaSharedmemCarveoutMaxShared);
+      if (e != cudaSuccess) return e;
+    }
   }
   return cudaSuccess;
 }
@@ -1196,7 +1318,7 @@ template <int P>
 cudaError_t launch_tile_p(int mode, const TileArgs& a, const OperatorCoeffs& c, cudaStream_t s) {
   TileFn<P> fn = tile_fn<P>(mode, a.geom, a.prec);
   if (!fn) return cudaErrorInvalidValue;
-  const size_t smem = tile_smem_elems(P, a.geom, prec_bytes(a.prec), a.g) * prec_bytes(a.prec);
+  const size_t smem = tile_smem_elems(P, a.geom, prec_bytes(a.prec), a.g, mode) * prec_bytes(a.prec);
   fn<<<(unsigned)a.g.n_tiles, kThreads, smem, s>>>(a, c);
   return cudaGetLastError();
 }

@@ -61,3 +61,29 @@ def boundary_zeroed(v: np.ndarray, nodes_per_dim) -> np.ndarray:
     out[:, 0], out[:, -1] = 0.0, 0.0
     out[:, :, 0], out[:, :, -1] = 0.0, 0.0
     return out.reshape(-1)
+
+
+def batch_problems(count: int = 64, seed: int = SEED_VECTORS, max_cells: int = 32) -> list[dict]:
+    """Independent problems of a batch: degree ~ U{2..8}, cells per direction
+    ~ U{4..max_cells} (cubes), deformation amplitude ~ U[0, 0.08] with the
+    coefficient a = 1 + 0.5 sin(pi x) on deformed meshes."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for _ in range(count):
+        p = int(rng.integers(2, 9))
+        n = int(rng.integers(4, max_cells + 1))
+        a = float(rng.uniform(0.0, 0.08))
+        out.append({"degree": p, "cells": (n, n, n), "amplitude": a, "coefficient": "sin_x",
+                    "geometry": "deformed_tensor"})
+    return out
+
+
+def batch_rhs(problems: list[dict], seed: int = SEED_RHS_BLOCK) -> list[np.ndarray]:
+    """Standard-normal right-hand sides of the batch problems (lexicographic
+    node order), zero on the Dirichlet nodes."""
+    out = []
+    for i, sp in enumerate(problems):
+        dims = tuple(sp["degree"] * c + 1 for c in sp["cells"])
+        v = random_vector(dims[0] * dims[1] * dims[2], seed, i)
+        out.append(boundary_zeroed(v, dims))
+    return out
