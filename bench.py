@@ -78,19 +78,70 @@ def geometry_values(geometry: str) -> int:
     return {"affine": 0, "deformed": 10, "deformed_tensor": 6}[geometry]
 
 
-def algorithmic_flops_per_iteration(degree: int, n_cells: int, n_dofs: int, geometry: str = "affine") -> float:
-    """FP64 flops of one fused iteration.  Affine cells: seven 1D sweeps of
-    (p+1)^4 FMAs per cell (Kronecker form); deformed cells: twelve sweeps
-    (interpolation, collocation derivative and their transposes) plus the
-    per-point metric (42 flops from J^{-1} and JxW a, 18 from the final
-    tensor).  Plus the vector work per unknown (r, z, p updates 5, x update 5
-    every other iteration, seven sums with M^-1 r and M^-1 v 16)."""
+DEFAULT_TILE = {"affine": [0, 16, 8, 5, 4, 3, 3, 2, 2], "deformed": [0, 8, 4, 4, 3, 2, 2, 2, 2]}
+
+
+def brick_segments(degree: int, cells, tile=None) -> tuple[int, int, int]:
+    """Cell segments that the whole-brick sweeps of a Cartesian operator pass
+    process per launch, summed over the tiles (z, y and x sweeps): a sweep
+    along direction d runs over every brick line across d, one segment per cell
+    along d.  Neighbouring cells share their face lines, so a cell costs about
+    p^2 segments per sweep instead of the (p+1)^2 pencils of a cell-wise sweep."""
+    T = tile or (DEFAULT_TILE["affine"][degree],) * 3
+    seg = [0, 0, 0]
+    # tile extents along each direction: full tiles of T cells and a ragged last one
+    ext = []
+    for d in range(3):
+        n, t = cells[d], T[d]
+        sizes = [t] * (n // t) + ([n % t] if n % t else [])
+        ext.append(sizes)
+    for nz in ext[2]:
+        for ny in ext[1]:
+            for nx in ext[0]:
+                bx, by, bz = degree * nx + 1, degree * ny + 1, degree * nz + 1
+                seg[2] += bx * by * nz
+                seg[1] += bx * bz * ny
+                seg[0] += by * bz * nx
+    return seg[2], seg[1], seg[0]
+
+
+def eo_segment_costs(n1: int, unit: str) -> tuple[float, float, float]:
+    """Operations of one cell segment of the z (M and K_z from x), y (M x;
+    K_y x + M z) and x (K_x x + M z) sweeps in even-odd form, with the carry of
+    the shared node.  unit "flop": FP64 flops (FMA = 2).  unit "dd": FP32-pipe
+    operations of the double-float arithmetic (pair addition 11, a K-term sum
+    12 K - 5: first product 4, each further product 12, normalisation 3)."""
+    h, ne = n1 // 2, n1 - n1 // 2
+    if unit == "flop":
+        add, dot = 1.0, (lambda k: 2.0 * k)
+    else:
+        add, dot = 11.0, (lambda k: 12.0 * k - 5.0)
+    one = h * (dot(ne) + dot(h) + 2 * add) + (dot(ne) if ne > h else 0)          # A x
+    two = h * (dot(2 * ne) + dot(2 * h) + 2 * add) + (dot(2 * ne) if ne > h else 0)  # A x + B z
+    form1, form2 = 2 * h * add, 4 * h * add
+    z = form1 + 2 * one + 2 * add
+    y = form2 + one + two + 2 * add
+    x = form2 + two + add
+    return z, y, x
+
+
+def algorithmic_flops_per_iteration(degree: int, n_cells: int, n_dofs: int, geometry: str = "affine",
+                                    cells=None, tile=None) -> float:
+    """FP64 flops of one fused iteration.  Affine cells: the whole-brick
+    sweeps in even-odd form over the segments of brick_segments; deformed
+    cells: twelve cell-wise sweeps of (p+1)^4 FMAs (interpolation,
+    collocation derivative and their transposes) plus the per-point metric (42
+    flops from J^{-1} and JxW a, 18 from the final tensor).  Plus the vector
+    work per unknown (r, z, p updates 5, x update 5 every other iteration,
+    seven sums with M^-1 r and M^-1 v 16)."""
     n1 = degree + 1
     if geometry == "affine":
-        per_cell = 2.0 * 7 * n1 ** 4
+        sz, sy, sx = brick_segments(degree, cells, tile)
+        cz, cy, cx = eo_segment_costs(n1, "flop")
+        op = sz * cz + sy * cy + sx * cx
     else:
-        per_cell = 2.0 * 12 * n1 ** 4 + (42 if geometry == "deformed" else 18) * n1 ** 3
-    return per_cell * n_cells + 23.5 * n_dofs
+        op = (2.0 * 12 * n1 ** 4 + (42 if geometry == "deformed" else 18) * n1 ** 3) * n_cells
+    return op + 23.5 * n_dofs
 
 
 ALGORITHMIC_BYTES_PER_DOF = 64.0  # r, p, v read+write, D^-1 read, x read+write every other iteration
@@ -236,30 +287,33 @@ def run_reference(args, world, rank):
     }
 
 
-def dd_ops_per_dof(degree: int, n_cells: int, n_dofs: int, geometry: str = "affine") -> float:
+def dd_ops_per_dof(degree: int, n_cells: int, n_dofs: int, geometry: str = "affine", cells=None,
+                   tile=None) -> float:
     """FP32-pipe operations of one fused double-float iteration per unknown,
     counted from the error-free transformations: a product accumulated into a
     (s, t) pair costs 12 (TwoProduct 2, cross terms 2, TwoSum 6, error sum 2),
     the first product of a sum 4, a normalisation 3, a pair addition 11, a pair
-    product 7.  Affine operator: per cell and pencil the z sweep (M, K_z), the
-    y sweep (M; K_y + M) and the x sweep (K_x + M, added into the node brick).
-    Deformed operator: twelve single-matrix sweeps, two accumulating
+    product 7.  Affine operator: the whole-brick sweeps in even-odd form
+    (eo_segment_costs) over the segments of brick_segments.  Deformed
+    operator: twelve single-matrix cell-wise sweeps, two accumulating
     transposed-derivative sweeps, the metric (3 three-term sums from the final
-    tensor; 6 sums and 3 pair products from J^{-1} and JxW a) and the
-    node gather (one pair addition per cell node)."""
+    tensor; 6 sums and 3 pair products from J^{-1} and JxW a) and the node
+    gather (one pair addition per cell node)."""
     n1 = degree + 1
     mv = n1 * (4 + 12 * (n1 - 1) + 3)
-    mv2 = n1 * (4 + 12 * (2 * n1 - 1) + 3)
     dot3 = 4 + 12 * 2 + 3
     if geometry == "affine":
-        per_cell = n1 * n1 * (2 * mv + (mv + mv2) + (mv2 + 11 * n1))
+        sz, sy, sx = brick_segments(degree, cells, tile)
+        cz, cy, cx = eo_segment_costs(n1, "dd")
+        op = (sz * cz + sy * cy + sx * cx) / n_dofs
     else:
         metric = 3 * dot3 if geometry == "deformed_tensor" else 6 * dot3 + 3 * 7
         per_cell = 12 * n1 * n1 * mv + 2 * 11 * n1 ** 3 + metric * n1 ** 3 + 11 * n1 ** 3
+        op = per_cell * n_cells / n_dofs
     pre = 34.0 * 1.2                                  # r and p updates on the tile brick (~1.2x the owned nodes)
     x_update = 48.0 / 2                               # every other iteration
     post = 2 * 7 + 7 * 12                             # M^-1 r, M^-1 v and seven accumulations
-    return per_cell * n_cells / n_dofs + pre + x_update + post
+    return op + pre + x_update + post
 
 
 def fp32_pipe_peak_tops() -> float:
@@ -377,13 +431,13 @@ def run_ours(args, world, rank, local):
     hbm_gbs = bytes_per_dof * w.n_dofs / (kernel_ms / 1e3) / 1e9
     traffic = stored_traffic(w.name, main_prec)
     if main_prec == "fp64":
-        flops = algorithmic_flops_per_iteration(w.degree, n_cells, w.n_dofs, geometry)
+        flops = algorithmic_flops_per_iteration(w.degree, n_cells, w.n_dofs, geometry, w.cells, tile)
         achieved = flops / (kernel_ms / 1e3) / 1e12
         roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
                     "peak_kind": "nominal FP64 (recipe table)", "algorithmic_flops_per_launch": flops}
     elif main_prec == "double_float":
-        ops = dd_ops_per_dof(w.degree, n_cells, w.n_dofs, geometry) * w.n_dofs
+        ops = dd_ops_per_dof(w.degree, n_cells, w.n_dofs, geometry, w.cells, tile) * w.n_dofs
         achieved = ops / (kernel_ms / 1e3) / 1e12
         peak = fp32_pipe_peak_tops()
         roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 2),

@@ -114,7 +114,7 @@ typedef struct mfcg_options {
   int32_t precision;        /* mfcg_precision                                                       */
   int32_t preconditioner;   /* mfcg_preconditioner                                                  */
   double inner_rtol;        /* MFCG_PREC_FP32_INNER: residual reduction of each inner solve (0 = 1e-3) */
-  int32_t components;       /* 0 or 1: scalar Laplacian; 2 or 3: vector-valued Laplacian (the BP4 form
+  int32_t components;       /* 0 or 1: scalar operator; 3: vector-valued operator (the BP2/BP4 form
                                of Sec. 2): every component is the scalar operator, one CG runs on the
                                coupled system, the Jacobi diagonal and the geometry are shared by the
                                components.  Vectors hold the components one after another (each in

@@ -46,8 +46,8 @@ def _eig_1d(p: int, n_cells: int):
 def solve(prob: fem.Problem, b: np.ndarray) -> np.ndarray:
     """x = A^{-1} b for the Cartesian Dirichlet problem (identity boundary
     rows: x_i = b_i there)."""
-    if not fem.cartesian_cells_identical(prob):
-        raise ValueError("fast diagonalisation needs a Cartesian mesh with a = 1")
+    if not fem.cartesian_cells_identical(prob) or prob.op != fem.OP_LAPLACE:
+        raise ValueError("fast diagonalisation needs the Laplacian on a Cartesian mesh with a = 1")
     nx, ny, nz = prob.nodes_per_dim
     B = b.reshape(nz, ny, nx)
     x = b.copy().reshape(nz, ny, nx)
@@ -79,8 +79,8 @@ def apply(prob: fem.Problem, u: np.ndarray) -> np.ndarray:
     A = K_z (x) M_y (x) M_x + M_z (x) K_y (x) M_x + M_z (x) M_y (x) K_x on the
     interior nodes (boundary columns zero), identity rows on the boundary.
     Cost O(n p) with sparse 1D factors, usable at any mesh size."""
-    if not fem.cartesian_cells_identical(prob):
-        raise ValueError("the Kronecker form needs a Cartesian mesh with a = 1")
+    if not fem.cartesian_cells_identical(prob) or prob.op != fem.OP_LAPLACE:
+        raise ValueError("the Kronecker form needs the Laplacian on a Cartesian mesh with a = 1")
     nx, ny, nz = prob.nodes_per_dim
     Kx, Mx = _sparse_1d(prob.p, prob.cells[0])
     Ky, My = _sparse_1d(prob.p, prob.cells[1])

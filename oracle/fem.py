@@ -106,19 +106,23 @@ def element_matrices_1d(p: int) -> tuple[np.ndarray, np.ndarray]:
 COEF_CONSTANT = 0  # a(x) = 1
 COEF_SIN_X = 1     # a(x) = 1 + 0.5 sin(pi x)
 
+OP_LAPLACE = 0     # (a grad phi_i, grad phi_j): Eq. 5
+OP_MASS = 1        # (a phi_i, phi_j): the mass operator of the bake-off family
+
 
 @dataclasses.dataclass(frozen=True)
 class Problem:
-    """A Q_p Poisson problem on the unit cube.
+    """A Q_p Poisson (or mass) problem on the unit cube.
 
     cells = (N_x, N_y, N_z); ``amplitude`` A deforms the mesh by
     x -> X + A sin(2 pi X) sin(2 pi Y) sin(2 pi Z) on each component (A = 0 is
-    the Cartesian mesh); ``coef`` selects a(x)."""
+    the Cartesian mesh); ``coef`` selects a(x); ``op`` the operator."""
 
     p: int
     cells: tuple[int, int, int]
     amplitude: float = 0.0
     coef: int = COEF_CONSTANT
+    op: int = OP_LAPLACE
 
     @property
     def nodes_per_dim(self) -> tuple[int, int, int]:
@@ -210,8 +214,11 @@ def manufactured_solution(x: np.ndarray) -> np.ndarray:
 
 
 def manufactured_forcing(prob: Problem, x: np.ndarray) -> np.ndarray:
-    """f = -div(a grad u*) for u* = sin(pi x) sin(pi y) sin(pi z)."""
+    """f = -div(a grad u*) for u* = sin(pi x) sin(pi y) sin(pi z); for the
+    mass operator f = a u*."""
     u = manufactured_solution(x)
+    if prob.op == OP_MASS:
+        return coefficient(prob, x) * u
     if prob.coef == COEF_CONSTANT:
         return 3.0 * math.pi ** 2 * u
     a = coefficient(prob, x)
@@ -243,16 +250,21 @@ def reference_tables(p: int, n_q1d: int | None = None):
 def element_matrices(prob: Problem, cell_ids: np.ndarray | None = None, chunk: int = 256) -> np.ndarray:
     """A_e for the requested cells with full (p+1)^3 Gauss quadrature (Eq. 5):
     A_e = sum_q w_q det J_q a(x_q) (G_q J_q^{-1}) (G_q J_q^{-1})^T where row i of
-    G_q is the reference gradient of phi_i at point q."""
+    G_q is the reference gradient of phi_i at point q.  Mass operator:
+    A_e = sum_q w_q det J_q a(x_q) phi(q) phi(q)^T."""
     if cell_ids is None:
         cell_ids = np.arange(prob.n_cells)
     cell_ids = np.asarray(cell_ids)
-    _, G = reference_tables(prob.p)
+    phi, G = reference_tables(prob.p)
     nloc = G.shape[1]
     out = np.empty((len(cell_ids), nloc, nloc))
     for s in range(0, len(cell_ids), chunk):
         ids = cell_ids[s:s + chunk]
         x, J, detJ, w = quadrature_geometry(prob, ids)
+        if prob.op == OP_MASS:
+            c = w[None, :] * detJ * coefficient(prob, x)          # [e, q]
+            out[s:s + chunk] = np.einsum("eq,qi,qj->eij", c, phi, phi)
+            continue
         Jinv = np.linalg.inv(J)
         c = w[None, :] * detJ * coefficient(prob, x)              # [e, q]
         Gp = np.einsum("qid,eqdk->eiqk", G, Jinv)                # physical gradients

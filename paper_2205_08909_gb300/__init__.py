@@ -41,7 +41,7 @@ class Problem:
     preconditioner: "jacobi" or "none" (Algorithm 4);
     precision: "fp64", "double_float" (FP32 pairs, ~48 bits) or "fp32_inner"
     (FP64 defect correction around an FP32 fused CG, inner_rtol per cycle);
-    components: 1 (scalar) or 2..3 (vector-valued operator, components stored
+    components: 1 (scalar) or 3 (vector-valued operator, components stored
     one after another; fused mode); operator: "laplace" (BP3/BP4) or "mass"
     (BP1/BP2; affine or geometry="deformed").
     Vectors are float64 CUDA tensors in the library's tile-blocked order.

@@ -859,7 +859,7 @@ int mfcg_setup(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, con
   if (o.precision < MFCG_PREC_FP64 || o.precision > MFCG_PREC_FP32_INNER) return MFCG_INVALID_ARG;
   if (o.precision == MFCG_PREC_FP32_INNER && o.mode != MFCG_MODE_FUSED) return MFCG_INVALID_ARG;
   if (!(o.inner_rtol >= 0.0 && o.inner_rtol < 1.0)) return MFCG_INVALID_ARG;
-  if (o.components < 0 || o.components > 3 || (o.components > 1 && o.mode != MFCG_MODE_FUSED))
+  if ((o.components != 0 && o.components != 1 && o.components != 3) || (o.components > 1 && o.mode != MFCG_MODE_FUSED))
     return MFCG_INVALID_ARG;
   if (o.operator_kind != MFCG_OP_LAPLACE && o.operator_kind != MFCG_OP_MASS) return MFCG_INVALID_ARG;
   if (o.operator_kind == MFCG_OP_MASS && geom->kind == MFCG_GEOM_DEFORMED_TENSOR) return MFCG_INVALID_ARG;

@@ -282,6 +282,14 @@ struct OperatorCoeffs {
   // the same matrices as float pairs (hi + lo) for the double-float and FP32 paths
   float fh[NMAT][kMat];
   float fl[NMAT][kMat];
+  // even-odd form of the centrosymmetric matrices (A[n-1-i][n-1-j] = A[i][j]):
+  // with e_j = x_j + x_{n-1-j}, o_j = x_j - x_{n-1-j} (j < h = n/2) and
+  // e_h = x_h for odd n, the halves ye = E e (ceil(n/2) rows, row-major,
+  // stride ceil(n/2)) and yo = O o (h rows, stride h, stored after E) give
+  // y_i = ye_i + yo_i and y_{n-1-i} = ye_i - yo_i (i < h), y_h = ye_h
+  double eo[NMAT][kMat];
+  float eoh[NMAT][kMat];
+  float eol[NMAT][kMat];
   double w[kMaxDegree + 1];  // Gauss weights on [0,1]
   double g[kMaxDegree + 1];  // Gauss points on [0,1]
   double h[3];               // cell sizes

@@ -43,7 +43,7 @@ int default_affine_tile(int p) {
 
 template <int P>
 cudaError_t launch_static_operator(const TileArgs& a, const OperatorCoeffs& c, cudaStream_t s, size_t& smem_set) {
-  auto tile = tile_kernel<P, MODE_OPERATOR, GEOM_AFFINE, PREC_F64>;
+  auto tile = tile_kernel<P, MODE_OPERATOR, GEOM_AFFINE, PREC_F64, 1>;
   const size_t smem = tile_smem_elems(P, GEOM_AFFINE, (int)sizeof(double), a.g, MODE_OPERATOR) * sizeof(double);
   if (smem > smem_set) {
     const cudaError_t e = cudaFuncSetAttribute(tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -130,6 +130,29 @@ void build_coeffs(int p, const double h[3], double amplitude, int coef, Operator
       c.fh[m][i] = hi;
       c.fl[m][i] = (float)(c.mat[m][i] - (double)hi);
     }
+  // even-odd halves (used for the centrosymmetric mass and stiffness matrices)
+  const int hh = n1 / 2, ne = n1 - hh;
+  for (int m = 0; m < NMAT; ++m) {
+    const double* A = c.mat[m];
+    double* E = c.eo[m];
+    double* O = c.eo[m] + ne * ne;
+    for (int i = 0; i < ne; ++i)
+      for (int j = 0; j < ne; ++j) {
+        double v;
+        if (j < hh)
+          v = i < hh ? 0.5 * (A[i * n1 + j] + A[i * n1 + (n1 - 1 - j)]) : A[i * n1 + j];
+        else
+          v = A[i * n1 + j];  // middle column (odd n)
+        E[i * ne + j] = v;
+      }
+    for (int i = 0; i < hh; ++i)
+      for (int j = 0; j < hh; ++j) O[i * hh + j] = 0.5 * (A[i * n1 + j] - A[i * n1 + (n1 - 1 - j)]);
+    for (int i = 0; i < ne * ne + hh * hh; ++i) {
+      const float hi = (float)c.eo[m][i];
+      c.eoh[m][i] = hi;
+      c.eol[m][i] = (float)(c.eo[m][i] - (double)hi);
+    }
+  }
   for (int q = 0; q < n1; ++q) {
     c.w[q] = w[q];
     c.g[q] = g[q];

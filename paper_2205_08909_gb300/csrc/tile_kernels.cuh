@@ -122,6 +122,89 @@ __device__ __forceinline__ void mv2(const OperatorCoeffs& c, int ma, const typen
   }
 }
 
+// ------------------------------------------------------------------------------------
+// Even-odd form of the centrosymmetric 1D matrices (M, K_d, the volume-scaled
+// M): y = A x from the halves E (ceil(n/2)^2) and O (floor(n/2)^2) of the
+// coefficient block, about half the multiply-adds of the plain product.
+// ------------------------------------------------------------------------------------
+// sum_j E_m[off + j] va_j (+ sum_j E_mb[offb + j] vb_j when TWO)
+template <int PREC, int K, bool TWO>
+__device__ __forceinline__ typename Num<PREC>::T eo_dot(const OperatorCoeffs& c, int ma, int offa,
+                                                        const typename Num<PREC>::T (&va)[K], int mb, int offb,
+                                                        const typename Num<PREC>::T (&vb)[K]) {
+  if constexpr (PREC == PREC_DD) {
+    dd_acc a;
+    acc_set(a, dd{c.eoh[ma][offa], c.eol[ma][offa]}, va[0]);
+#pragma unroll
+    for (int j = 1; j < K; ++j) acc_madd(a, dd{c.eoh[ma][offa + j], c.eol[ma][offa + j]}, va[j]);
+    if constexpr (TWO) {
+#pragma unroll
+      for (int j = 0; j < K; ++j) acc_madd(a, dd{c.eoh[mb][offb + j], c.eol[mb][offb + j]}, vb[j]);
+    }
+    return acc_get(a);
+  } else if constexpr (PREC == PREC_F64) {
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < K; ++j) s = fma(c.eo[ma][offa + j], va[j], s);
+    if constexpr (TWO) {
+#pragma unroll
+      for (int j = 0; j < K; ++j) s = fma(c.eo[mb][offb + j], vb[j], s);
+    }
+    return s;
+  } else {
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < K; ++j) s = fmaf(c.eoh[ma][offa + j], va[j], s);
+    if constexpr (TWO) {
+#pragma unroll
+      for (int j = 0; j < K; ++j) s = fmaf(c.eoh[mb][offb + j], vb[j], s);
+    }
+    return s;
+  }
+}
+
+// ya = A_m1 x (WA) and yb = A_m2 x (+ A_m3 z when HZ) (WB), all in even-odd form
+template <int PREC, int N1, bool WA, bool WB, bool HZ>
+__device__ __forceinline__ void eo_apply(const OperatorCoeffs& c, int m1, int m2, int m3,
+                                         const typename Num<PREC>::T (&x)[N1], const typename Num<PREC>::T (&z)[N1],
+                                         typename Num<PREC>::T (&ya)[N1], typename Num<PREC>::T (&yb)[N1]) {
+  using T = typename Num<PREC>::T;
+  constexpr int H = N1 / 2, NE = N1 - H;
+  T ex[NE], ox[H], ez[NE], oz[H];
+#pragma unroll
+  for (int j = 0; j < H; ++j) {
+    ex[j] = t_add<PREC>(x[j], x[N1 - 1 - j]);
+    ox[j] = t_sub<PREC>(x[j], x[N1 - 1 - j]);
+    if constexpr (HZ) {
+      ez[j] = t_add<PREC>(z[j], z[N1 - 1 - j]);
+      oz[j] = t_sub<PREC>(z[j], z[N1 - 1 - j]);
+    }
+  }
+  if constexpr (NE > H) {
+    ex[H] = x[H];
+    if constexpr (HZ) ez[H] = z[H];
+  }
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    if constexpr (WA) {
+      const T ye = eo_dot<PREC, NE, false>(c, m1, i * NE, ex, m1, 0, ex);
+      const T yo = eo_dot<PREC, H, false>(c, m1, NE * NE + i * H, ox, m1, 0, ox);
+      ya[i] = t_add<PREC>(ye, yo);
+      ya[N1 - 1 - i] = t_sub<PREC>(ye, yo);
+    }
+    if constexpr (WB) {
+      const T ye = eo_dot<PREC, NE, HZ>(c, m2, i * NE, ex, m3, i * NE, ez);
+      const T yo = eo_dot<PREC, H, HZ>(c, m2, NE * NE + i * H, ox, m3, NE * NE + i * H, oz);
+      yb[i] = t_add<PREC>(ye, yo);
+      yb[N1 - 1 - i] = t_sub<PREC>(ye, yo);
+    }
+  }
+  if constexpr (NE > H) {
+    if constexpr (WA) ya[H] = eo_dot<PREC, NE, false>(c, m1, H * NE, ex, m1, 0, ex);
+    if constexpr (WB) yb[H] = eo_dot<PREC, NE, HZ>(c, m2, H * NE, ex, m3, H * NE, ez);
+  }
+}
+
 // a0 b0 + a1 b1 + a2 b2
 template <int PREC>
 __device__ __forceinline__ typename Num<PREC>::T dot3(typename Num<PREC>::T a0, typename Num<PREC>::T b0,
@@ -259,18 +342,20 @@ __device__ __forceinline__ void brick_line_sweep(const OperatorCoeffs& c, typena
       T x[N1], z[N1], ya[N1], yb[N1];
 #pragma unroll
       for (int s = 0; s < N1; ++s) x[s] = a[s * st];
-      if constexpr (KIND == 0) {
-        mv<PREC, N1, false>(c, MAT_M, x, ya);
-        mv<PREC, N1, false>(c, matK, x, yb);
-      } else if constexpr (KIND == 3) {
-        mv<PREC, N1, false>(c, matK, x, ya);
-      } else if constexpr (KIND == 4) {
-        mv<PREC, N1, false>(c, matK, x, yb);
-      } else {
+      if constexpr (KIND == 1 || KIND == 2) {
 #pragma unroll
         for (int s = 0; s < N1; ++s) z[s] = b[s * st];
-        if constexpr (KIND == 1) mv<PREC, N1, false>(c, MAT_M, x, ya);
-        mv2<PREC, N1>(c, matK, x, MAT_M, z, yb);
+      }
+      if constexpr (KIND == 0) {
+        eo_apply<PREC, N1, true, true, false>(c, MAT_M, matK, MAT_M, x, z, ya, yb);
+      } else if constexpr (KIND == 1) {
+        eo_apply<PREC, N1, true, true, true>(c, MAT_M, matK, MAT_M, x, z, ya, yb);
+      } else if constexpr (KIND == 2) {
+        eo_apply<PREC, N1, false, true, true>(c, MAT_M, matK, MAT_M, x, z, ya, yb);
+      } else if constexpr (KIND == 3) {
+        eo_apply<PREC, N1, true, false, false>(c, matK, matK, matK, x, z, ya, yb);
+      } else {
+        eo_apply<PREC, N1, false, true, false>(c, matK, matK, matK, x, z, ya, yb);
       }
       constexpr bool WA = KIND == 0 || KIND == 1 || KIND == 3;  // writes A
       constexpr bool WB = KIND != 3;                             // writes B
@@ -517,8 +602,10 @@ __device__ void cell_diag(const OperatorCoeffs& c, double* V, double* S, int bx,
         if (GEOM == GEOM_AFFINE) {
           const int qa = q % N1, qb = (q / N1) % N1, qc = q / N2;
           C = c.w[qa] * c.w[qb] * c.w[qc] * c.h[0] * c.h[1] * c.h[2];
-        } else {
+        } else if (GEOM == GEOM_DEFORMED) {
           C = __ldg(geo + (int64_t)cc.cell[ci] * 10 * N3 + 9 * N3 + q);
+        } else {
+          C = 0.0;  // the final tensor stores no JxW: set-up rejects the mass operator there
         }
       } else if (GEOM == GEOM_AFFINE) {
         const int qa = q % N1, qb = (q / N1) % N1, qc = q / N2;
@@ -695,6 +782,7 @@ __device__ __forceinline__ void post_sums(DotAcc<PREC> (&sm)[7], typename Num<PR
 // ------------------------------------------------------------------------------------
 // The tile kernel
 // ------------------------------------------------------------------------------------
+
 // 16-byte loads and stores of VN = 16 / sizeof(T) consecutive values
 template <typename T>
 __device__ __forceinline__ void ld16(const T* p, T (&v)[16 / sizeof(T)]) {
@@ -720,7 +808,7 @@ __device__ __forceinline__ int64_t brick_global_index(const TileGeom& g, int tx,
   return tile_base(g, ntx, nty, ntz) + nli + (int64_t)nox * (nlj + (int64_t)noy * nlk);
 }
 
-template <int P, int MODE, int GEOM, int PREC>
+template <int P, int MODE, int GEOM, int PREC, int NC>
 __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a_all, const OperatorCoeffs c) {
   using T = typename Num<PREC>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -827,25 +915,27 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a_all, co
   // 1-3, with the per-CTA sums accumulated over all of them; the geometry and
   // the Jacobi diagonal are shared by the components.
   DotAcc<PREC> sm[7];
-  const int ncomp = (MODE == MODE_CG || MODE == MODE_OPERATOR) ? a_all.ncomp : 1;
-  for (int comp = 0; comp < ncomp; ++comp) {
-  TileArgs a = a_all;
-  if (comp > 0) {
-    __syncthreads();  // the previous component is finished with U and V
-    const int64_t co = comp * a_all.comp_stride;
-    constexpr int64_t ve = MODE == MODE_CG ? (int64_t)sizeof(T) : (int64_t)sizeof(double);
-    auto shift = [&](const void* ptr, int64_t es) { return (const void*)(static_cast<const char*>(ptr) + co * es); };
-    a.in0 = shift(a_all.in0, ve);
-    a.out0 = const_cast<void*>(shift(a_all.out0, ve));
-    if constexpr (MODE == MODE_CG) {
-      a.in1 = shift(a_all.in1, ve);
-      a.in2 = shift(a_all.in2, ve);
-      a.out1 = const_cast<void*>(shift(a_all.out1, ve));
-      a.out2 = const_cast<void*>(shift(a_all.out2, ve));
-      a.x = const_cast<void*>(shift(a_all.x, ve));
-    }
-    a.shell = static_cast<char*>(a_all.shell) + comp * a_all.shell_comp_stride * (int64_t)sizeof(T);
-  }
+  // NC (1 or 3) is a template parameter: a run-time trip count moves the
+  // FP64 kernel's per-thread arrays to local memory
+#pragma unroll 1
+  for (int comp = 0; comp < NC; ++comp) {
+  const TileArgs& a = a_all;
+  // this component's vectors (the diagonal, geometry and scalars are shared)
+  const int64_t co = comp * a_all.comp_stride;
+  constexpr int64_t ve = MODE == MODE_CG ? (int64_t)sizeof(T) : (int64_t)sizeof(double);
+  auto shifted = [&](const void* ptr) -> void* {
+    return ptr ? const_cast<char*>(static_cast<const char*>(ptr)) + co * ve : nullptr;
+  };
+  const void* const c_in0 = shifted(a_all.in0);
+  const void* const c_in1 = shifted(a_all.in1);
+  const void* const c_in2 = shifted(a_all.in2);
+  void* const c_out0 = shifted(a_all.out0);
+  void* const c_out1 = shifted(a_all.out1);
+  void* const c_out2 = shifted(a_all.out2);
+  void* const c_x = shifted(a_all.x);
+  void* const c_shell = static_cast<char*>(a_all.shell) + comp * a_all.shell_comp_stride * (int64_t)sizeof(T);
+  if (comp > 0) __syncthreads();  // the previous component is finished with U and V
+
   // ---------------- phase 1: pre ----------------
   // CG mode: the owned block is processed in 16-byte chunks of VN nodes (it is
   // contiguous and, when base and n_own are multiples of VN, aligned), two
@@ -855,17 +945,19 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a_all, co
   constexpr int VN = 16 / sizeof(T);
   // the whole-brick affine operator overwrites V completely; the cell-wise ones accumulate into it
   constexpr bool kZeroV = !(GEOM == GEOM_AFFINE && (MODE == MODE_CG || MODE == MODE_OPERATOR));
-  const bool vec_ok = MODE == MODE_CG && (base % VN) == 0 && (n_own % VN) == 0;
+  // 16-byte accesses need the tile's block aligned in every vector: the
+  // component's vectors start co elements in, the shared diagonal does not
+  const bool vec_ok = MODE == MODE_CG && (base % VN) == 0 && (co % VN) == 0 && (n_own % VN) == 0;
   const int n_chunks = vec_ok ? n_own / VN : 0;
   const int scalar_begin = vec_ok ? n_own : 0;
   if constexpr (MODE == MODE_CG) {
-    const T* r_old = static_cast<const T*>(a.in0) + base;
-    const T* v_old = static_cast<const T*>(a.in1) + base;
-    const T* p_old = static_cast<const T*>(a.in2) + base;
+    const T* r_old = static_cast<const T*>(c_in0) + base;
+    const T* v_old = static_cast<const T*>(c_in1) + base;
+    const T* p_old = static_cast<const T*>(c_in2) + base;
     const T* dinv_o = static_cast<const T*>(a.diag_inv) + base;
-    T* r_new = static_cast<T*>(a.out0) + base;
-    T* p_new = static_cast<T*>(a.out2) + base;
-    T* x_o = static_cast<T*>(a.x) + base;
+    T* r_new = static_cast<T*>(c_out0) + base;
+    T* p_new = static_cast<T*>(c_out2) + base;
+    T* x_o = static_cast<T*>(c_x) + base;
     for (int c0 = threadIdx.x; c0 < n_chunks; c0 += 2 * kThreads) {
       T r4[2][VN], v4[2][VN], p4[2][VN], d4[2][VN];
 #pragma unroll
@@ -937,7 +1029,7 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a_all, co
     if constexpr (MODE == MODE_OPERATOR) {
       double src[NB];
 #pragma unroll
-      for (int b = 0; b < NB; ++b) src[b] = static_cast<const double*>(a.in0)[gi[b]];
+      for (int b = 0; b < NB; ++b) src[b] = static_cast<const double*>(c_in0)[gi[b]];
 #pragma unroll
       for (int b = 0; b < NB; ++b)
         if (ok[b]) U[sidx[b]] = dir[b] ? t_zero<PREC>() : t_from_double<PREC>(src[b]);
@@ -945,9 +1037,9 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a_all, co
       T r_o[NB], v_o[NB], p_o[NB], dinv[NB];
 #pragma unroll
       for (int b = 0; b < NB; ++b) {
-        r_o[b] = static_cast<const T*>(a.in0)[gi[b]];
-        v_o[b] = static_cast<const T*>(a.in1)[gi[b]];
-        p_o[b] = static_cast<const T*>(a.in2)[gi[b]];
+        r_o[b] = static_cast<const T*>(c_in0)[gi[b]];
+        v_o[b] = static_cast<const T*>(c_in1)[gi[b]];
+        p_o[b] = static_cast<const T*>(c_in2)[gi[b]];
         dinv[b] = static_cast<const T*>(a.diag_inv)[gi[b]];
       }
 #pragma unroll
@@ -957,10 +1049,10 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a_all, co
         const T pk = t_axby<PREC>(dinv[b], rk, beta_t, p_o[b]);      // M^{-1} r_k + beta_{k-1} p_{k-1}
         U[sidx[b]] = dir[b] ? t_zero<PREC>() : pk;
         if (own[b]) {
-          static_cast<T*>(a.out0)[gi[b]] = rk;
-          static_cast<T*>(a.out2)[gi[b]] = pk;
+          static_cast<T*>(c_out0)[gi[b]] = rk;
+          static_cast<T*>(c_out2)[gi[b]] = pk;
           if (xupd) {
-            T* x = static_cast<T*>(a.x);
+            T* x = static_cast<T*>(c_x);
             const T dp = t_sub<PREC>(p_o[b], t_mul<PREC>(dinv[b], r_o[b]));  // p_{k-1} - M^{-1} r_{k-1}
             x[gi[b]] = t_add<PREC>(x[gi[b]], t_axby<PREC>(xa, p_o[b], xr, dp));
           }
@@ -1026,12 +1118,12 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a_all, co
   // shell; the other owned nodes are final.  In the chunked path the value
   // stored for a shared owned node is a placeholder that the tail kernel
   // overwrites with the complete sum.
-  T* shell = static_cast<T*>(a.shell);
+  T* shell = static_cast<T*>(c_shell);
   if constexpr (MODE == MODE_CG) {
-    const T* r_k = static_cast<const T*>(a.out0) + base;
-    const T* p_k = static_cast<const T*>(a.out2) + base;
+    const T* r_k = static_cast<const T*>(c_out0) + base;
+    const T* p_k = static_cast<const T*>(c_out2) + base;
     const T* dinv_o = static_cast<const T*>(a.diag_inv) + base;
-    T* v_new = static_cast<T*>(a.out1) + base;
+    T* v_new = static_cast<T*>(c_out1) + base;
     for (int c0 = threadIdx.x; c0 < n_chunks; c0 += 2 * kThreads) {
       T r4[2][VN], p4[2][VN], d4[2][VN];
 #pragma unroll
@@ -1107,25 +1199,25 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a_all, co
       T rk[NB], dv[NB], pd[NB];
 #pragma unroll
       for (int b = 0; b < NB; ++b) {
-        rk[b] = static_cast<const T*>(a.out0)[gi[b]];
+        rk[b] = static_cast<const T*>(c_out0)[gi[b]];
         dv[b] = static_cast<const T*>(a.diag_inv)[gi[b]];
-        pd[b] = static_cast<const T*>(a.out2)[gi[b]];
+        pd[b] = static_cast<const T*>(c_out2)[gi[b]];
       }
 #pragma unroll
       for (int b = 0; b < NB; ++b) {
         if (!fin[b]) continue;
         const T pk = pd[b];
         const T v = dir[b] ? pk : V[sidx[b]];
-        static_cast<T*>(a.out1)[gi[b]] = v;
+        static_cast<T*>(c_out1)[gi[b]] = v;
         post_sums<PREC>(sm, rk[b], pk, v, dv[b]);
       }
     } else {
 #pragma unroll
       for (int b = 0; b < NB; ++b) {
         if (!fin[b]) continue;
-        double* out = static_cast<double*>(a.out0);
+        double* out = static_cast<double*>(c_out0);
         if constexpr (MODE == MODE_OPERATOR)
-          out[gi[b]] = dir[b] ? static_cast<const double*>(a.in0)[gi[b]] : t_to_double<PREC>(V[sidx[b]]);
+          out[gi[b]] = dir[b] ? static_cast<const double*>(c_in0)[gi[b]] : t_to_double<PREC>(V[sidx[b]]);
         else if constexpr (MODE == MODE_RHS)
           out[gi[b]] = dir[b] ? 0.0 : t_to_double<PREC>(V[sidx[b]]);
         else
@@ -1272,40 +1364,50 @@ inline size_t tile_smem_elems(int P, int geom, int elem_bytes, const TileGeom& g
 template <int P>
 using TileFn = void (*)(const TileArgs, const OperatorCoeffs);
 
-// supported (mode, precision) pairs; nullptr otherwise
-template <int P, int GEOM>
-TileFn<P> tile_fn_g(int mode, int prec) {
+// supported (mode, precision, component count) triples; nullptr otherwise
+template <int P, int GEOM, int NC>
+TileFn<P> tile_fn_gn(int mode, int prec) {
   switch (mode) {
     case MODE_CG:
-      return prec == PREC_F64 ? tile_kernel<P, MODE_CG, GEOM, PREC_F64>
-                              : (prec == PREC_DD ? tile_kernel<P, MODE_CG, GEOM, PREC_DD>
-                                                 : tile_kernel<P, MODE_CG, GEOM, PREC_F32>);
+      return prec == PREC_F64 ? tile_kernel<P, MODE_CG, GEOM, PREC_F64, NC>
+                              : (prec == PREC_DD ? tile_kernel<P, MODE_CG, GEOM, PREC_DD, NC>
+                                                 : tile_kernel<P, MODE_CG, GEOM, PREC_F32, NC>);
     case MODE_OPERATOR:
-      return prec == PREC_F64 ? tile_kernel<P, MODE_OPERATOR, GEOM, PREC_F64>
-                              : (prec == PREC_DD ? tile_kernel<P, MODE_OPERATOR, GEOM, PREC_DD> : nullptr);
-    case MODE_RHS: return prec == PREC_F64 ? tile_kernel<P, MODE_RHS, GEOM, PREC_F64> : nullptr;
-    case MODE_DIAG: return prec == PREC_F64 ? tile_kernel<P, MODE_DIAG, GEOM, PREC_F64> : nullptr;
+      return prec == PREC_F64 ? tile_kernel<P, MODE_OPERATOR, GEOM, PREC_F64, NC>
+                              : (prec == PREC_DD ? tile_kernel<P, MODE_OPERATOR, GEOM, PREC_DD, NC> : nullptr);
+    case MODE_RHS:
+      if constexpr (NC == 1) return prec == PREC_F64 ? tile_kernel<P, MODE_RHS, GEOM, PREC_F64, 1> : nullptr;
+      return nullptr;
+    case MODE_DIAG:
+      if constexpr (NC == 1) return prec == PREC_F64 ? tile_kernel<P, MODE_DIAG, GEOM, PREC_F64, 1> : nullptr;
+      return nullptr;
     default: return nullptr;
   }
 }
 
+template <int P, int GEOM>
+TileFn<P> tile_fn_g(int mode, int prec, int ncomp) {
+  return ncomp == 3 ? tile_fn_gn<P, GEOM, 3>(mode, prec) : tile_fn_gn<P, GEOM, 1>(mode, prec);
+}
+
 template <int P>
-TileFn<P> tile_fn(int mode, int geom, int prec) {
-  if (geom == GEOM_AFFINE) return tile_fn_g<P, GEOM_AFFINE>(mode, prec);
-  if (geom == GEOM_TENSOR) return tile_fn_g<P, GEOM_TENSOR>(mode, prec);
-  return tile_fn_g<P, GEOM_DEFORMED>(mode, prec);
+TileFn<P> tile_fn(int mode, int geom, int prec, int ncomp) {
+  if (geom == GEOM_AFFINE) return tile_fn_g<P, GEOM_AFFINE>(mode, prec, ncomp);
+  if (geom == GEOM_TENSOR) return tile_fn_g<P, GEOM_TENSOR>(mode, prec, ncomp);
+  return tile_fn_g<P, GEOM_DEFORMED>(mode, prec, ncomp);
 }
 
 // once per problem (outside any stream capture): allow the dynamic shared memory
 template <int P>
 cudaError_t prepare_tile_p(int geom, int prec, size_t smem) {
-  for (int mode = 0; mode < 4; ++mode) {
-    TileFn<P> fn = tile_fn<P>(mode, geom, prec);
+  for (int k = 0; k < 8; ++k) {
+    TileFn<P> fn = tile_fn<P>(k & 3, geom, prec, k < 4 ? 1 : 3);
     if (!fn) continue;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    // FP32 kernels fit three CTAs per SM by registers: give them the shared memory for it
-    if (prec == PREC_F32) {
+    // FP32 and whole-brick affine kernels can fit three CTAs per SM by
+    // registers: give them the shared memory for it
+    if (prec == PREC_F32 || geom == GEOM_AFFINE) {
       e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
                                (int)cudaSharedmemCarveoutMaxShared);
       if (e != cudaSuccess) return e;
@@ -1316,7 +1418,7 @@ cudaError_t prepare_tile_p(int geom, int prec, size_t smem) {
 
 template <int P>
 cudaError_t launch_tile_p(int mode, const TileArgs& a, const OperatorCoeffs& c, cudaStream_t s) {
-  TileFn<P> fn = tile_fn<P>(mode, a.geom, a.prec);
+  TileFn<P> fn = tile_fn<P>(mode, a.geom, a.prec, a.ncomp);
   if (!fn) return cudaErrorInvalidValue;
   const size_t smem = tile_smem_elems(P, a.geom, prec_bytes(a.prec), a.g, mode) * prec_bytes(a.prec);
   fn<<<(unsigned)a.g.n_tiles, kThreads, smem, s>>>(a, c);

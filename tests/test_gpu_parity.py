@@ -465,3 +465,58 @@ def test_vector_valued_operator_and_solve(mfcg, p, cells, amp, coef, geometry, p
         assert np.linalg.norm(b - A3 @ xh) < 1e-10 * np.linalg.norm(b)
     assert _rel(_to_host(prob, x), ref.x) <= SOL_TOL
     prob.close()
+
+
+MASS_CASES = [
+    (2, (8, 8, 8), 0.0, "constant", None),
+    (5, (3, 4, 3), 0.0, "constant", (2, 2, 3)),
+    (3, (3, 4, 3), 0.05, "sin_x", None),
+    (6, (2, 3, 2), 0.08, "constant", None),
+]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "double_float", "fp32_inner"])
+@pytest.mark.parametrize("p,cells,amp,coef,tile", MASS_CASES)
+def test_mass_operator_matches_oracle(mfcg, p, cells, amp, coef, tile, precision):
+    # the mass operator (BP1): operator, diagonal and right-hand side, and the
+    # Jacobi-CG solution of M x = b, against the oracle's mass matrix
+    op = fem.Problem(p, tuple(cells), amp, fem.COEF_SIN_X if coef == "sin_x" else fem.COEF_CONSTANT,
+                     op=fem.OP_MASS)
+    A = fem.assemble(op)
+    prob = _gpu_problem(mfcg, p, cells, amp, coef, tile=tile, precision=precision, operator="mass")
+    u = inputs.random_vector(op.n_dofs, salt=p)
+    got = _to_host(prob, prob.apply_operator(_to_dev(prob, u)))
+    assert _rel(got, A @ u) <= OP_TOL
+    assert _rel(_to_host(prob, prob.diagonal()), A.diagonal()) <= OP_TOL
+    b = fem.rhs(op)
+    assert _rel(_to_host(prob, prob.rhs()), b) <= 1e-12
+    ref = ocg.pcg_algorithm1(lambda v: A @ v, b, 1.0 / A.diagonal(), 1e-10, 5000)
+    x, info = prob.cg_solve(_to_dev(prob, b), rtol=1e-10, maxit=5000)
+    assert info["converged"] == 1
+    if precision != "fp32_inner":
+        assert abs(info["iterations"] - ref.iterations) <= 1
+    assert _rel(_to_host(prob, x), ref.x) <= SOL_TOL
+    prob.close()
+
+
+def test_vector_valued_mass_operator(mfcg):
+    # BP2: three components of the mass operator in one CG
+    import scipy.sparse as sp
+
+    op = fem.Problem(4, (4, 3, 5), op=fem.OP_MASS)
+    A = fem.assemble(op)
+    prob = mfcg.Problem(4, (4, 3, 5), operator="mass", components=3, precision="double_float")
+    b1 = fem.rhs(op)
+    b = np.concatenate([(c + 1) * b1 for c in range(3)])
+    assert _rel(_to_host(prob, prob.rhs()), b) <= 1e-12
+    A3 = sp.block_diag([A, A, A], format="csr")
+    ref = ocg.pcg_algorithm1(lambda v: A3 @ v, b, 1.0 / A3.diagonal(), 1e-10, 5000)
+    x, info = prob.cg_solve(_to_dev(prob, b), rtol=1e-10, maxit=5000)
+    assert info["converged"] == 1 and abs(info["iterations"] - ref.iterations) <= 1
+    assert _rel(_to_host(prob, x), ref.x) <= SOL_TOL
+    prob.close()
+
+
+def test_mass_operator_rejects_final_tensor_storage(mfcg):
+    with pytest.raises(mfcg.MfcgError):
+        mfcg.Problem(3, (2, 2, 2), amplitude=0.05, geometry="deformed_tensor", operator="mass")

@@ -349,3 +349,69 @@ def test_algorithm5_with_identity_is_algorithm4_exact_rationals():
     assert r1.iterations == r5.iterations
     assert r1.alphas == r5.alphas and r1.betas == r5.betas
     assert list(r1.x) == list(r5.x)
+
+
+# ---------------------------------------------------------------- mass operator
+
+
+def _mass_kronecker(p, cells, M1, dirichlet=True):
+    """h^3 M (x) M (x) M from 1D assembled mass matrices (x fastest)."""
+    mats = []
+    for d in range(3):
+        n = p * cells[d] + 1
+        h = 1.0 / cells[d]
+        Mg = np.zeros((n, n))
+        for c in range(cells[d]):
+            s = slice(p * c, p * c + p + 1)
+            Mg[s, s] += M1 * h
+        mats.append(sp.csr_matrix(Mg))
+    Mx, My, Mz = mats
+    A = sp.kron(Mz, sp.kron(My, Mx)).tocsr()
+    if not dirichlet:
+        return A
+    bnd = fem.boundary_mask(fem.Problem(p, cells))
+    keep = sp.diags((~bnd).astype(float))
+    return (keep @ A @ keep + sp.diags(bnd.astype(float))).tocsr()
+
+
+def test_mass_matrix_equals_kronecker_q2_exact_1d():
+    # Cartesian mass matrix = Kronecker product of the exact rational Q2 1D mass matrices
+    rows = {(r[0], int(r[1])): np.array([float(Fraction(t)) for t in r[2:]]) for r in _read_golden("q1_q2_1d_matrices.txt")}
+    M1 = rows[("M", 2)].reshape(3, 3)
+    cells = (3, 2, 4)
+    A = fem.assemble(fem.Problem(2, cells, op=fem.OP_MASS))
+    B = _mass_kronecker(2, cells, M1)
+    assert abs(A - B).max() < 1e-14 * abs(B).max()
+
+
+@pytest.mark.parametrize("p,amp,tol", [(3, 0.0, 1e-14), (4, 0.05, 1e-13), (2, 0.08, 1e-13)])
+def test_mass_matrix_total_is_domain_volume(p, amp, tol):
+    # without boundary rows, 1^T M 1 = |Omega| = 1: the deformation maps the unit
+    # cube onto itself.  On deformed cells det J/h^3 = 1 + A (ds/dX + ds/dY + ds/dZ)
+    # and each derivative term sums to zero exactly over a uniform row of cells
+    # with the same Gauss rule in every cell (a sum of e^{2 pi i c/N} over c)
+    A = fem.assemble(fem.Problem(p, (3, 3, 2), amp, op=fem.OP_MASS), dirichlet=False)
+    one = np.ones(A.shape[0])
+    assert abs(one @ (A @ one) - 1.0) < tol
+
+
+def test_mass_projection_reproduces_polynomial():
+    # u = x(1-x) y(1-y) z(1-z) lies in Q_2 and vanishes on the boundary: the
+    # discrete L2 projection (mass matrix, right-hand side by the same Gauss rule,
+    # exact for this integrand) returns its nodal values
+    prob = fem.Problem(2, (3, 2, 3), op=fem.OP_MASS)
+    A = fem.assemble(prob)
+    phi, _ = fem.reference_tables(prob.p)
+    b = np.zeros(prob.n_dofs)
+    ids = np.arange(prob.n_cells)
+    x, _, detJ, w = fem.quadrature_geometry(prob, ids)
+    u = np.prod(x * (1.0 - x), axis=-1)
+    np.add.at(b, fem.local_to_global(prob, ids), (u * detJ * w[None, :]) @ phi)
+    b[fem.boundary_mask(prob)] = 0.0
+    xs = spla.spsolve(A.tocsc(), b)
+    nx, ny, nz = prob.nodes_per_dim
+    nodes = fem.gauss_lobatto_nodes(prob.p)
+    coord = [np.concatenate([(c + nodes[:-1]) / n for c in range(n)] + [np.array([1.0])]) for n in prob.cells]
+    Z, Y, X = np.meshgrid(coord[2], coord[1], coord[0], indexing="ij")
+    exact = (X * (1 - X) * Y * (1 - Y) * Z * (1 - Z)).reshape(-1)
+    np.testing.assert_allclose(xs, exact, atol=1e-14)
