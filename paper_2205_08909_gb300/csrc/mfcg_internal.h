@@ -77,6 +77,60 @@ __host__ __device__ inline int64_t tile_base(const TileGeom& g, int tx, int ty, 
          (int64_t)(g.p * g.T[0]) * tx * oy * oz;
 }
 
+// Position of owned node (li, lj, lk) inside its tile's block of ox*oy*oz
+// values, "x face first": the li = 0 plane (lj fastest) comes first, then the
+// nodes with li >= 1 in lexicographic order (rows of ox - 1; ox >= 2 always).
+// The li = 0 plane holds the nodes shared with the lower x neighbour, so the
+// tail kernel reads and writes them contiguously.
+__host__ __device__ inline int64_t owned_offset(int li, int lj, int lk, int ox, int oy, int oz) {
+  if (li == 0) return lj + (int64_t)oy * lk;
+  return (int64_t)oy * oz + (li - 1) + (int64_t)(ox - 1) * (lj + (int64_t)oy * lk);
+}
+
+// Decoding of owned positions in the same order: coordinates of position o,
+// and the step to the next position.
+struct OwnedShape {
+  int ox, oy, oz;
+  FastDiv foy, fox1;
+};
+
+__host__ __device__ inline OwnedShape owned_shape(int ox, int oy, int oz) {
+  return {ox, oy, oz, make_fastdiv((uint32_t)oy), make_fastdiv((uint32_t)(ox - 1))};
+}
+
+__host__ __device__ inline void owned_coords(const OwnedShape& s, int o, int& li, int& lj, int& lk) {
+  const int n_xface = s.oy * s.oz;
+  if (o < n_xface) {
+    li = 0;
+    lk = (int)fdiv((uint32_t)o, s.foy);
+    lj = o - lk * s.oy;
+    return;
+  }
+  const int r = o - n_xface;
+  const int row = (int)fdiv((uint32_t)r, s.fox1);
+  li = 1 + r - row * (s.ox - 1);
+  lk = (int)fdiv((uint32_t)row, s.foy);
+  lj = row - lk * s.oy;
+}
+
+__host__ __device__ inline void owned_next(const OwnedShape& s, int& li, int& lj, int& lk) {
+  if (li == 0) {
+    if (++lj == s.oy) {
+      lj = 0;
+      if (++lk == s.oz) {
+        lk = 0;
+        li = 1;
+      }
+    }
+  } else if (++li == s.ox) {
+    li = 1;
+    if (++lj == s.oy) {
+      lj = 0;
+      ++lk;
+    }
+  }
+}
+
 // position of node (i,j,k) in the tile-blocked vector
 __host__ __device__ inline int64_t node_index(const TileGeom& g, int i, int j, int k) {
   const int tx = tile_of(g, 0, i), ty = tile_of(g, 1, j), tz = tile_of(g, 2, k);
@@ -85,7 +139,7 @@ __host__ __device__ inline int64_t node_index(const TileGeom& g, int i, int j, i
   const int li = i - pTx * tx, lj = j - pTy * ty, lk = k - pTz * tz;
   const int64_t base = (int64_t)g.nn[0] * g.nn[1] * pTz * tz + (int64_t)g.nn[0] * pTy * ty * oz +
                        (int64_t)pTx * tx * oy * oz;
-  return base + li + (int64_t)ox * (lj + (int64_t)oy * lk);
+  return base + owned_offset(li, lj, lk, ox, oy, oz);
 }
 
 __host__ __device__ inline bool is_dirichlet(const TileGeom& g, int i, int j, int k) {

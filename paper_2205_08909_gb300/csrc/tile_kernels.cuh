@@ -801,11 +801,11 @@ __device__ __forceinline__ void st16(T* p, const T (&v)[16 / sizeof(T)]) {
 // nodes past the owned extent belong to the next tile along that direction
 __device__ __forceinline__ int64_t brick_global_index(const TileGeom& g, int tx, int ty, int tz, int li, int lj,
                                                       int lk, int ox, int oy, int oz, int64_t base) {
-  if (li < ox && lj < oy && lk < oz) return base + li + (int64_t)ox * (lj + (int64_t)oy * lk);
+  if (li < ox && lj < oy && lk < oz) return base + owned_offset(li, lj, lk, ox, oy, oz);
   const int ntx = li < ox ? tx : tx + 1, nty = lj < oy ? ty : ty + 1, ntz = lk < oz ? tz : tz + 1;
   const int nli = li < ox ? li : li - ox, nlj = lj < oy ? lj : lj - oy, nlk = lk < oz ? lk : lk - oz;
-  const int nox = owned_count(g, 0, ntx), noy = owned_count(g, 1, nty);
-  return tile_base(g, ntx, nty, ntz) + nli + (int64_t)nox * (nlj + (int64_t)noy * nlk);
+  const int nox = owned_count(g, 0, ntx), noy = owned_count(g, 1, nty), noz = owned_count(g, 2, ntz);
+  return tile_base(g, ntx, nty, ntz) + owned_offset(nli, nlj, nlk, nox, noy, noz);
 }
 
 template <int P, int MODE, int GEOM, int PREC, int NC>
@@ -864,17 +864,14 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a_all, co
   // tiles.  Dirichlet tests only in tiles that touch the domain boundary.
   const bool bnd_tile = tx == 0 || ty == 0 || tz == 0 || lastx || lasty || lastz;
   const int n_own = ox * oy * oz;
-  const FastDiv fox = make_fastdiv((uint32_t)ox), foxy = make_fastdiv((uint32_t)(ox * oy));
+  const FastDiv fox = make_fastdiv((uint32_t)ox);
   const FastDiv fby = make_fastdiv((uint32_t)by);
   const int nfx = lastx ? 0 : by * bz, nfy = lasty ? 0 : ox * bz, nfz = lastz ? 0 : ox * oy;
   const int n_face = nfx + nfy + nfz;
-  // (li, lj, lk) of owned node o
-  auto own_coords = [&](int o, int& li, int& lj, int& lk) {
-    lk = (int)fdiv((uint32_t)o, foxy);
-    const int rem = o - lk * ox * oy;
-    lj = (int)fdiv((uint32_t)rem, fox);
-    li = rem - lj * ox;
-  };
+  // (li, lj, lk) of owned node o (x face first, see owned_offset) and the step to the next one
+  const OwnedShape osh = owned_shape(ox, oy, oz);
+  auto own_coords = [&](int o, int& li, int& lj, int& lk) { owned_coords(osh, o, li, lj, lk); };
+  auto own_next = [&](int& li, int& lj, int& lk) { owned_next(osh, li, lj, lk); };
   // (li, lj, lk) of "+" face node f
   auto face_coords = [&](int f, int& li, int& lj, int& lk) {
     if (f < nfx) {
@@ -977,13 +974,7 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a_all, co
         own_coords(c * VN, li, lj, lk);
 #pragma unroll
         for (int e = 0; e < VN; ++e) {
-          if (e > 0 && ++li == ox) {
-            li = 0;
-            if (++lj == oy) {
-              lj = 0;
-              ++lk;
-            }
-          }
+          if (e > 0) own_next(li, lj, lk);
           rk[e] = t_axpy<PREC>(alpha_m, v4[h][e], r4[h][e]);        // r_{k-1} - alpha_{k-1} v_{k-1}
           pk[e] = t_axby<PREC>(d4[h][e], rk[e], beta_t, p4[h][e]);  // M^{-1} r_k + beta_{k-1} p_{k-1}
           const int sidx = li + bx * (lj + by * lk);
@@ -1142,13 +1133,7 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a_all, co
         own_coords(c * VN, li, lj, lk);
 #pragma unroll
         for (int e = 0; e < VN; ++e) {
-          if (e > 0 && ++li == ox) {
-            li = 0;
-            if (++lj == oy) {
-              lj = 0;
-              ++lk;
-            }
-          }
+          if (e > 0) own_next(li, lj, lk);
           const int sidx = li + bx * (lj + by * lk);
           const bool dir = bnd_tile && is_dirichlet(g, gi0 + li, gj0 + lj, gk0 + lk);
           const bool shared = !dir && ((li == 0 && tx > 0) || (lj == 0 && ty > 0) || (lk == 0 && tz > 0));

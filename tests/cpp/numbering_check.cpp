@@ -51,6 +51,18 @@ static int check(int p, const int N[3], const int T[3]) {
             }
         REQUIRE(lo == expect_base && hi - lo + 1 == (int64_t)ox * oy * oz);
         expect_base += (int64_t)ox * oy * oz;
+        // the kernels' decoding of owned positions inverts owned_offset, and
+        // the step visits the positions in order
+        const OwnedShape sh = owned_shape(ox, oy, oz);
+        int si = 0, sj = 0, sk = 0;
+        for (int o = 0; o < ox * oy * oz; ++o) {
+          int li, lj, lk;
+          owned_coords(sh, o, li, lj, lk);
+          REQUIRE(li >= 0 && li < ox && lj >= 0 && lj < oy && lk >= 0 && lk < oz);
+          REQUIRE(owned_offset(li, lj, lk, ox, oy, oz) == o);
+          if (o > 0) owned_next(sh, si, sj, sk);
+          REQUIRE(si == li && sj == lj && sk == lk);
+        }
       }
   // 3. shell writes of the tile kernel: unique slots
   std::map<int64_t, int64_t> slot_node;  // slot -> global node id written there
