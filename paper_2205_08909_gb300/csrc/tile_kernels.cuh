@@ -935,11 +935,14 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a_all, co
 
   // ---------------- phase 1: pre ----------------
   // CG mode: the owned block is processed in 16-byte chunks of VN nodes (it is
-  // contiguous and, when base and n_own are multiples of VN, aligned), two
+  // contiguous and, when base and n_own are multiples of VN, aligned), CH
   // chunks per thread in flight; the remaining owned nodes and the "+" face
   // nodes take the scalar path with NB nodes per thread in flight.
   constexpr int NB = PREC == PREC_F32 ? 4 : 2;
   constexpr int VN = 16 / sizeof(T);
+  // 16-byte chunks in flight per thread in the owned-block loops (four
+  // measured slower for double-float and spill for FP64)
+  constexpr int CH = 2;
   // the whole-brick affine operator overwrites V completely; the cell-wise ones accumulate into it
   constexpr bool kZeroV = !(GEOM == GEOM_AFFINE && (MODE == MODE_CG || MODE == MODE_OPERATOR));
   // 16-byte accesses need the tile's block aligned in every vector: the
@@ -955,10 +958,10 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a_all, co
     T* r_new = static_cast<T*>(c_out0) + base;
     T* p_new = static_cast<T*>(c_out2) + base;
     T* x_o = static_cast<T*>(c_x) + base;
-    for (int c0 = threadIdx.x; c0 < n_chunks; c0 += 2 * kThreads) {
-      T r4[2][VN], v4[2][VN], p4[2][VN], d4[2][VN];
+    for (int c0 = threadIdx.x; c0 < n_chunks; c0 += CH * kThreads) {
+      T r4[CH][VN], v4[CH][VN], p4[CH][VN], d4[CH][VN];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
+      for (int h = 0; h < CH; ++h) {
         const int c = min(c0 + h * kThreads, n_chunks - 1);
         ld16(r_old + c * VN, r4[h]);
         ld16(v_old + c * VN, v4[h]);
@@ -966,7 +969,7 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a_all, co
         ld16(dinv_o + c * VN, d4[h]);
       }
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
+      for (int h = 0; h < CH; ++h) {
         const int c = c0 + h * kThreads;
         if (c >= n_chunks) continue;
         T rk[VN], pk[VN];
@@ -1115,17 +1118,17 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a_all, co
     const T* p_k = static_cast<const T*>(c_out2) + base;
     const T* dinv_o = static_cast<const T*>(a.diag_inv) + base;
     T* v_new = static_cast<T*>(c_out1) + base;
-    for (int c0 = threadIdx.x; c0 < n_chunks; c0 += 2 * kThreads) {
-      T r4[2][VN], p4[2][VN], d4[2][VN];
+    for (int c0 = threadIdx.x; c0 < n_chunks; c0 += CH * kThreads) {
+      T r4[CH][VN], p4[CH][VN], d4[CH][VN];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
+      for (int h = 0; h < CH; ++h) {
         const int c = min(c0 + h * kThreads, n_chunks - 1);
         ld16(r_k + c * VN, r4[h]);
         ld16(p_k + c * VN, p4[h]);
         ld16(dinv_o + c * VN, d4[h]);
       }
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
+      for (int h = 0; h < CH; ++h) {
         const int c = c0 + h * kThreads;
         if (c >= n_chunks) continue;
         T vv[VN];
