@@ -125,22 +125,50 @@ def eo_segment_costs(n1: int, unit: str) -> tuple[float, float, float]:
     return z, y, x
 
 
+def eo_product_cost(n1: int, unit: str, anti: bool = False) -> float:
+    """Operations of one even-odd 1D product y = A x (A centrosymmetric, or
+    anti-centrosymmetric for the collocation derivative): forming the even and
+    odd halves, the two half-size products and the recombination."""
+    h, ne = n1 // 2, n1 - n1 // 2
+    if unit == "flop":
+        add, dot = 1.0, (lambda k: 2.0 * k)
+    else:
+        add, dot = 11.0, (lambda k: 12.0 * k - 5.0)
+    rows = h * (dot(ne) + dot(h) + 2 * add)
+    mid = (dot(h) if anti else dot(ne)) if ne > h else 0.0
+    return 2 * h * add + rows + mid
+
+
+def deformed_cell_cost(n1: int, unit: str, geometry: str) -> float:
+    """Operations per deformed cell: 6 interpolation and 6 collocation-derivative
+    sweeps of (p+1)^2 even-odd products each, two accumulating sweeps, the
+    per-point metric and the node gather."""
+    pencils = n1 * n1
+    sweeps = 6 * pencils * eo_product_cost(n1, unit) + 6 * pencils * eo_product_cost(n1, unit, anti=True)
+    if unit == "flop":
+        metric = 42 if geometry == "deformed" else 18
+        return sweeps + (2 + metric + 1) * n1 ** 3
+    dot3 = 4 + 12 * 2 + 3
+    metric = 3 * dot3 if geometry == "deformed_tensor" else 6 * dot3 + 3 * 7
+    return sweeps + (2 * 11 + metric + 11) * n1 ** 3
+
+
 def algorithmic_flops_per_iteration(degree: int, n_cells: int, n_dofs: int, geometry: str = "affine",
                                     cells=None, tile=None) -> float:
     """FP64 flops of one fused iteration.  Affine cells: the whole-brick
     sweeps in even-odd form over the segments of brick_segments; deformed
-    cells: twelve cell-wise sweeps of (p+1)^4 FMAs (interpolation,
+    cells: twelve cell-wise sweeps in even-odd form (interpolation,
     collocation derivative and their transposes) plus the per-point metric (42
-    flops from J^{-1} and JxW a, 18 from the final tensor).  Plus the vector
-    work per unknown (r, z, p updates 5, x update 5 every other iteration,
-    seven sums with M^-1 r and M^-1 v 16)."""
+    flops from J^{-1} and JxW a, 18 from the final tensor) and the gather
+    (deformed_cell_cost).  Plus the vector work per unknown (r, z, p updates
+    5, x update 5 every other iteration, seven sums with M^-1 r and M^-1 v 16)."""
     n1 = degree + 1
     if geometry == "affine":
         sz, sy, sx = brick_segments(degree, cells, tile)
         cz, cy, cx = eo_segment_costs(n1, "flop")
         op = sz * cz + sy * cy + sx * cx
     else:
-        op = (2.0 * 12 * n1 ** 4 + (42 if geometry == "deformed" else 18) * n1 ** 3) * n_cells
+        op = deformed_cell_cost(n1, "flop", geometry) * n_cells
     return op + 23.5 * n_dofs
 
 
@@ -295,21 +323,17 @@ def dd_ops_per_dof(degree: int, n_cells: int, n_dofs: int, geometry: str = "affi
     the first product of a sum 4, a normalisation 3, a pair addition 11, a pair
     product 7.  Affine operator: the whole-brick sweeps in even-odd form
     (eo_segment_costs) over the segments of brick_segments.  Deformed
-    operator: twelve single-matrix cell-wise sweeps, two accumulating
+    operator: twelve cell-wise sweeps in even-odd form, two accumulating
     transposed-derivative sweeps, the metric (3 three-term sums from the final
     tensor; 6 sums and 3 pair products from J^{-1} and JxW a) and the node
-    gather (one pair addition per cell node)."""
+    gather (one pair addition per cell node): deformed_cell_cost."""
     n1 = degree + 1
-    mv = n1 * (4 + 12 * (n1 - 1) + 3)
-    dot3 = 4 + 12 * 2 + 3
     if geometry == "affine":
         sz, sy, sx = brick_segments(degree, cells, tile)
         cz, cy, cx = eo_segment_costs(n1, "dd")
         op = (sz * cz + sy * cy + sx * cx) / n_dofs
     else:
-        metric = 3 * dot3 if geometry == "deformed_tensor" else 6 * dot3 + 3 * 7
-        per_cell = 12 * n1 * n1 * mv + 2 * 11 * n1 ** 3 + metric * n1 ** 3 + 11 * n1 ** 3
-        op = per_cell * n_cells / n_dofs
+        op = deformed_cell_cost(n1, "dd", geometry) * n_cells / n_dofs
     pre = 34.0 * 1.2                                  # r and p updates on the tile brick (~1.2x the owned nodes)
     x_update = 48.0 / 2                               # every other iteration
     post = 2 * 7 + 7 * 12                             # M^-1 r, M^-1 v and seven accumulations
@@ -394,7 +418,12 @@ def run_ours(args, world, rank, local):
 
     # ---------------- comparators on the same workload
     variants = {}
-    for mode, prec in (("unfused", main_prec), ("fused", "fp64"), ("unfused", "fp64")):
+    # algorithmic bytes per unknown of each form: fused 64; semi-fused (the GPU form of Sec. 6.4:
+    # pre 56, operator 16, post 32) 104; unfused Algorithm 1 152
+    form_bytes = {"fused": 64, "semi_fused": 104, "unfused": 152}
+    for mode, prec in (("unfused", main_prec), ("fused", "fp64"), ("unfused", "fp64"), ("semi_fused", "fp64")):
+        if mode != "fused" and prec == "fp32_inner":
+            continue  # the FP32 inner solver exists in fused form only
         if args.skip_unfused and mode == "unfused":
             continue
         if args.skip_variants and (mode, prec) != ("unfused", main_prec):
@@ -405,7 +434,7 @@ def run_ours(args, world, rank, local):
         bv = prob.rhs()  # each problem's own tile-blocked order
         ms_v, _ = timed_steps(prob, bv, K, W)
         v = dof_its / (ms_v / 1e3) / 1e9
-        vb = (64 if mode == "fused" else 152) + geo_bytes_per_dof
+        vb = form_bytes[mode] + geo_bytes_per_dof
         variants[f"{mode}_{prec}"] = {"value": round(v, 4), "ms_per_step": round(ms_v / K, 3),
                                       "hbm_roofline_frac": round(v / world * vb / hbm, 4),
                                       "algorithmic_bytes_per_dof": round(vb, 2),

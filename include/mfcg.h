@@ -14,8 +14,9 @@
  * ---------------------------------------
  *  - Vectors are arrays of n doubles, n = (p*Nx+1)(p*Ny+1)(p*Nz+1), one per mesh
  *    node including the Dirichlet nodes, in the library's tile-blocked DoF
- *    ordering (the nodes of each tile of cells are contiguous; see
- *    mfcg_to_lexicographic for the conversion).  Dirichlet nodes stay in the
+ *    ordering (the nodes each tile of cells owns are contiguous, its lower x
+ *    face first; see mfcg_to_lexicographic for the conversion); with
+ *    components = 3 the components follow one another.  Dirichlet nodes stay in the
  *    system as identity rows (Sec. 5.3): (A u)_i = u_i there.
  *  - Unless the name ends in _host, pointers are DEVICE pointers on the device
  *    that was current at mfcg_setup; the caller owns them and keeps them alive
@@ -145,14 +146,18 @@ typedef struct mfcg_problem mfcg_problem;
  *   opt           in: may be NULL for defaults.
  *   cuda_stream   in: cudaStream_t (NULL = legacy default stream) used by every call.
  *   out           out: new handle; release with mfcg_destroy.
+ * With tile = {-1,-1,-1} the call sets up and times a few candidate tiles first
+ * (short fixed-iteration solves) and keeps the fastest.
  * Errors: INVALID_ARG (cells < 1, |amplitude| >= 0.1, affine kind with A != 0 or
- * a != 1, bad enums, FP32_INNER without FUSED, SEMI_FUSED with FP32_INNER), UNSUPPORTED_DEGREE,
- * OUT_OF_MEMORY, CUDA_ERROR. */
+ * a != 1, bad enums, FP32_INNER without FUSED, SEMI_FUSED with FP32_INNER,
+ * components other than 0, 1, 3 or components 3 without FUSED, MFCG_OP_MASS with
+ * MFCG_GEOM_DEFORMED_TENSOR), UNSUPPORTED_DEGREE, OUT_OF_MEMORY, CUDA_ERROR. */
 int mfcg_setup(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, const mfcg_options* opt,
                void* cuda_stream, mfcg_problem** out);
 
 /* mfcg_n_dofs -- number n of unknowns, all mesh nodes including Dirichlet ones
- * (Sec. 2: n counts the unique coefficients of the expansion). */
+ * (Sec. 2: n counts the unique coefficients of the expansion), times the number
+ * of components. */
 int mfcg_n_dofs(const mfcg_problem* prob, int64_t* n);
 
 /* mfcg_apply_operator -- dst = A src (Eq. 4 with the cell operator of Eq. 5),

@@ -317,7 +317,7 @@ enum GeomKind { GEOM_AFFINE = 0, GEOM_DEFORMED = 1, GEOM_TENSOR = 2 };
 // values stored per quadrature point by the deformed geometry kinds
 __host__ __device__ constexpr int geo_values(int geom) { return geom == GEOM_TENSOR ? 6 : 10; }
 
-enum MatId { MAT_M = 0, MAT_K0 = 1, MAT_K1 = 2, MAT_K2 = 3, MAT_S = 4, MAT_DC = 5, MAT_MV = 6, NMAT = 7 };
+enum MatId { MAT_M = 0, MAT_K0 = 1, MAT_K1 = 2, MAT_K2 = 3, MAT_S = 4, MAT_DC = 5, MAT_MV = 6, MAT_ST = 7, MAT_DCT = 8, NMAT = 9 };
 
 // operator of the problem: Laplacian (Eq. 5) or mass matrix
 enum OpKind { OP_LAPLACE = 0, OP_MASS = 1 };
@@ -328,19 +328,22 @@ struct OperatorCoeffs {
   // MAT_K0..2 the reference stiffness scaled per direction for box cells
   // (h_y h_z / h_x, ...), MAT_S the interpolation from the Gauss-Lobatto
   // nodes to the Gauss points, MAT_DC the Gauss collocation derivative,
-  // MAT_MV the mass matrix scaled by the cell volume h_x h_y h_z.
+  // MAT_MV the mass matrix scaled by the cell volume h_x h_y h_z, MAT_ST and
+  // MAT_DCT the transposes of MAT_S and MAT_DC.
   double mat[NMAT][kMat];
   // products of 1D tables used by the exact diagonal: SS = S.*S, DS = D.*S,
   // DD = D.*D with D[q][a] = L_a'(g_q)
   double T2[3][kMat];
   // the same matrices as float pairs (hi + lo) for the double-float and FP32 paths
-  float fh[NMAT][kMat];
-  float fl[NMAT][kMat];
-  // even-odd form of the centrosymmetric matrices (A[n-1-i][n-1-j] = A[i][j]):
-  // with e_j = x_j + x_{n-1-j}, o_j = x_j - x_{n-1-j} (j < h = n/2) and
-  // e_h = x_h for odd n, the halves ye = E e (ceil(n/2) rows, row-major,
+  // Even-odd form, with e_j = x_j + x_{n-1-j}, o_j = x_j - x_{n-1-j} (j < h =
+  // n/2) and e_h = x_h for odd n.  Centrosymmetric matrices (A[n-1-i][n-1-j]
+  // = A[i][j]: M, K_d, S, S^T, the scaled M): ye = E e (ceil(n/2) rows,
   // stride ceil(n/2)) and yo = O o (h rows, stride h, stored after E) give
-  // y_i = ye_i + yo_i and y_{n-1-i} = ye_i - yo_i (i < h), y_h = ye_h
+  // y_i = ye_i + yo_i, y_{n-1-i} = ye_i - yo_i (i < h), y_h = ye_h.
+  // Anti-centrosymmetric matrices (A[n-1-i][n-1-j] = -A[i][j]: the collocation
+  // derivative and its transpose): yd = E' e (h rows, stride ceil(n/2)) and
+  // ys = O' o (ceil(n/2) rows, stride h, stored after E') give
+  // y_i = ys_i + yd_i, y_{n-1-i} = ys_i - yd_i (i < h), y_h = ys_h.
   double eo[NMAT][kMat];
   float eoh[NMAT][kMat];
   float eol[NMAT][kMat];

@@ -123,30 +123,41 @@ void build_coeffs(int p, const double h[3], double amplitude, int coef, Operator
     c.T2[1][i] = D[i] * S[i];
     c.T2[2][i] = D[i] * D[i];
   }
-  // float pairs: hi = nearest float, lo = nearest float of the remainder
-  for (int m = 0; m < NMAT; ++m)
-    for (int i = 0; i < n1 * n1; ++i) {
-      const float hi = (float)c.mat[m][i];
-      c.fh[m][i] = hi;
-      c.fl[m][i] = (float)(c.mat[m][i] - (double)hi);
+  for (int i = 0; i < n1; ++i)
+    for (int j = 0; j < n1; ++j) {
+      c.mat[MAT_ST][i * n1 + j] = S[j * n1 + i];
+      c.mat[MAT_DCT][i * n1 + j] = Dc[j * n1 + i];
     }
-  // even-odd halves (used for the centrosymmetric mass and stiffness matrices)
+  // even-odd halves of every matrix (layouts in OperatorCoeffs); float
+  // pairs: hi = nearest float, lo = nearest float of the remainder
   const int hh = n1 / 2, ne = n1 - hh;
   for (int m = 0; m < NMAT; ++m) {
     const double* A = c.mat[m];
-    double* E = c.eo[m];
-    double* O = c.eo[m] + ne * ne;
-    for (int i = 0; i < ne; ++i)
-      for (int j = 0; j < ne; ++j) {
-        double v;
-        if (j < hh)
-          v = i < hh ? 0.5 * (A[i * n1 + j] + A[i * n1 + (n1 - 1 - j)]) : A[i * n1 + j];
-        else
-          v = A[i * n1 + j];  // middle column (odd n)
-        E[i * ne + j] = v;
-      }
-    for (int i = 0; i < hh; ++i)
-      for (int j = 0; j < hh; ++j) O[i * hh + j] = 0.5 * (A[i * n1 + j] - A[i * n1 + (n1 - 1 - j)]);
+    const bool anti = m == MAT_DC || m == MAT_DCT;
+    if (!anti) {
+      double* E = c.eo[m];
+      double* O = c.eo[m] + ne * ne;
+      for (int i = 0; i < ne; ++i)
+        for (int j = 0; j < ne; ++j) {
+          double v;
+          if (j < hh)
+            v = i < hh ? 0.5 * (A[i * n1 + j] + A[i * n1 + (n1 - 1 - j)]) : A[i * n1 + j];
+          else
+            v = A[i * n1 + j];  // middle column (odd n)
+          E[i * ne + j] = v;
+        }
+      for (int i = 0; i < hh; ++i)
+        for (int j = 0; j < hh; ++j) O[i * hh + j] = 0.5 * (A[i * n1 + j] - A[i * n1 + (n1 - 1 - j)]);
+    } else {
+      double* E = c.eo[m];            // hh x ne, multiplies e
+      double* O = c.eo[m] + hh * ne;  // ne x hh, multiplies o
+      for (int i = 0; i < hh; ++i)
+        for (int j = 0; j < ne; ++j)
+          E[i * ne + j] = j < hh ? 0.5 * (A[i * n1 + j] + A[i * n1 + (n1 - 1 - j)]) : A[i * n1 + j];
+      for (int i = 0; i < ne; ++i)
+        for (int j = 0; j < hh; ++j)
+          O[i * hh + j] = i < hh ? 0.5 * (A[i * n1 + j] - A[i * n1 + (n1 - 1 - j)]) : A[i * n1 + j];
+    }
     for (int i = 0; i < ne * ne + hh * hh; ++i) {
       const float hi = (float)c.eo[m][i];
       c.eoh[m][i] = hi;

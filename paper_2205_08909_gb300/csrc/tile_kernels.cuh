@@ -59,69 +59,6 @@ __host__ __device__ inline int deformed_batch_cells(int P, int elem_bytes, const
 // ------------------------------------------------------------------------------------
 // 1D contractions on a pencil of N1 = P+1 values held in registers
 // ------------------------------------------------------------------------------------
-template <int N1, bool TRANS>
-__device__ __forceinline__ int midx(int i, int j) {
-  return TRANS ? j * N1 + i : i * N1 + j;
-}
-
-// y = A x (or A^T x) with the 1D matrix m of the coefficient block
-template <int PREC, int N1, bool TRANS>
-__device__ __forceinline__ void mv(const OperatorCoeffs& c, int m, const typename Num<PREC>::T (&x)[N1],
-                                   typename Num<PREC>::T (&y)[N1]) {
-#pragma unroll
-  for (int i = 0; i < N1; ++i) {
-    if constexpr (PREC == PREC_DD) {
-      dd_acc a;
-      acc_set(a, dd{c.fh[m][midx<N1, TRANS>(i, 0)], c.fl[m][midx<N1, TRANS>(i, 0)]}, x[0]);
-#pragma unroll
-      for (int j = 1; j < N1; ++j) acc_madd(a, dd{c.fh[m][midx<N1, TRANS>(i, j)], c.fl[m][midx<N1, TRANS>(i, j)]}, x[j]);
-      y[i] = acc_get(a);
-    } else if constexpr (PREC == PREC_F64) {
-      double s = 0.0;
-#pragma unroll
-      for (int j = 0; j < N1; ++j) s = fma(c.mat[m][midx<N1, TRANS>(i, j)], x[j], s);
-      y[i] = s;
-    } else {
-      float s = 0.f;
-#pragma unroll
-      for (int j = 0; j < N1; ++j) s = fmaf(c.fh[m][midx<N1, TRANS>(i, j)], x[j], s);
-      y[i] = s;
-    }
-  }
-}
-
-// y = A x + B z
-template <int PREC, int N1>
-__device__ __forceinline__ void mv2(const OperatorCoeffs& c, int ma, const typename Num<PREC>::T (&x)[N1], int mb,
-                                    const typename Num<PREC>::T (&z)[N1], typename Num<PREC>::T (&y)[N1]) {
-#pragma unroll
-  for (int i = 0; i < N1; ++i) {
-    if constexpr (PREC == PREC_DD) {
-      dd_acc a;
-      acc_set(a, dd{c.fh[ma][i * N1], c.fl[ma][i * N1]}, x[0]);
-#pragma unroll
-      for (int j = 1; j < N1; ++j) acc_madd(a, dd{c.fh[ma][i * N1 + j], c.fl[ma][i * N1 + j]}, x[j]);
-#pragma unroll
-      for (int j = 0; j < N1; ++j) acc_madd(a, dd{c.fh[mb][i * N1 + j], c.fl[mb][i * N1 + j]}, z[j]);
-      y[i] = acc_get(a);
-    } else if constexpr (PREC == PREC_F64) {
-      double s = 0.0;
-#pragma unroll
-      for (int j = 0; j < N1; ++j) s = fma(c.mat[ma][i * N1 + j], x[j], s);
-#pragma unroll
-      for (int j = 0; j < N1; ++j) s = fma(c.mat[mb][i * N1 + j], z[j], s);
-      y[i] = s;
-    } else {
-      float s = 0.f;
-#pragma unroll
-      for (int j = 0; j < N1; ++j) s = fmaf(c.fh[ma][i * N1 + j], x[j], s);
-#pragma unroll
-      for (int j = 0; j < N1; ++j) s = fmaf(c.fh[mb][i * N1 + j], z[j], s);
-      y[i] = s;
-    }
-  }
-}
-
 // ------------------------------------------------------------------------------------
 // Even-odd form of the centrosymmetric 1D matrices (M, K_d, the volume-scaled
 // M): y = A x from the halves E (ceil(n/2)^2) and O (floor(n/2)^2) of the
@@ -205,6 +142,43 @@ __device__ __forceinline__ void eo_apply(const OperatorCoeffs& c, int m1, int m2
   }
 }
 
+// y = A x for an anti-centrosymmetric A (the collocation derivative and its transpose)
+template <int PREC, int N1>
+__device__ __forceinline__ void eo_apply_anti(const OperatorCoeffs& c, int m, const typename Num<PREC>::T (&x)[N1],
+                                              typename Num<PREC>::T (&y)[N1]) {
+  using T = typename Num<PREC>::T;
+  constexpr int H = N1 / 2, NE = N1 - H;
+  T e[NE], o[H];
+#pragma unroll
+  for (int j = 0; j < H; ++j) {
+    e[j] = t_add<PREC>(x[j], x[N1 - 1 - j]);
+    o[j] = t_sub<PREC>(x[j], x[N1 - 1 - j]);
+  }
+  if constexpr (NE > H) e[H] = x[H];
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    const T yd = eo_dot<PREC, NE, false>(c, m, i * NE, e, m, 0, e);
+    const T ys = eo_dot<PREC, H, false>(c, m, H * NE + i * H, o, m, 0, o);
+    y[i] = t_add<PREC>(ys, yd);
+    y[N1 - 1 - i] = t_sub<PREC>(ys, yd);
+  }
+  if constexpr (NE > H) y[H] = eo_dot<PREC, H, false>(c, m, H * NE + H * H, o, m, 0, o);
+}
+
+// y = A x (TRANS: A^T x) with the interpolation matrix (M = MAT_S) or the
+// collocation derivative (M = MAT_DC), in even-odd form
+template <int PREC, int N1, bool TRANS, int M>
+__device__ __forceinline__ void mv(const OperatorCoeffs& c, const typename Num<PREC>::T (&x)[N1],
+                                   typename Num<PREC>::T (&y)[N1]) {
+  static_assert(M == MAT_S || M == MAT_DC, "interpolation or collocation derivative");
+  if constexpr (M == MAT_S) {
+    constexpr int ME = TRANS ? MAT_ST : MAT_S;
+    eo_apply<PREC, N1, true, false, false>(c, ME, ME, ME, x, x, y, y);
+  } else {
+    eo_apply_anti<PREC, N1>(c, TRANS ? MAT_DCT : MAT_DC, x, y);
+  }
+}
+
 // a0 b0 + a1 b1 + a2 b2
 template <int PREC>
 __device__ __forceinline__ typename Num<PREC>::T dot3(typename Num<PREC>::T a0, typename Num<PREC>::T b0,
@@ -233,11 +207,11 @@ __device__ __forceinline__ int pencil_idx(int dir, int e1, int e2, int s) {
   return dir == 0 ? cidx<N1>(s, e1, e2) : (dir == 1 ? cidx<N1>(e1, s, e2) : cidx<N1>(e1, e2, s));
 }
 
-// In-place application of the 1D matrix m (or its transpose) along `dir` to
+// In-place application of the 1D matrix M (or its transpose) along `dir` to
 // the cell arrays arr + ci*stride, ci < nc.  Ends with a barrier.
-template <int PREC, int P, bool TRANS>
+template <int PREC, int P, bool TRANS, int M>
 __device__ __forceinline__ void sweep_inplace(typename Num<PREC>::T* arr, int stride, int nc, int dir,
-                                              const OperatorCoeffs& c, int m) {
+                                              const OperatorCoeffs& c) {
   using T = typename Num<PREC>::T;
   constexpr int N1 = P + 1, N2 = N1 * N1;
   for (int t = threadIdx.x; t < nc * N2; t += kThreads) {
@@ -246,7 +220,7 @@ __device__ __forceinline__ void sweep_inplace(typename Num<PREC>::T* arr, int st
     T x[N1], y[N1];
 #pragma unroll
     for (int s = 0; s < N1; ++s) x[s] = a[pencil_idx<N1>(dir, e1, e2, s)];
-    mv<PREC, N1, TRANS>(c, m, x, y);
+    mv<PREC, N1, TRANS, M>(c, x, y);
 #pragma unroll
     for (int s = 0; s < N1; ++s) a[pencil_idx<N1>(dir, e1, e2, s)] = y[s];
   }
@@ -254,9 +228,9 @@ __device__ __forceinline__ void sweep_inplace(typename Num<PREC>::T* arr, int st
 }
 
 // out (+)= A^(T) in along `dir`, separate arrays.  Ends with a barrier.
-template <int PREC, int P, bool TRANS, bool ACCUM>
+template <int PREC, int P, bool TRANS, bool ACCUM, int M>
 __device__ __forceinline__ void sweep_copy(const typename Num<PREC>::T* in, typename Num<PREC>::T* out, int stride,
-                                           int nc, int dir, const OperatorCoeffs& c, int m) {
+                                           int nc, int dir, const OperatorCoeffs& c) {
   using T = typename Num<PREC>::T;
   constexpr int N1 = P + 1, N2 = N1 * N1;
   for (int t = threadIdx.x; t < nc * N2; t += kThreads) {
@@ -266,7 +240,7 @@ __device__ __forceinline__ void sweep_copy(const typename Num<PREC>::T* in, type
     T x[N1], y[N1];
 #pragma unroll
     for (int s = 0; s < N1; ++s) x[s] = a[pencil_idx<N1>(dir, e1, e2, s)];
-    mv<PREC, N1, TRANS>(c, m, x, y);
+    mv<PREC, N1, TRANS, M>(c, x, y);
 #pragma unroll
     for (int s = 0; s < N1; ++s) {
       const int id = pencil_idx<N1>(dir, e1, e2, s);
@@ -419,9 +393,9 @@ __device__ void cell_op_deformed(const OperatorCoeffs& c, const typename Num<PRE
     S[ci * stride + e] = U[cc.org[ci] + a + bx * (b + by * cz)];
   }
   __syncthreads();
-  sweep_inplace<PREC, P, false>(S, stride, nc, 0, c, MAT_S);
-  sweep_inplace<PREC, P, false>(S, stride, nc, 1, c, MAT_S);
-  sweep_inplace<PREC, P, false>(S, stride, nc, 2, c, MAT_S);
+  sweep_inplace<PREC, P, false, MAT_S>(S, stride, nc, 0, c);
+  sweep_inplace<PREC, P, false, MAT_S>(S, stride, nc, 1, c);
+  sweep_inplace<PREC, P, false, MAT_S>(S, stride, nc, 2, c);
   if constexpr (GEOM == GEOM_DEFORMED) {
     if (op_kind == OP_MASS) {
       // mass operator: values at the Gauss points times JxW a, transposed interpolation
@@ -431,9 +405,9 @@ __device__ void cell_op_deformed(const OperatorCoeffs& c, const typename Num<PRE
         s[q] = t_mul<PREC>(geo[(int64_t)cc.cell[ci] * 10 * N3 + 9 * N3 + q], s[q]);
       }
       __syncthreads();
-      sweep_inplace<PREC, P, true>(S, stride, nc, 0, c, MAT_S);
-      sweep_inplace<PREC, P, true>(S, stride, nc, 1, c, MAT_S);
-      sweep_inplace<PREC, P, true>(S, stride, nc, 2, c, MAT_S);
+      sweep_inplace<PREC, P, true, MAT_S>(S, stride, nc, 0, c);
+      sweep_inplace<PREC, P, true, MAT_S>(S, stride, nc, 1, c);
+      sweep_inplace<PREC, P, true, MAT_S>(S, stride, nc, 2, c);
       return;
     }
   }
@@ -447,7 +421,7 @@ __device__ void cell_op_deformed(const OperatorCoeffs& c, const typename Num<PRE
     T x[N1], y[N1];
 #pragma unroll
     for (int s = 0; s < N1; ++s) x[s] = a[pencil_idx<N1>(dir, e1, e2, s)];
-    mv<PREC, N1, false>(c, MAT_DC, x, y);
+    mv<PREC, N1, false, MAT_DC>(c, x, y);
 #pragma unroll
     for (int s = 0; s < N1; ++s) o[pencil_idx<N1>(dir, e1, e2, s)] = y[s];
   }
@@ -481,12 +455,12 @@ __device__ void cell_op_deformed(const OperatorCoeffs& c, const typename Num<PRE
   }
   __syncthreads();
   // transposed derivative sweeps, summed into s0
-  sweep_copy<PREC, P, true, false>(S + N3, S, stride, nc, 0, c, MAT_DC);
-  sweep_copy<PREC, P, true, true>(S + 2 * N3, S, stride, nc, 1, c, MAT_DC);
-  sweep_copy<PREC, P, true, true>(S + 3 * N3, S, stride, nc, 2, c, MAT_DC);
-  sweep_inplace<PREC, P, true>(S, stride, nc, 0, c, MAT_S);
-  sweep_inplace<PREC, P, true>(S, stride, nc, 1, c, MAT_S);
-  sweep_inplace<PREC, P, true>(S, stride, nc, 2, c, MAT_S);
+  sweep_copy<PREC, P, true, false, MAT_DC>(S + N3, S, stride, nc, 0, c);
+  sweep_copy<PREC, P, true, true, MAT_DC>(S + 2 * N3, S, stride, nc, 1, c);
+  sweep_copy<PREC, P, true, true, MAT_DC>(S + 3 * N3, S, stride, nc, 2, c);
+  sweep_inplace<PREC, P, true, MAT_S>(S, stride, nc, 0, c);
+  sweep_inplace<PREC, P, true, MAT_S>(S, stride, nc, 1, c);
+  sweep_inplace<PREC, P, true, MAT_S>(S, stride, nc, 2, c);
 }
 
 // Sum of the cell results of a batch of cells [c0, c0 + nb) (tile-local
@@ -564,9 +538,9 @@ __device__ void cell_rhs(const OperatorCoeffs& c, double* V, double* S, int bx, 
     S[ci * stride + q] = c.w[qa] * c.w[qb] * c.w[qc] * detJ * f;
   }
   __syncthreads();
-  sweep_inplace<PREC_F64, P, true>(S, stride, nc, 0, c, MAT_S);
-  sweep_inplace<PREC_F64, P, true>(S, stride, nc, 1, c, MAT_S);
-  sweep_inplace<PREC_F64, P, true>(S, stride, nc, 2, c, MAT_S);
+  sweep_inplace<PREC_F64, P, true, MAT_S>(S, stride, nc, 0, c);
+  sweep_inplace<PREC_F64, P, true, MAT_S>(S, stride, nc, 1, c);
+  sweep_inplace<PREC_F64, P, true, MAT_S>(S, stride, nc, 2, c);
   for (int t = threadIdx.x; t < nc * N3; t += kThreads) {
     const int ci = t / N3, e = t - ci * N3, a = e % N1, b = (e / N1) % N1, cz = e / N2;
     V[cc.org[ci] + a + bx * (b + by * cz)] += S[ci * stride + e];
