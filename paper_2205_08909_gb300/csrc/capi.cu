@@ -73,6 +73,8 @@ struct mfcg_problem {
   int64_t fam[3] = {0, 0, 0};
   TailDiv tdiv{};
   int tail_ctas = 1;
+  int ahead_cg = 0;  // prefetch distance (tiles) of the fused CG and operator passes
+  int ahead_op = 0;
   int graph_iters = 16;
   cudaGraphExec_t graph_fused = nullptr;
   cudaGraphExec_t graph_unfused = nullptr;
@@ -154,6 +156,7 @@ int run_pass(mfcg_problem* P, int mode, const double* src, double* dst) {
   const int prec = mode == MODE_OPERATOR ? P->op_prec : PREC_F64;
   TileArgs a = base_args(P, prec, mode == MODE_OPERATOR ? P->geo_op : P->geo);
   if (mode != MODE_OPERATOR) a.ncomp = 1;  // diagonal and right-hand side of the scalar operator
+  a.prefetch_ahead = mode == MODE_OPERATOR ? P->ahead_op : 0;
   a.in0 = src;
   a.out0 = dst;
   CK(launch_tile(P->degree, mode, a, P->c, P->exec));
@@ -166,6 +169,7 @@ int run_pass(mfcg_problem* P, int mode, const double* src, double* dst) {
 int enqueue_fused_iteration(mfcg_problem* P, int odd, cudaEvent_t t0, cudaEvent_t t1) {
   const int o = odd ? 0 : 1, n = odd ? 1 : 0;
   TileArgs a = base_args(P, P->cg_prec, P->geo_cg);
+  a.prefetch_ahead = P->ahead_cg;
   a.in0 = P->r[o];
   a.in1 = P->v[o];
   a.in2 = P->p[o];
@@ -200,6 +204,7 @@ int enqueue_unfused_iteration(mfcg_problem* P, cudaEvent_t t0, cudaEvent_t t1) {
   if (t0) CK(cudaEventRecord(t0, P->exec));
   // v = A p
   TileArgs a = base_args(P, P->op_prec, P->geo_op);
+  a.prefetch_ahead = P->ahead_op;
   a.in0 = u.p;
   a.out0 = u.v;
   CK(launch_tile(P->degree, MODE_OPERATOR, a, P->c, P->exec));
@@ -220,6 +225,7 @@ int enqueue_semi_iteration(mfcg_problem* P, cudaEvent_t t0, cudaEvent_t t1) {
   const int64_t n = P->nv();
   CK(launch_semi_pre(n, P->state, P->x, P->ur, P->up, P->uv, P->diag_inv, P->exec));
   TileArgs a = base_args(P, P->op_prec, P->geo_op);
+  a.prefetch_ahead = P->ahead_op;
   a.in0 = P->up;
   a.out0 = P->uv;
   if (t0) CK(cudaEventRecord(t0, P->exec));
@@ -915,6 +921,13 @@ int mfcg_setup(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, con
     if (smem + static_smem > (size_t)max_smem) return fail(MFCG_INVALID_ARG);
     if (prepare_tile(degree, P->geom_kind, pr, smem) != cudaSuccess) return fail(MFCG_CUDA_ERROR);
   }
+  // prefetch distance of the operator passes: the CTAs resident in one wave
+  // (the fused CG kernel has no look-ahead prefetch)
+  int n_sm = 0;
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, P->device);
+  P->ahead_cg = 0;
+  P->ahead_op = n_sm * tile_occupancy(degree, MODE_OPERATOR, P->geom_kind, P->op_prec, P->ncomp,
+                                      tile_smem_bytes(degree, P->geom_kind, P->op_prec, g, MODE_OPERATOR));
   P->tail_nodes = P->fam[0] + P->fam[1] + P->fam[2];
   P->tail_ctas = (int)std::min<int64_t>(std::max<int64_t>((P->tail_nodes + 2 * kThreads - 1) / (2 * kThreads), 1), 152 * 32);
 

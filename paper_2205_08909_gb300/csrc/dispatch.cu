@@ -7,7 +7,8 @@ namespace mfcg {
 #define MFCG_DECLARE_DEG(P)                                                                         \
   cudaError_t launch_tile_deg##P(int mode, const TileArgs& a, const OperatorCoeffs& c, cudaStream_t s); \
   cudaError_t launch_tail_deg##P(int mode, const TileArgs& a, cudaStream_t s);                      \
-  cudaError_t prepare_tile_deg##P(int geom, int prec, size_t smem);
+  cudaError_t prepare_tile_deg##P(int geom, int prec, size_t smem);                                 \
+  int tile_occupancy_deg##P(int mode, int geom, int prec, int ncomp, size_t smem);
 MFCG_DECLARE_DEG(1)
 MFCG_DECLARE_DEG(2)
 MFCG_DECLARE_DEG(3)
@@ -60,8 +61,22 @@ cudaError_t prepare_tile(int degree, int geom, int prec, size_t smem) {
   }
 }
 
-size_t tile_smem_bytes(int degree, int geom, int prec, const TileGeom& g) {
-  return tile_smem_elems(degree, geom, prec_bytes(prec), g) * prec_bytes(prec);
+int tile_occupancy(int degree, int mode, int geom, int prec, int ncomp, size_t smem) {
+  switch (degree) {
+    case 1: return tile_occupancy_deg1(mode, geom, prec, ncomp, smem);
+    case 2: return tile_occupancy_deg2(mode, geom, prec, ncomp, smem);
+    case 3: return tile_occupancy_deg3(mode, geom, prec, ncomp, smem);
+    case 4: return tile_occupancy_deg4(mode, geom, prec, ncomp, smem);
+    case 5: return tile_occupancy_deg5(mode, geom, prec, ncomp, smem);
+    case 6: return tile_occupancy_deg6(mode, geom, prec, ncomp, smem);
+    case 7: return tile_occupancy_deg7(mode, geom, prec, ncomp, smem);
+    case 8: return tile_occupancy_deg8(mode, geom, prec, ncomp, smem);
+    default: return 0;
+  }
+}
+
+size_t tile_smem_bytes(int degree, int geom, int prec, const TileGeom& g, int mode) {
+  return tile_smem_elems(degree, geom, prec_bytes(prec), g, mode) * prec_bytes(prec);
 }
 
 }  // namespace mfcg

@@ -383,13 +383,19 @@ struct TileArgs {
   int64_t shell_comp_stride;  // shell elements per component (= g.n_tiles * g.face_stride)
   int op_kind;           // OpKind
   int tail_ctas;
+  int prefetch_ahead;    // operator passes: during its cell phase, a CTA prefetches into L2 the
+                         // owned input block (and geometry) of tile blockIdx + prefetch_ahead
+                         // (the CTAs resident in one wave); 0 = off
 };
 
 // launchers (one set per degree, see tile_kernels.cuh)
 cudaError_t launch_tile(int degree, int mode, const TileArgs& a, const OperatorCoeffs& c, cudaStream_t s);
 cudaError_t launch_tail(int degree, int mode, const TileArgs& a, cudaStream_t s);
-size_t tile_smem_bytes(int degree, int geom, int prec, const TileGeom& g);
+// dynamic shared memory of a tile kernel launch of `mode` (-1: the largest over the modes)
+size_t tile_smem_bytes(int degree, int geom, int prec, const TileGeom& g, int mode = -1);
 cudaError_t prepare_tile(int degree, int geom, int prec, size_t smem);
+// resident CTAs per SM of the fused CG tile kernel (0 on error)
+int tile_occupancy(int degree, int mode, int geom, int prec, int ncomp, size_t smem);
 
 // BLAS-1 / reduction / utility kernels (cg_kernels.cu)
 cudaError_t launch_fill(double* v, double value, int64_t n, cudaStream_t s);

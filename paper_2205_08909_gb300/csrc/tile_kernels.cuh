@@ -207,8 +207,19 @@ __device__ __forceinline__ int pencil_idx(int dir, int e1, int e2, int s) {
   return dir == 0 ? cidx<N1>(s, e1, e2) : (dir == 1 ? cidx<N1>(e1, s, e2) : cidx<N1>(e1, e2, s));
 }
 
+// first element and stride of the pencil along `dir` with transverse indices (e1, e2)
+template <int N1>
+__device__ __forceinline__ void pencil_base_step(int dir, int e1, int e2, int& base, int& step) {
+  constexpr int N2 = N1 * N1;
+  base = dir == 0 ? N1 * (e1 + N1 * e2) : (dir == 1 ? e1 + N2 * e2 : e1 + N1 * e2);
+  step = dir == 0 ? 1 : (dir == 1 ? N1 : N2);
+}
+
 // In-place application of the 1D matrix M (or its transpose) along `dir` to
-// the cell arrays arr + ci*stride, ci < nc.  Ends with a barrier.
+// the cell arrays arr + ci*stride, ci < nc.  Ends with a barrier.  Callers
+// loop over dir without unrolling: one copy of the (long, fully unrolled)
+// product serves the three directions, which keeps the deformed kernels
+// within the instruction cache.
 template <int PREC, int P, bool TRANS, int M>
 __device__ __forceinline__ void sweep_inplace(typename Num<PREC>::T* arr, int stride, int nc, int dir,
                                               const OperatorCoeffs& c) {
@@ -216,36 +227,37 @@ __device__ __forceinline__ void sweep_inplace(typename Num<PREC>::T* arr, int st
   constexpr int N1 = P + 1, N2 = N1 * N1;
   for (int t = threadIdx.x; t < nc * N2; t += kThreads) {
     const int ci = t / N2, e = t - ci * N2, e1 = e % N1, e2 = e / N1;
-    T* a = arr + ci * stride;
+    int base, step;
+    pencil_base_step<N1>(dir, e1, e2, base, step);
+    T* a = arr + ci * stride + base;
     T x[N1], y[N1];
 #pragma unroll
-    for (int s = 0; s < N1; ++s) x[s] = a[pencil_idx<N1>(dir, e1, e2, s)];
+    for (int s = 0; s < N1; ++s) x[s] = a[s * step];
     mv<PREC, N1, TRANS, M>(c, x, y);
 #pragma unroll
-    for (int s = 0; s < N1; ++s) a[pencil_idx<N1>(dir, e1, e2, s)] = y[s];
+    for (int s = 0; s < N1; ++s) a[s * step] = y[s];
   }
   __syncthreads();
 }
 
-// out (+)= A^(T) in along `dir`, separate arrays.  Ends with a barrier.
-template <int PREC, int P, bool TRANS, bool ACCUM, int M>
+// out = A^(T) in (accum: out += ...) along `dir`, separate arrays.  Ends with a barrier.
+template <int PREC, int P, bool TRANS, int M>
 __device__ __forceinline__ void sweep_copy(const typename Num<PREC>::T* in, typename Num<PREC>::T* out, int stride,
-                                           int nc, int dir, const OperatorCoeffs& c) {
+                                           int nc, int dir, bool accum, const OperatorCoeffs& c) {
   using T = typename Num<PREC>::T;
   constexpr int N1 = P + 1, N2 = N1 * N1;
   for (int t = threadIdx.x; t < nc * N2; t += kThreads) {
     const int ci = t / N2, e = t - ci * N2, e1 = e % N1, e2 = e / N1;
-    const T* a = in + ci * stride;
-    T* o = out + ci * stride;
+    int base, step;
+    pencil_base_step<N1>(dir, e1, e2, base, step);
+    const T* a = in + ci * stride + base;
+    T* o = out + ci * stride + base;
     T x[N1], y[N1];
 #pragma unroll
-    for (int s = 0; s < N1; ++s) x[s] = a[pencil_idx<N1>(dir, e1, e2, s)];
+    for (int s = 0; s < N1; ++s) x[s] = a[s * step];
     mv<PREC, N1, TRANS, M>(c, x, y);
 #pragma unroll
-    for (int s = 0; s < N1; ++s) {
-      const int id = pencil_idx<N1>(dir, e1, e2, s);
-      o[id] = ACCUM ? t_add<PREC>(o[id], y[s]) : y[s];
-    }
+    for (int s = 0; s < N1; ++s) o[s * step] = accum ? t_add<PREC>(o[s * step], y[s]) : y[s];
   }
   __syncthreads();
 }
@@ -393,9 +405,8 @@ __device__ void cell_op_deformed(const OperatorCoeffs& c, const typename Num<PRE
     S[ci * stride + e] = U[cc.org[ci] + a + bx * (b + by * cz)];
   }
   __syncthreads();
-  sweep_inplace<PREC, P, false, MAT_S>(S, stride, nc, 0, c);
-  sweep_inplace<PREC, P, false, MAT_S>(S, stride, nc, 1, c);
-  sweep_inplace<PREC, P, false, MAT_S>(S, stride, nc, 2, c);
+#pragma unroll 1
+  for (int dir = 0; dir < 3; ++dir) sweep_inplace<PREC, P, false, MAT_S>(S, stride, nc, dir, c);
   if constexpr (GEOM == GEOM_DEFORMED) {
     if (op_kind == OP_MASS) {
       // mass operator: values at the Gauss points times JxW a, transposed interpolation
@@ -405,9 +416,8 @@ __device__ void cell_op_deformed(const OperatorCoeffs& c, const typename Num<PRE
         s[q] = t_mul<PREC>(geo[(int64_t)cc.cell[ci] * 10 * N3 + 9 * N3 + q], s[q]);
       }
       __syncthreads();
-      sweep_inplace<PREC, P, true, MAT_S>(S, stride, nc, 0, c);
-      sweep_inplace<PREC, P, true, MAT_S>(S, stride, nc, 1, c);
-      sweep_inplace<PREC, P, true, MAT_S>(S, stride, nc, 2, c);
+#pragma unroll 1
+      for (int dir = 0; dir < 3; ++dir) sweep_inplace<PREC, P, true, MAT_S>(S, stride, nc, dir, c);
       return;
     }
   }
@@ -416,14 +426,16 @@ __device__ void cell_op_deformed(const OperatorCoeffs& c, const typename Num<PRE
     const int dir = t / (nc * N2);
     const int tt = t - dir * nc * N2;
     const int ci = tt / N2, e = tt - ci * N2, e1 = e % N1, e2 = e / N1;
-    const T* a = S + ci * stride;
-    T* o = S + ci * stride + (1 + dir) * N3;
+    int base, step;
+    pencil_base_step<N1>(dir, e1, e2, base, step);
+    const T* a = S + ci * stride + base;
+    T* o = S + ci * stride + (1 + dir) * N3 + base;
     T x[N1], y[N1];
 #pragma unroll
-    for (int s = 0; s < N1; ++s) x[s] = a[pencil_idx<N1>(dir, e1, e2, s)];
+    for (int s = 0; s < N1; ++s) x[s] = a[s * step];
     mv<PREC, N1, false, MAT_DC>(c, x, y);
 #pragma unroll
-    for (int s = 0; s < N1; ++s) o[pencil_idx<N1>(dir, e1, e2, s)] = y[s];
+    for (int s = 0; s < N1; ++s) o[s * step] = y[s];
   }
   __syncthreads();
   // metric at each point: flux = J^{-1} (JxW a) J^{-T} grad_ref
@@ -455,12 +467,10 @@ __device__ void cell_op_deformed(const OperatorCoeffs& c, const typename Num<PRE
   }
   __syncthreads();
   // transposed derivative sweeps, summed into s0
-  sweep_copy<PREC, P, true, false, MAT_DC>(S + N3, S, stride, nc, 0, c);
-  sweep_copy<PREC, P, true, true, MAT_DC>(S + 2 * N3, S, stride, nc, 1, c);
-  sweep_copy<PREC, P, true, true, MAT_DC>(S + 3 * N3, S, stride, nc, 2, c);
-  sweep_inplace<PREC, P, true, MAT_S>(S, stride, nc, 0, c);
-  sweep_inplace<PREC, P, true, MAT_S>(S, stride, nc, 1, c);
-  sweep_inplace<PREC, P, true, MAT_S>(S, stride, nc, 2, c);
+#pragma unroll 1
+  for (int dir = 0; dir < 3; ++dir) sweep_copy<PREC, P, true, MAT_DC>(S + (1 + dir) * N3, S, stride, nc, dir, dir > 0, c);
+#pragma unroll 1
+  for (int dir = 0; dir < 3; ++dir) sweep_inplace<PREC, P, true, MAT_S>(S, stride, nc, dir, c);
 }
 
 // Sum of the cell results of a batch of cells [c0, c0 + nb) (tile-local
@@ -538,9 +548,8 @@ __device__ void cell_rhs(const OperatorCoeffs& c, double* V, double* S, int bx, 
     S[ci * stride + q] = c.w[qa] * c.w[qb] * c.w[qc] * detJ * f;
   }
   __syncthreads();
-  sweep_inplace<PREC_F64, P, true, MAT_S>(S, stride, nc, 0, c);
-  sweep_inplace<PREC_F64, P, true, MAT_S>(S, stride, nc, 1, c);
-  sweep_inplace<PREC_F64, P, true, MAT_S>(S, stride, nc, 2, c);
+#pragma unroll 1
+  for (int dir = 0; dir < 3; ++dir) sweep_inplace<PREC_F64, P, true, MAT_S>(S, stride, nc, dir, c);
   for (int t = threadIdx.x; t < nc * N3; t += kThreads) {
     const int ci = t / N3, e = t - ci * N3, a = e % N1, b = (e / N1) % N1, cz = e / N2;
     V[cc.org[ci] + a + bx * (b + by * cz)] += S[ci * stride + e];
@@ -1032,6 +1041,48 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a_all, co
       if (kZeroV && ok[b]) V[sidx[b]] = t_zero<PREC>();
   }
 
+  // Operator passes: L2 prefetch for the tile one wave of resident CTAs ahead
+  // -- its owned input block (contiguous) and, on deformed meshes, its
+  // geometry -- so that its gather reads from L2 (every prefetched line lies
+  // inside the prefetched block).  The fused CG kernel, which reads four
+  // vectors per node, measured 3-5% slower with it and does without.
+  if constexpr (MODE == MODE_OPERATOR) {
+    const int64_t ahead = tile + a_all.prefetch_ahead;
+    if (a_all.prefetch_ahead > 0 && ahead < g.n_tiles) {
+      const int px = (int)(ahead % g.nt[0]), py = (int)((ahead / g.nt[0]) % g.nt[1]);
+      const int pz = (int)(ahead / ((int64_t)g.nt[0] * g.nt[1]));
+      const int64_t pbase = tile_base(g, px, py, pz);
+      const int64_t pown = (int64_t)owned_count(g, 0, px) * owned_count(g, 1, py) * owned_count(g, 2, pz);
+      auto prefetch_block = [&](const void* vec, int64_t first, int64_t bytes) {
+        const char* p0 = static_cast<const char*>(vec) + first;
+        for (int64_t l = threadIdx.x; l * 128 < bytes; l += kThreads)
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(__cvta_generic_to_global(p0 + l * 128)));
+      };
+      constexpr int64_t ve = MODE == MODE_CG ? (int64_t)sizeof(T) : (int64_t)sizeof(double);
+      prefetch_block(c_in0, pbase * ve, pown * ve);
+      if constexpr (MODE == MODE_CG) {
+        prefetch_block(c_in1, pbase * ve, pown * ve);
+        prefetch_block(c_in2, pbase * ve, pown * ve);
+        if (comp == 0) prefetch_block(a.diag_inv, pbase * ve, pown * ve);
+        if (xupd) prefetch_block(c_x, pbase * ve, pown * ve);
+      }
+      if constexpr (GEOM != GEOM_AFFINE) {
+        if (comp == 0) {
+          constexpr int N3 = (P + 1) * (P + 1) * (P + 1);
+          const int64_t cell_bytes = (int64_t)geo_values(GEOM) * N3 * (int64_t)sizeof(T);
+          const int pcx = min(g.T[0], g.N[0] - px * g.T[0]), pcy = min(g.T[1], g.N[1] - py * g.T[1]);
+          const int pcz = min(g.T[2], g.N[2] - pz * g.T[2]);
+          // cells of one row of the tile are consecutive in the geometry array
+          for (int r = 0; r < pcy * pcz; ++r) {
+            const int cy = r % pcy, cz = r / pcy;
+            const int64_t cell0 = (int64_t)px * g.T[0] + g.N[0] * ((int64_t)py * g.T[1] + cy + (int64_t)g.N[1] * ((int64_t)pz * g.T[2] + cz));
+            prefetch_block(a.geo, cell0 * cell_bytes, pcx * cell_bytes);
+          }
+        }
+      }
+    }
+  }
+
   // ---------------- phase 2: cell integrals ----------------
   if constexpr (GEOM == GEOM_AFFINE && (MODE == MODE_CG || MODE == MODE_OPERATOR)) {
     __syncthreads();  // phase 1 finished with U
@@ -1376,6 +1427,17 @@ cudaError_t prepare_tile_p(int geom, int prec, size_t smem) {
     }
   }
   return cudaSuccess;
+}
+
+template <int P>
+int tile_occupancy_p(int mode, int geom, int prec, int ncomp, size_t smem) {
+  TileFn<P> fn = tile_fn<P>(mode, geom, prec, ncomp);
+  int blocks = 0;
+  if (!fn || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, kThreads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return blocks;
 }
 
 template <int P>

@@ -8,4 +8,7 @@ cudaError_t launch_tile_deg8(int mode, const TileArgs& a, const OperatorCoeffs& 
 }
 cudaError_t launch_tail_deg8(int mode, const TileArgs& a, cudaStream_t s) { return launch_tail_p<8>(mode, a, s); }
 cudaError_t prepare_tile_deg8(int geom, int prec, size_t smem) { return prepare_tile_p<8>(geom, prec, smem); }
+int tile_occupancy_deg8(int mode, int geom, int prec, int ncomp, size_t smem) {
+  return tile_occupancy_p<8>(mode, geom, prec, ncomp, smem);
+}
 }  // namespace mfcg
