@@ -249,6 +249,9 @@ typedef struct mfcg_batch mfcg_batch;
  *   count   in: 1..4096.
  *   meshes, degrees, geoms: host arrays of count entries, read during the call.
  *   out     out: new handle; release with mfcg_destroy_batch.
+ * Members with the identical definition (mesh, degree and geometry; the
+ * options are common) share the stored geometry and the Jacobi diagonal: a
+ * block of right-hand sides on one mesh holds one copy of the operator data.
  * Errors: those of mfcg_setup for any member (nothing is left allocated),
  * INVALID_ARG for a mode or precision a batch does not support. */
 int mfcg_setup_batch(int count, const mfcg_mesh* meshes, const int* degrees, const mfcg_geometry* geoms,

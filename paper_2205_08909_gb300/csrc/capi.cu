@@ -22,6 +22,10 @@
 #include "mfcg_internal.h"
 #include "precision.cuh"
 
+struct mfcg_problem;
+int setup_impl(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, const mfcg_options* opt,
+               void* cuda_stream, mfcg_problem** out, const mfcg_problem* share);
+
 namespace mfcg {
 void build_coeffs(int p, const double h[3], double amplitude, int coef, OperatorCoeffs& c);
 int vec_grid(int64_t n);
@@ -754,8 +758,15 @@ int mfcg_setup_batch(int count, const mfcg_mesh* meshes, const int* degrees, con
   if (B->graph_iters < 0 || (B->graph_iters & 1)) return fail(MFCG_INVALID_ARG);
   B->members.reserve(count);
   for (int i = 0; i < count; ++i) {
+    // a member identical to an earlier one shares its geometry and diagonal
+    const mfcg_problem* share = nullptr;
+    for (int j = 0; j < i && !share; ++j)
+      if (degrees[j] == degrees[i] && meshes[j].nx == meshes[i].nx && meshes[j].ny == meshes[i].ny &&
+          meshes[j].nz == meshes[i].nz && meshes[j].amplitude == meshes[i].amplitude &&
+          geoms[j].kind == geoms[i].kind && geoms[j].coefficient == geoms[i].coefficient)
+        share = B->members[j];
     mfcg_problem* P = nullptr;
-    const int st = mfcg_setup(&meshes[i], degrees[i], &geoms[i], &o, cuda_stream, &P);
+    const int st = setup_impl(&meshes[i], degrees[i], &geoms[i], &o, cuda_stream, &P, share);
     if (st != MFCG_OK) return fail(st);
     B->members.push_back(P);
   }
@@ -802,7 +813,7 @@ int mfcg_destroy_batch(mfcg_batch* B) {
   cudaSetDevice(B->device);
   if (B->exec) cudaStreamSynchronize(B->exec);
   if (B->graph) cudaGraphExecDestroy(B->graph);
-  for (mfcg_problem* P : B->members) mfcg_destroy(P);
+  for (auto it = B->members.rbegin(); it != B->members.rend(); ++it) mfcg_destroy(*it);  // sharers first
   for (cudaEvent_t e : B->ev_join)
     if (e) cudaEventDestroy(e);
   if (B->ev_in) cudaEventDestroy(B->ev_in);
@@ -849,6 +860,17 @@ int mfcg_destroy(mfcg_problem* P) {
 
 int mfcg_setup(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, const mfcg_options* opt,
                void* cuda_stream, mfcg_problem** out) {
+  return setup_impl(mesh, degree, geom, opt, cuda_stream, out, nullptr);
+}
+
+}  // extern "C"
+
+// Set-up of one problem.  With `share` (a problem of the identical definition:
+// mesh, degree, geometry and options) the stored geometry and the diagonal,
+// its inverse and its converted copy are taken from `share` instead of being
+// allocated and computed (batches of right-hand sides on one mesh).
+int setup_impl(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, const mfcg_options* opt,
+               void* cuda_stream, mfcg_problem** out, const mfcg_problem* share) {
   if (!mesh || !geom || !out) return MFCG_INVALID_ARG;
   *out = nullptr;
   if (degree < 1 || degree > kMaxDegree) return MFCG_UNSUPPORTED_DEGREE;
@@ -944,7 +966,7 @@ int mfcg_setup(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, con
       st = alloc_bytes(P, &P->v[i], n8);
     }
     if (st == MFCG_OK) st = alloc_bytes(P, &P->xs, n8);
-    if (st == MFCG_OK) st = alloc_bytes(P, &P->dinv_s, n8);
+    if (st == MFCG_OK && !share) st = alloc_bytes(P, &P->dinv_s, n8);
     if (st == MFCG_OK && o.precision == MFCG_PREC_FP32_INNER) st = alloc_bytes(P, &P->x, n8);
   } else {
     if (st == MFCG_OK) st = alloc_bytes(P, &P->x, n8);
@@ -954,14 +976,22 @@ int mfcg_setup(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, con
     if (st == MFCG_OK) st = alloc_bytes(P, &P->uv, n8);
   }
   if (st == MFCG_OK) st = alloc_bytes(P, &P->work, n8);
-  if (st == MFCG_OK) st = alloc_bytes(P, &P->diag, n8);
-  if (st == MFCG_OK) st = alloc_bytes(P, &P->diag_inv, n8);
+  if (st == MFCG_OK && !share) st = alloc_bytes(P, &P->diag, n8);
+  if (st == MFCG_OK && !share) st = alloc_bytes(P, &P->diag_inv, n8);
   if (st == MFCG_OK) st = alloc_bytes(P, &P->shell, P->ncomp * g.n_tiles * g.face_stride * 8);
   const int64_t nparts = std::max<int64_t>(g.n_tiles + P->tail_ctas, 152 * 8);
   if (st == MFCG_OK) st = alloc_bytes(P, &P->partial, nparts * 8 * 8);
   const int64_t ngeo =
       (int64_t)N[0] * N[1] * N[2] * geo_values(P->geom_kind) * (degree + 1) * (degree + 1) * (degree + 1);
-  if (st == MFCG_OK && P->geom_kind != GEOM_AFFINE) {
+  if (share) {
+    P->geo = share->geo;
+    P->geo_op = share->geo_op;
+    P->geo_cg = share->geo_cg;
+    P->diag = share->diag;
+    P->diag_inv = share->diag_inv;
+    P->dinv_s = share->dinv_s;
+  }
+  if (st == MFCG_OK && P->geom_kind != GEOM_AFFINE && !share) {
     st = alloc_bytes(P, &P->geo, ngeo * 8);
     if (st == MFCG_OK && P->op_prec != PREC_F64) st = alloc_bytes(P, &P->geo_op, ngeo * 8);
     if (st == MFCG_OK && P->cg_prec != PREC_F64 && P->cg_prec != P->op_prec)
@@ -976,6 +1006,13 @@ int mfcg_setup(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, con
   if (cudaMallocHost(&P->h_state, 2 * sizeof(CGState)) != cudaSuccess) return fail(MFCG_OUT_OF_MEMORY);
   if (cudaMemsetAsync(P->state, 0, sizeof(CGState), P->exec) != cudaSuccess) return fail(MFCG_CUDA_ERROR);
   if (enter(P) != MFCG_OK) return fail(MFCG_CUDA_ERROR);
+  if (share) {
+    // geometry and diagonal come from the identical problem
+    if (cudaStreamSynchronize(P->exec) != cudaSuccess) return fail(MFCG_CUDA_ERROR);
+    if (leave(P) != MFCG_OK) return fail(MFCG_CUDA_ERROR);
+    *out = P;
+    return MFCG_OK;
+  }
   if (P->geom_kind != GEOM_AFFINE) {
     if (launch_geometry(g, P->c, P->geom_kind, P->geo, P->exec) != cudaSuccess) return fail(MFCG_CUDA_ERROR);
     if (P->geo_op != P->geo && launch_to_prec(P->op_prec, P->geo, P->geo_op, ngeo, P->exec) != cudaSuccess)
@@ -1005,6 +1042,8 @@ int mfcg_setup(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, con
   *out = P;
   return MFCG_OK;
 }
+
+extern "C" {
 
 int mfcg_n_dofs(const mfcg_problem* P, int64_t* n) {
   if (!P || !n) return MFCG_INVALID_ARG;

@@ -520,3 +520,26 @@ def test_vector_valued_mass_operator(mfcg):
 def test_mass_operator_rejects_final_tensor_storage(mfcg):
     with pytest.raises(mfcg.MfcgError):
         mfcg.Problem(3, (2, 2, 2), amplitude=0.05, geometry="deformed_tensor", operator="mass")
+
+
+def test_batch_of_right_hand_sides_shares_operator_data(mfcg):
+    # identical members (one mesh, several right-hand sides) share geometry and
+    # diagonal; each solve matches the oracle and its single-problem solve
+    spec = {"degree": 3, "cells": (3, 4, 3), "amplitude": 0.05, "coefficient": "sin_x"}
+    specs = [spec] * 4
+    batch = mfcg.Batch(specs, precision="double_float")
+    op = _oracle_problem(3, (3, 4, 3), 0.05, "sin_x")
+    A = fem.assemble(op)
+    rhs = inputs.batch_rhs(specs)
+    bs = [_to_dev(m, r) for m, r in zip(batch.members, rhs)]
+    xs, infos = batch.cg_solve(bs, rtol=1e-10, maxit=5000)
+    single = _gpu_problem(mfcg, 3, (3, 4, 3), 0.05, "sin_x", precision="double_float")
+    for m, b, x, info, r in zip(batch.members, bs, xs, infos, rhs):
+        ref = ocg.pcg_algorithm1(lambda v: A @ v, r, 1.0 / A.diagonal(), 1e-10, 5000)
+        assert info["converged"] == 1 and abs(info["iterations"] - ref.iterations) <= 1
+        assert _rel(_to_host(m, x), ref.x) <= SOL_TOL
+        assert _rel(_to_host(m, m.diagonal()), A.diagonal()) <= OP_TOL
+        x1, _ = single.cg_solve(b, rtol=1e-10, maxit=5000)
+        assert torch.equal(x1, x)
+    single.close()
+    batch.close()
