@@ -951,7 +951,8 @@ int setup_impl(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, con
   P->ahead_op = n_sm * tile_occupancy(degree, MODE_OPERATOR, P->geom_kind, P->op_prec, P->ncomp,
                                       tile_smem_bytes(degree, P->geom_kind, P->op_prec, g, MODE_OPERATOR));
   P->tail_nodes = P->fam[0] + P->fam[1] + P->fam[2];
-  P->tail_ctas = (int)std::min<int64_t>(std::max<int64_t>((P->tail_nodes + 2 * kThreads - 1) / (2 * kThreads), 1), 152 * 32);
+  // about four shared-face nodes per tail thread (two iterations of two)
+  P->tail_ctas = (int)std::min<int64_t>(std::max<int64_t>((P->tail_nodes + 4 * kThreads - 1) / (4 * kThreads), 1), 152 * 16);
 
   const double h[3] = {1.0 / N[0], 1.0 / N[1], 1.0 / N[2]};
   build_coeffs(degree, h, mesh->amplitude, geom->coefficient, P->c);

@@ -84,8 +84,8 @@ extern "C" int mfcg_apply_operator_static(const mfcg_mesh* mesh, int degree, con
     g_scratch_addr[dev] = ptr;
   }
   a.tail_nodes = a.fam[0] + a.fam[1] + a.fam[2];
-  const int64_t ctas = (a.tail_nodes + 2 * kThreads - 1) / (2 * kThreads);
-  a.tail_ctas = (int)(ctas < 1 ? 1 : (ctas > 152 * 32 ? 152 * 32 : ctas));
+  const int64_t ctas = (a.tail_nodes + 4 * kThreads - 1) / (4 * kThreads);
+  a.tail_ctas = (int)(ctas < 1 ? 1 : (ctas > 152 * 16 ? 152 * 16 : ctas));
   a.shell = g_scratch_addr[dev];
   a.in0 = src;
   a.out0 = dst;

@@ -1306,29 +1306,66 @@ __global__ void __launch_bounds__(kThreads) tail_kernel(const TileArgs a) {
   } else {
     dst = static_cast<double*>(a.out0) + co;
   }
-  for (int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x; t < a.tail_nodes; t += (int64_t)gridDim.x * kThreads) {
-    int i, j, k;
-    decode_tail_node(g, a.fam, a.tdiv, t, i, j, k);
-    int txs[2], lis[2], tys[2], ljs[2], tzs[2], lks[2];
-    const int nx = contributors(g, 0, i, txs, lis);
-    const int ny = contributors(g, 1, j, tys, ljs);
-    const int nz = contributors(g, 2, k, tzs, lks);
-    T v = t_zero<PREC>();
-    for (int cz = 0; cz < nz; ++cz)
-      for (int cy = 0; cy < ny; ++cy)
-        for (int cx = 0; cx < nx; ++cx) {
-          const int64_t tl = txs[cx] + (int64_t)g.nt[0] * (tys[cy] + (int64_t)g.nt[1] * tzs[cz]);
-          const int bx = brick_extent(g, 0, txs[cx]), by = brick_extent(g, 1, tys[cy]),
-                    bz = brick_extent(g, 2, tzs[cz]);
-          v = t_add<PREC>(v, shell[tl * g.face_stride + shell_slot(g, lis[cx], ljs[cy], lks[cz], bx, by, bz)]);
-        }
-    const int64_t gi = node_index(g, i, j, k);
+  // Two nodes per thread and iteration, each summing its (up to eight) shell
+  // partials through a fixed 2x2x2 loop of predicated loads, so that all loads
+  // of both nodes are in flight together; the sum order is the fixed (z, y, x)
+  // order of the contributing tiles.
+  const int64_t gstride = (int64_t)gridDim.x * kThreads;
+  for (int64_t t0 = (int64_t)blockIdx.x * kThreads + threadIdx.x; t0 < a.tail_nodes; t0 += 2 * gstride) {
+    T v[2];
+    int64_t gi[2];
+    bool ok[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t t = t0 + h * gstride;
+      ok[h] = t < a.tail_nodes;
+      v[h] = t_zero<PREC>();
+      gi[h] = 0;
+      if (!ok[h]) continue;
+      int i, j, k;
+      decode_tail_node(g, a.fam, a.tdiv, t, i, j, k);
+      int txs[2], lis[2], tys[2], ljs[2], tzs[2], lks[2];
+      const int nx = contributors(g, 0, i, txs, lis);
+      const int ny = contributors(g, 1, j, tys, ljs);
+      const int nz = contributors(g, 2, k, tzs, lks);
+      T part[8];
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const int cx = m & 1, cy = (m >> 1) & 1, cz = m >> 2;
+        const bool use = cx < nx && cy < ny && cz < nz;
+        const int ux = use ? cx : 0, uy = use ? cy : 0, uz = use ? cz : 0;
+        const int64_t tl = txs[ux] + (int64_t)g.nt[0] * (tys[uy] + (int64_t)g.nt[1] * tzs[uz]);
+        const int bx = brick_extent(g, 0, txs[ux]), by = brick_extent(g, 1, tys[uy]), bz = brick_extent(g, 2, tzs[uz]);
+        part[m] = use ? shell[tl * g.face_stride + shell_slot(g, lis[ux], ljs[uy], lks[uz], bx, by, bz)]
+                      : t_zero<PREC>();
+      }
+      // the same (z, y, x) order as the contributing tiles
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const int cx = m & 1, cy = (m >> 1) & 1, cz = m >> 2;
+        if (cx < nx && cy < ny && cz < nz) v[h] = m == 0 ? part[m] : t_add<PREC>(v[h], part[m]);
+      }
+      gi[h] = node_index(g, i, j, k);
+    }
     if constexpr (MODE == MODE_CG) {
-      const T rk = r_k[gi], pk = p_k[gi];
-      v_k[gi] = v;
-      post_sums<PREC>(sm, rk, pk, v, static_cast<const T*>(a.diag_inv)[gi]);
+      T rk[2], pk[2], dv[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (!ok[h]) continue;
+        rk[h] = r_k[gi[h]];
+        pk[h] = p_k[gi[h]];
+        dv[h] = static_cast<const T*>(a.diag_inv)[gi[h]];
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (!ok[h]) continue;
+        v_k[gi[h]] = v[h];
+        post_sums<PREC>(sm, rk[h], pk[h], v[h], dv[h]);
+      }
     } else {
-      dst[gi] = t_to_double<PREC>(v);
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+        if (ok[h]) dst[gi[h]] = t_to_double<PREC>(v[h]);
     }
   }
   }  // components
