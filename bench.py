@@ -49,10 +49,15 @@ def measured_peaks():
 
 
 def kernel_sources_hash() -> str:
+    """Hash of the kernel sources with comments and whitespace removed, so that
+    an edit of comments alone keeps the stored ncu counters valid."""
     h = hashlib.sha256()
     for rel in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, rel), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, rel)) as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

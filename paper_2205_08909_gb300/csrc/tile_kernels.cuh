@@ -6,9 +6,12 @@
 //            neighbour tile, stored by the owner only), the delayed x update
 //            on odd k > 1, and p_k staged in shared memory;
 //   phase 2 (Eq. 4 / Eq. 5): sum-factorised cell integrals of all cells of the
-//            tile, accumulated into a shared-memory node brick, cells of one
-//            colour (parity of the cell index) at a time so that no two
-//            concurrent cells share a node;
+//            tile into a shared-memory node brick: on Cartesian tiles as three
+//            even-odd sweeps along whole brick lines (the Kronecker sum of the
+//            assembled 1D matrices), on deformed tiles cell batch by cell batch
+//            with a fixed-order node gather, in the set-up passes one colour
+//            (parity of the cell index) at a time -- no two threads ever add
+//            into the same node;
 //   phase 3 ("post"): nodes whose last contribution came from this tile are
 //            final: v_k is stored and the seven sums of Algorithm 5 are
 //            accumulated; nodes on faces shared with another tile store their
@@ -18,8 +21,9 @@
 // per-CTA sums in a fixed order and computes alpha_k, the Eq. 8 residual
 // estimate, the convergence flag and beta_k (Eq. 7) on the device.
 //
-// Every kernel is a template on the degree P, the mode, the geometry kind and
-// the arithmetic precision (precision.cuh): FP64, double-float or FP32.
+// Every kernel is a template on the degree P, the mode, the geometry kind, the
+// arithmetic precision (precision.cuh: FP64, double-float or FP32) and, for the
+// tile kernel, the number of components (1 or 3).
 #pragma once
 
 #include <algorithm>
