@@ -60,8 +60,11 @@ typedef enum mfcg_geometry_kind {
   MFCG_GEOM_AFFINE = 0,     /* constant Jacobian per cell (Cartesian box cells), Sec. 2.2 "affine" variant */
   MFCG_GEOM_DEFORMED = 1,   /* per-quadrature-point inverse Jacobian and JxW stored in FP64, Sec. 2.2
                                "inverse Jacobian load" variant (10 values per point)                        */
-  MFCG_GEOM_DEFORMED_TENSOR = 2  /* the same mesh with the symmetric tensor J^{-1} (w det J a) J^{-T}
+  MFCG_GEOM_DEFORMED_TENSOR = 2, /* the same mesh with the symmetric tensor J^{-1} (w det J a) J^{-T}
                                stored per point, Sec. 2.2 "final tensor load" variant (6 values per point) */
+  MFCG_GEOM_USER = 3        /* per-point data supplied by the caller (mfcg_geometry.user_data), stored
+                               like MFCG_GEOM_DEFORMED: any cell geometry and coefficient whose
+                               mesh is logically the Nx x Ny x Nz box of cells                       */
 } mfcg_geometry_kind;
 
 typedef enum mfcg_coefficient_kind {
@@ -71,7 +74,13 @@ typedef enum mfcg_coefficient_kind {
 
 typedef struct mfcg_geometry {
   int32_t kind;             /* mfcg_geometry_kind   */
-  int32_t coefficient;      /* mfcg_coefficient_kind */
+  int32_t coefficient;      /* mfcg_coefficient_kind (MFCG_GEOM_USER: folded into user_data)       */
+  const double* user_data;  /* MFCG_GEOM_USER: HOST array of Nx*Ny*Nz * 10 * (p+1)^3 doubles, read
+                               during mfcg_setup only.  Cells in lexicographic order
+                               (cx + Nx (cy + Ny cz)); per cell ten blocks of (p+1)^3 values at the
+                               tensor Gauss points q = qa + (p+1)(qb + (p+1) qc) of the reference
+                               cell [0,1]^3: the nine entries of J^{-1} row-major (J_ij = dx_i/dxhat_j),
+                               then w_q det J_q a(x_q).  NULL for the other kinds.                  */
 } mfcg_geometry;
 
 typedef enum mfcg_mode {
@@ -151,7 +160,8 @@ typedef struct mfcg_problem mfcg_problem;
  * Errors: INVALID_ARG (cells < 1, |amplitude| >= 0.1, affine kind with A != 0 or
  * a != 1, bad enums, FP32_INNER without FUSED, SEMI_FUSED with FP32_INNER,
  * components other than 0, 1, 3 or components 3 without FUSED, MFCG_OP_MASS with
- * MFCG_GEOM_DEFORMED_TENSOR), UNSUPPORTED_DEGREE, OUT_OF_MEMORY, CUDA_ERROR. */
+ * MFCG_GEOM_DEFORMED_TENSOR, MFCG_GEOM_USER without user_data), UNSUPPORTED_DEGREE,
+ * OUT_OF_MEMORY, CUDA_ERROR. */
 int mfcg_setup(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, const mfcg_options* opt,
                void* cuda_stream, mfcg_problem** out);
 
@@ -173,7 +183,7 @@ int mfcg_diagonal(mfcg_problem* prob, double* diag);
 /* mfcg_rhs -- right-hand side b_i = int f phi_i for the manufactured solution
  * u = sin(pi x) sin(pi y) sin(pi z) (f = -div(a grad u)), same Gauss rule,
  * 0 on Dirichlet nodes; for MFCG_OP_MASS the right-hand side of the same u
- * (f = a u).  b: device, n doubles.  With components > 1, component c holds the
+ * (f = a u).  Not defined for MFCG_GEOM_USER (INVALID_ARG).  b: device, n doubles.  With components > 1, component c holds the
  * right-hand side of u_c = (c + 1) u.  Asynchronous. */
 int mfcg_rhs(mfcg_problem* prob, double* b);
 

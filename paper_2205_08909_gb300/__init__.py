@@ -34,6 +34,8 @@ class Problem:
     degree: 1..8; cells: (Nx, Ny, Nz); amplitude: sine deformation of the mesh
     (needs geometry="deformed", which stores J^{-1} and JxW per quadrature
     point, or "deformed_tensor", which stores the symmetric J^{-1} JxW a J^{-T});
+    geometry="user" takes those ten values per point from user_data (host array,
+    cells x 10 x (degree+1)^3, cells lexicographic);
     coefficient: "constant" (a = 1) or "sin_x"
     (a = 1 + 0.5 sin(pi x)); mode: "fused" (Algorithm 5 inside the operator
     pass), "unfused" (Algorithm 1, one kernel per vector operation) or
@@ -51,7 +53,7 @@ class Problem:
                  coefficient: str = "constant", mode: str = "fused", precision: str = "fp64",
                  preconditioner: str = "jacobi", inner_rtol: float = 0.0, graph_iterations: int = 0,
                  instrument: bool = False, tile=None, components: int = 1, operator: str = "laplace",
-                 stream: torch.cuda.Stream | None = None):
+                 user_data=None, stream: torch.cuda.Stream | None = None):
         if not torch.cuda.is_available():
             raise RuntimeError("paper_2205_08909_gb300 needs a CUDA device (no CPU fallback)")
         self._lib = _binding.load()
@@ -60,7 +62,15 @@ class Problem:
         cells = tuple(int(c) for c in (cells if hasattr(cells, "__len__") else (cells,) * 3))
         self.degree, self.cells = int(degree), cells
         mesh = _binding.Mesh(cells[0], cells[1], cells[2], float(amplitude))
-        geom = _binding.Geometry(_binding.GEOM[geometry], _binding.COEF[coefficient])
+        geom = _binding.Geometry(_binding.GEOM[geometry], _binding.COEF[coefficient], None)
+        if geometry == "user":
+            # host array of cells x 10 x (degree+1)^3 doubles (J^{-1} row-major, then w det J a)
+            import numpy as np
+
+            user = np.ascontiguousarray(user_data, dtype=np.float64)
+            if user.size != cells[0] * cells[1] * cells[2] * 10 * (int(degree) + 1) ** 3:
+                raise ValueError("user_data: expected cells x 10 x (degree+1)^3 values")
+            geom.user_data = user.ctypes.data_as(ctypes.c_void_p)
         opt = _binding.Options()
         opt.mode = _binding.MODE[mode]
         opt.precision = _binding.PRECISION[precision]

@@ -763,7 +763,8 @@ int mfcg_setup_batch(int count, const mfcg_mesh* meshes, const int* degrees, con
     for (int j = 0; j < i && !share; ++j)
       if (degrees[j] == degrees[i] && meshes[j].nx == meshes[i].nx && meshes[j].ny == meshes[i].ny &&
           meshes[j].nz == meshes[i].nz && meshes[j].amplitude == meshes[i].amplitude &&
-          geoms[j].kind == geoms[i].kind && geoms[j].coefficient == geoms[i].coefficient)
+          geoms[j].kind == geoms[i].kind && geoms[j].coefficient == geoms[i].coefficient &&
+          geoms[j].user_data == geoms[i].user_data)
         share = B->members[j];
     mfcg_problem* P = nullptr;
     const int st = setup_impl(&meshes[i], degrees[i], &geoms[i], &o, cuda_stream, &P, share);
@@ -876,8 +877,10 @@ int setup_impl(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, con
   if (degree < 1 || degree > kMaxDegree) return MFCG_UNSUPPORTED_DEGREE;
   if (mesh->nx < 1 || mesh->ny < 1 || mesh->nz < 1) return MFCG_INVALID_ARG;
   if (!(std::fabs(mesh->amplitude) < 0.1)) return MFCG_INVALID_ARG;
-  if (geom->kind != MFCG_GEOM_AFFINE && geom->kind != MFCG_GEOM_DEFORMED && geom->kind != MFCG_GEOM_DEFORMED_TENSOR)
+  if (geom->kind != MFCG_GEOM_AFFINE && geom->kind != MFCG_GEOM_DEFORMED && geom->kind != MFCG_GEOM_DEFORMED_TENSOR &&
+      geom->kind != MFCG_GEOM_USER)
     return MFCG_INVALID_ARG;
+  if (geom->kind == MFCG_GEOM_USER && !geom->user_data) return MFCG_INVALID_ARG;
   if (geom->coefficient != MFCG_COEF_CONSTANT && geom->coefficient != MFCG_COEF_SIN_X) return MFCG_INVALID_ARG;
   if (geom->kind == MFCG_GEOM_AFFINE && (mesh->amplitude != 0.0 || geom->coefficient != MFCG_COEF_CONSTANT))
     return MFCG_INVALID_ARG;
@@ -917,6 +920,7 @@ int setup_impl(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, con
   P->op_kind = o.operator_kind == MFCG_OP_MASS ? OP_MASS : OP_LAPLACE;
   P->geom_kind = geom->kind == MFCG_GEOM_AFFINE ? GEOM_AFFINE
                   : (geom->kind == MFCG_GEOM_DEFORMED_TENSOR ? GEOM_TENSOR : GEOM_DEFORMED);
+  P->geom.user_data = nullptr;  // read during set-up only
   // the defect correction forms its outer residual with the native FP64
   // operator: its true-residual floor is 2^5 lower than the double-float one
   P->op_prec = o.precision == MFCG_PREC_DOUBLE_FLOAT ? PREC_DD : PREC_F64;
@@ -1015,7 +1019,13 @@ int setup_impl(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, con
     return MFCG_OK;
   }
   if (P->geom_kind != GEOM_AFFINE) {
-    if (launch_geometry(g, P->c, P->geom_kind, P->geo, P->exec) != cudaSuccess) return fail(MFCG_CUDA_ERROR);
+    if (geom->kind == MFCG_GEOM_USER) {
+      if (cudaMemcpyAsync(P->geo, geom->user_data, ngeo * sizeof(double), cudaMemcpyHostToDevice, P->exec) !=
+          cudaSuccess)
+        return fail(MFCG_CUDA_ERROR);
+    } else if (launch_geometry(g, P->c, P->geom_kind, P->geo, P->exec) != cudaSuccess) {
+      return fail(MFCG_CUDA_ERROR);
+    }
     if (P->geo_op != P->geo && launch_to_prec(P->op_prec, P->geo, P->geo_op, ngeo, P->exec) != cudaSuccess)
       return fail(MFCG_CUDA_ERROR);
     if (P->geo_cg != P->geo && P->geo_cg != P->geo_op &&
@@ -1069,7 +1079,7 @@ int mfcg_diagonal(mfcg_problem* P, double* diag) {
 }
 
 int mfcg_rhs(mfcg_problem* P, double* b) {
-  if (!P || !b) return MFCG_INVALID_ARG;
+  if (!P || !b || P->geom.kind == MFCG_GEOM_USER) return MFCG_INVALID_ARG;
   int st;
   if ((st = enter(P)) != MFCG_OK) return st;
   if ((st = run_pass(P, MODE_RHS, nullptr, b)) != MFCG_OK) return st;

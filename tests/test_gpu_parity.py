@@ -543,3 +543,34 @@ def test_batch_of_right_hand_sides_shares_operator_data(mfcg):
         assert torch.equal(x1, x)
     single.close()
     batch.close()
+
+
+def _oracle_point_data(op):
+    """The oracle's per-point geometry in the layout of MFCG_GEOM_USER:
+    cells x (9 entries of J^{-1}, w det J a) x points."""
+    x, J, detJ, w = fem.quadrature_geometry(op)
+    Jinv = np.linalg.inv(J).reshape(J.shape[0], J.shape[1], 9)            # [e, q, 9]
+    jxw = w[None, :] * detJ * fem.coefficient(op, x)                        # [e, q]
+    return np.concatenate([Jinv.transpose(0, 2, 1), jxw[:, None, :]], axis=1)  # [e, 10, q]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "double_float"])
+@pytest.mark.parametrize("p,cells,amp,coef", [(3, (3, 4, 3), 0.05, "sin_x"), (5, (2, 3, 2), 0.08, "constant"),
+                                              (2, (4, 3, 5), 0.0, "constant")])
+def test_user_point_data_geometry(mfcg, p, cells, amp, coef, precision):
+    # the operator on per-point data supplied by the caller (here: the oracle's
+    # own Jacobians and weights) equals the oracle's assembled matrix
+    op = _oracle_problem(p, cells, amp, coef)
+    A = fem.assemble(op)
+    prob = mfcg.Problem(p, cells, geometry="user", user_data=_oracle_point_data(op), precision=precision)
+    u = inputs.random_vector(op.n_dofs, salt=p)
+    assert _rel(_to_host(prob, prob.apply_operator(_to_dev(prob, u))), A @ u) <= OP_TOL
+    assert _rel(_to_host(prob, prob.diagonal()), A.diagonal()) <= OP_TOL
+    b = fem.rhs(op)
+    ref = ocg.pcg_algorithm1(lambda v: A @ v, b, 1.0 / A.diagonal(), 1e-10, 5000)
+    x, info = prob.cg_solve(_to_dev(prob, b), rtol=1e-10, maxit=5000)
+    assert info["converged"] == 1 and abs(info["iterations"] - ref.iterations) <= 1
+    assert _rel(_to_host(prob, x), ref.x) <= SOL_TOL
+    with pytest.raises(mfcg.MfcgError):
+        prob.rhs()
+    prob.close()
