@@ -130,6 +130,10 @@ typedef struct mfcg_options {
                                components.  Vectors hold the components one after another (each in
                                the tile-blocked order); FUSED mode only                               */
   int32_t operator_kind;    /* mfcg_operator                                                        */
+  int32_t x_update_every_iteration; /* 0: the delayed x update of Algorithm 5 (every other iteration,
+                               two steps at once); 1: x_k = x_{k-1} + alpha_{k-1} p_{k-1} in every
+                               iteration (FUSED and SEMI_FUSED; the same iterates in exact arithmetic) */
+  int32_t reserved;
 } mfcg_options;
 
 typedef struct mfcg_solve_info {

@@ -35,7 +35,8 @@ class Problem:
     (needs geometry="deformed", which stores J^{-1} and JxW per quadrature
     point, or "deformed_tensor", which stores the symmetric J^{-1} JxW a J^{-T});
     geometry="user" takes those ten values per point from user_data (host array,
-    cells x 10 x (degree+1)^3, cells lexicographic);
+    cells x 10 x (degree+1)^3, cells lexicographic); x_every_iteration: update x
+    in every iteration instead of Algorithm 5's delayed update;
     coefficient: "constant" (a = 1) or "sin_x"
     (a = 1 + 0.5 sin(pi x)); mode: "fused" (Algorithm 5 inside the operator
     pass), "unfused" (Algorithm 1, one kernel per vector operation) or
@@ -53,7 +54,7 @@ class Problem:
                  coefficient: str = "constant", mode: str = "fused", precision: str = "fp64",
                  preconditioner: str = "jacobi", inner_rtol: float = 0.0, graph_iterations: int = 0,
                  instrument: bool = False, tile=None, components: int = 1, operator: str = "laplace",
-                 user_data=None, stream: torch.cuda.Stream | None = None):
+                 user_data=None, x_every_iteration: bool = False, stream: torch.cuda.Stream | None = None):
         if not torch.cuda.is_available():
             raise RuntimeError("paper_2205_08909_gb300 needs a CUDA device (no CPU fallback)")
         self._lib = _binding.load()
@@ -80,6 +81,7 @@ class Problem:
         opt.instrument = 1 if instrument else 0
         opt.components = int(components)
         opt.operator_kind = _binding.OPERATOR[operator]
+        opt.x_update_every_iteration = 1 if x_every_iteration else 0
         self.components = int(components)
         if tile is not None:
             for d in range(3):

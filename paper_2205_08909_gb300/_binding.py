@@ -38,7 +38,8 @@ class Geometry(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("graph_iterations", ctypes.c_int32), ("instrument", ctypes.c_int32),
                 ("tile", ctypes.c_int32 * 3), ("precision", ctypes.c_int32), ("preconditioner", ctypes.c_int32),
-                ("inner_rtol", ctypes.c_double), ("components", ctypes.c_int32), ("operator_kind", ctypes.c_int32)]
+                ("inner_rtol", ctypes.c_double), ("components", ctypes.c_int32), ("operator_kind", ctypes.c_int32),
+                ("x_update_every_iteration", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class SolveInfo(ctypes.Structure):

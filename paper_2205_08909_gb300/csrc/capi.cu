@@ -350,7 +350,7 @@ int run_iterations(mfcg_problem* P, int kind, int maxit, IterStats& stats) {
 int fused_start(mfcg_problem* P, const double* b, const double* r0, double rtol, int maxit, int fixed) {
   const int64_t n = P->nv();
   const size_t es = prec_bytes(P->cg_prec);
-  CK(launch_cg_init(P->state, b, r0, n, rtol, maxit, fixed, P->partial, 0, P->exec));
+  CK(launch_cg_init(P->state, b, r0, n, rtol, maxit, fixed, P->partial, P->opt.x_update_every_iteration, P->exec));
   CK(launch_to_prec(P->cg_prec, r0, P->r[0], n, P->exec));
   CK(cudaMemsetAsync(P->p[0], 0, n * es, P->exec));
   CK(cudaMemsetAsync(P->v[0], 0, n * es, P->exec));
@@ -423,7 +423,8 @@ int solve_direct(mfcg_problem* P, const double* b, double* x_user, double rtol, 
     CK(cudaMemcpyAsync(P->ur, P->work, n * sizeof(double), cudaMemcpyDeviceToDevice, P->exec));
     CK(cudaMemsetAsync(P->up, 0, n * sizeof(double), P->exec));
     CK(cudaMemsetAsync(P->uv, 0, n * sizeof(double), P->exec));
-    CK(launch_cg_init(P->state, b, P->ur, n, rtol, maxit, fixed, P->partial, 0, P->exec));
+    CK(launch_cg_init(P->state, b, P->ur, n, rtol, maxit, fixed, P->partial, P->opt.x_update_every_iteration,
+                      P->exec));
     P->launches += 1;
     if ((st = run_iterations(P, ITER_SEMI, maxit, stats)) != MFCG_OK) return st;
     CK(launch_finalize_fused(PREC_F64, n, P->state, P->x, P->up, P->up, P->ur, P->ur, P->diag_inv, P->exec));
@@ -474,8 +475,8 @@ int solve_defect_correction(mfcg_problem* P, const double* b, double* x_user, do
     // (r, r) gives ||r||^2 and the inner tolerance inner_rtol^2 ||r||^2
     if ((st = run_pass(P, MODE_OPERATOR, P->x, P->work)) != MFCG_OK) return st;
     CK(launch_residual(b, P->work, P->work, n, P->exec));
-    CK(launch_cg_init(P->state, P->work, P->work, n, inner, std::max(maxit - total_it, 1), 0, P->partial, 0,
-                      P->exec));
+    CK(launch_cg_init(P->state, P->work, P->work, n, inner, std::max(maxit - total_it, 1), 0, P->partial,
+                      P->opt.x_update_every_iteration, P->exec));
     CK(cudaMemcpyAsync(P->h_state, P->state, sizeof(CGState), cudaMemcpyDeviceToHost, P->exec));
     CK(cudaStreamSynchronize(P->exec));
     P->launches += 2;
@@ -893,6 +894,7 @@ int setup_impl(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, con
   if (o.precision < MFCG_PREC_FP64 || o.precision > MFCG_PREC_FP32_INNER) return MFCG_INVALID_ARG;
   if (o.precision == MFCG_PREC_FP32_INNER && o.mode != MFCG_MODE_FUSED) return MFCG_INVALID_ARG;
   if (!(o.inner_rtol >= 0.0 && o.inner_rtol < 1.0)) return MFCG_INVALID_ARG;
+  if (o.x_update_every_iteration != 0 && o.x_update_every_iteration != 1) return MFCG_INVALID_ARG;
   if ((o.components != 0 && o.components != 1 && o.components != 3) || (o.components > 1 && o.mode != MFCG_MODE_FUSED))
     return MFCG_INVALID_ARG;
   if (o.operator_kind != MFCG_OP_LAPLACE && o.operator_kind != MFCG_OP_MASS) return MFCG_INVALID_ARG;

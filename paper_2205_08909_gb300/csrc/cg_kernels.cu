@@ -143,7 +143,7 @@ __global__ void residual_kernel(const double* b, const double* ax, double* r, in
 
 // CG start: eps^2 = rtol^2 ||b||^2; an exactly zero initial residual finishes at once.
 __global__ void cg_init_kernel(CGState* st, const double* b, const double* r0, int64_t n, double rtol, int maxit,
-                               int fixed, double* partial) {
+                               int fixed, double* partial, int x_every_iter) {
   double v[2] = {0.0, 0.0};
   for (int64_t i = blockIdx.x * (int64_t)kVecThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVecThreads) {
     v[0] = fma(b[i], b[i], v[0]);
@@ -161,7 +161,7 @@ __global__ void cg_init_kernel(CGState* st, const double* b, const double* r0, i
     st->maxit = maxit;
     st->iterations = 0;
     st->fixed = fixed;
-    st->x_every_iter = 0;
+    st->x_every_iter = x_every_iter;
     st->done = (tot[1] == 0.0 || maxit <= 0) ? 1 : 0;
     if (!isfinite(tot[0]) || !isfinite(tot[1])) st->done = 3;
     prepare_iteration_scalars(st);
@@ -180,11 +180,12 @@ __global__ void finalize_fused_kernel(int64_t n, const CGState* st, void* xv, co
   const T* r = static_cast<const T*>((k & 1) ? r1v : r0v);
   const T* dinv = static_cast<const T*>(dinvv);
   T* x = static_cast<T*>(xv);
+  const bool current = (k & 1) || st->x_every_iter;  // x holds x_k: one plain step
   const T a = t_from_double<PREC>(st->alpha_cur);
-  const T c = t_from_double<PREC>((k & 1) ? 0.0 : st->alpha_prev / st->beta_prev);
+  const T c = t_from_double<PREC>(current ? 0.0 : st->alpha_prev / st->beta_prev);
   for (int64_t i = blockIdx.x * (int64_t)kVecThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVecThreads) {
     const T pk = p[i];
-    if (k & 1)
+    if (current)
       x[i] = t_axpy<PREC>(a, pk, x[i]);
     else
       x[i] = t_add<PREC>(x[i], t_axby<PREC>(a, pk, c, t_sub<PREC>(pk, t_mul<PREC>(dinv[i], r[i]))));
@@ -330,9 +331,8 @@ cudaError_t launch_residual(const double* b, const double* ax, double* r, int64_
 }
 
 cudaError_t launch_cg_init(CGState* st, const double* b, const double* r0, int64_t n, double rtol, int maxit, int fixed,
-                           double* partial, int n_ctas, cudaStream_t s) {
-  (void)n_ctas;
-  cg_init_kernel<<<grid_for(n), kVecThreads, 0, s>>>(st, b, r0, n, rtol, maxit, fixed, partial);
+                           double* partial, int x_every_iter, cudaStream_t s) {
+  cg_init_kernel<<<grid_for(n), kVecThreads, 0, s>>>(st, b, r0, n, rtol, maxit, fixed, partial, x_every_iter);
   return cudaGetLastError();
 }
 

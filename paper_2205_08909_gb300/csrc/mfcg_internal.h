@@ -287,7 +287,7 @@ struct CGState {
   int maxit;
   int iterations;                  // finished iterations
   unsigned int ticket;             // last-CTA election counter
-  int x_every_iter;                // unused (kept for layout)
+  int x_every_iter;                // 1: x += alpha_{k-1} p_{k-1} every iteration instead of the delayed update
   int fixed;                       // 1: ignore the tolerance, run maxit iterations
   int pad;
   // scalars of the next iteration, prepared once by the scalar step so that the
@@ -301,7 +301,7 @@ struct CGState {
 // fills ratio and sc[] from alpha_prev, beta_prev, alpha_prev2, beta_prev2, k
 __host__ __device__ inline void prepare_iteration_scalars(CGState* st) {
   const int k = st->k;
-  st->ratio = (k > 1 && (k & 1)) ? st->alpha_prev2 / st->beta_prev2 : 0.0;
+  st->ratio = (!st->x_every_iter && k > 1 && (k & 1)) ? st->alpha_prev2 / st->beta_prev2 : 0.0;
   const double v[4] = {-st->alpha_prev, st->beta_prev, st->alpha_prev, st->ratio};
   for (int m = 0; m < 4; ++m) {
     const float hi = (float)v[m];
@@ -419,7 +419,7 @@ struct UnfusedArgs {
 cudaError_t launch_unfused_dot(int which, const UnfusedArgs& a, cudaStream_t s);
 cudaError_t launch_unfused_axpy(int which, const UnfusedArgs& a, cudaStream_t s);
 cudaError_t launch_cg_init(CGState* st, const double* b, const double* r0, int64_t n, double rtol, int maxit,
-                           int fixed, double* partial, int n_ctas, cudaStream_t s);
+                           int fixed, double* partial, int x_every_iter, cudaStream_t s);
 cudaError_t launch_residual(const double* b, const double* ax, double* r, int64_t n, cudaStream_t s);
 cudaError_t launch_scale(const double* in, double* out, double factor, int64_t n, cudaStream_t s);
 cudaError_t launch_gather_done(const CGState* const* states, int count, int* done, cudaStream_t s);

@@ -24,7 +24,7 @@ __global__ void semi_pre_kernel(int64_t n, const CGState* st, double* x, double*
                                 const double* dinv) {
   if (st->done) return;
   const int k = st->k;
-  const bool xupd = k > 1 && (k & 1);
+  const bool xupd = k > 1 && ((k & 1) || st->x_every_iter);
   const double am = -st->alpha_prev, beta = st->beta_prev, xa = st->alpha_prev, xr = st->ratio;
   for (int64_t i = blockIdx.x * (int64_t)kVec + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVec) {
     const double r_o = r[i], p_o = p[i], d = dinv[i];

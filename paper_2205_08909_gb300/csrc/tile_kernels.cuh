@@ -810,7 +810,7 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a_all, co
     const CGState* st = a_all.state;
     if (st->done) return;
     const int k = st->k;
-    xupd = (k > 1) && (k & 1);
+    xupd = (k > 1) && ((k & 1) || st->x_every_iter);
     if constexpr (PREC == PREC_F64) {
       alpha_m = -st->alpha_prev;
       beta_t = st->beta_prev;
@@ -1275,7 +1275,7 @@ __device__ inline void cg_scalar_step(CGState* st, const double (&s)[7]) {
     return;
   }
   const double beta = fma(alpha * alpha, fv, fma(-2.0 * alpha, ev, dv)) / dv;  // Eq. 7
-  if ((k + 1) % 2 == 1 && !(st->beta_prev != 0.0)) {
+  if (!st->x_every_iter && (k + 1) % 2 == 1 && !(st->beta_prev != 0.0)) {
     // the delayed update of the next (odd) iteration divides by beta_{k-1}
     st->done = 3;
     return;

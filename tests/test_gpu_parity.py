@@ -574,3 +574,28 @@ def test_user_point_data_geometry(mfcg, p, cells, amp, coef, precision):
     with pytest.raises(mfcg.MfcgError):
         prob.rhs()
     prob.close()
+
+
+@pytest.mark.parametrize("mode,precision", [("fused", "fp64"), ("fused", "double_float"), ("semi_fused", "fp64"),
+                                            ("fused", "fp32_inner")])
+@pytest.mark.parametrize("maxit", [1, 2, 3, 6, 7, 0])
+def test_x_update_every_iteration(mfcg, mode, precision, maxit):
+    # the plain x update in every iteration gives Algorithm 1's iterates too
+    # (maxit 0: run to rtol 1e-10)
+    op = _oracle_problem(3, (3, 4, 3), 0.05, "sin_x")
+    A = fem.assemble(op)
+    b = fem.rhs(op)
+    prob = _gpu_problem(mfcg, 3, (3, 4, 3), 0.05, "sin_x", mode=mode, precision=precision, x_every_iteration=True)
+    if maxit == 0:
+        ref = ocg.pcg_algorithm1(lambda v: A @ v, b, 1.0 / A.diagonal(), 1e-10, 5000)
+        x, info = prob.cg_solve(_to_dev(prob, b), rtol=1e-10, maxit=5000)
+        assert info["converged"] == 1
+        if precision != "fp32_inner":
+            assert abs(info["iterations"] - ref.iterations) <= 1
+        assert _rel(_to_host(prob, x), ref.x) <= SOL_TOL
+    elif precision != "fp32_inner":
+        ref = ocg.pcg_algorithm1(lambda v: A @ v, b, 1.0 / A.diagonal(), 0.0, maxit)
+        x, info = prob.cg_solve(_to_dev(prob, b), rtol=0.0, maxit=maxit)
+        assert info["iterations"] == maxit
+        assert _rel(_to_host(prob, x), ref.x) <= 1e-10
+    prob.close()
