@@ -133,7 +133,8 @@ typedef struct mfcg_options {
   int32_t x_update_every_iteration; /* 0: the delayed x update of Algorithm 5 (every other iteration,
                                two steps at once); 1: x_k = x_{k-1} + alpha_{k-1} p_{k-1} in every
                                iteration (FUSED and SEMI_FUSED; the same iterates in exact arithmetic) */
-  int32_t reserved;
+  int32_t true_residual;    /* 1: after a solve, form ||b - A x||^2 with the FP64 operator
+                               (mfcg_solve_info.true_residual_sq)                                     */
 } mfcg_options;
 
 typedef struct mfcg_solve_info {
@@ -147,6 +148,8 @@ typedef struct mfcg_solve_info {
   int64_t kernel_launches;    /* kernels this call enqueued, graph replays included                */
   int32_t outer_cycles;       /* MFCG_PREC_FP32_INNER: defect-correction cycles, else 0            */
   int32_t reserved2;
+  double true_residual_sq;    /* mfcg_options.true_residual = 1: ||b - A x||^2 of the returned x with
+                                 the FP64 operator (one extra operator pass); else -1               */
 } mfcg_solve_info;
 
 typedef struct mfcg_problem mfcg_problem;

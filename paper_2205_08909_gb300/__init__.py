@@ -54,7 +54,8 @@ class Problem:
                  coefficient: str = "constant", mode: str = "fused", precision: str = "fp64",
                  preconditioner: str = "jacobi", inner_rtol: float = 0.0, graph_iterations: int = 0,
                  instrument: bool = False, tile=None, components: int = 1, operator: str = "laplace",
-                 user_data=None, x_every_iteration: bool = False, stream: torch.cuda.Stream | None = None):
+                 user_data=None, x_every_iteration: bool = False, true_residual: bool = False,
+                 stream: torch.cuda.Stream | None = None):
         if not torch.cuda.is_available():
             raise RuntimeError("paper_2205_08909_gb300 needs a CUDA device (no CPU fallback)")
         self._lib = _binding.load()
@@ -82,6 +83,7 @@ class Problem:
         opt.components = int(components)
         opt.operator_kind = _binding.OPERATOR[operator]
         opt.x_update_every_iteration = 1 if x_every_iteration else 0
+        opt.true_residual = 1 if true_residual else 0
         self.components = int(components)
         if tile is not None:
             for d in range(3):

@@ -39,14 +39,15 @@ class Options(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("graph_iterations", ctypes.c_int32), ("instrument", ctypes.c_int32),
                 ("tile", ctypes.c_int32 * 3), ("precision", ctypes.c_int32), ("preconditioner", ctypes.c_int32),
                 ("inner_rtol", ctypes.c_double), ("components", ctypes.c_int32), ("operator_kind", ctypes.c_int32),
-                ("x_update_every_iteration", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("x_update_every_iteration", ctypes.c_int32), ("true_residual", ctypes.c_int32)]
 
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("converged", ctypes.c_int32), ("status", ctypes.c_int32),
                 ("main_kernel_launches", ctypes.c_int32), ("residual_sq_est", ctypes.c_double),
                 ("rhs_norm_sq", ctypes.c_double), ("main_kernel_ms", ctypes.c_double),
-                ("kernel_launches", ctypes.c_int64), ("outer_cycles", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
+                ("kernel_launches", ctypes.c_int64), ("outer_cycles", ctypes.c_int32), ("reserved2", ctypes.c_int32),
+                ("true_residual_sq", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -155,12 +155,13 @@ TileArgs base_args(const mfcg_problem* P, int prec, const void* geo) {
   return a;
 }
 
-// operator-like pass (tile kernel + tail) with FP64 input/output
-int run_pass(mfcg_problem* P, int mode, const double* src, double* dst) {
-  const int prec = mode == MODE_OPERATOR ? P->op_prec : PREC_F64;
-  TileArgs a = base_args(P, prec, mode == MODE_OPERATOR ? P->geo_op : P->geo);
+// operator-like pass (tile kernel + tail) with FP64 input/output; fp64_operator
+// forces the FP64 operator (true residuals) whatever the operator precision
+int run_pass(mfcg_problem* P, int mode, const double* src, double* dst, bool fp64_operator = false) {
+  const int prec = mode == MODE_OPERATOR && !fp64_operator ? P->op_prec : PREC_F64;
+  TileArgs a = base_args(P, prec, mode == MODE_OPERATOR && !fp64_operator ? P->geo_op : P->geo);
   if (mode != MODE_OPERATOR) a.ncomp = 1;  // diagonal and right-hand side of the scalar operator
-  a.prefetch_ahead = mode == MODE_OPERATOR ? P->ahead_op : 0;
+  a.prefetch_ahead = mode == MODE_OPERATOR && prec == P->op_prec ? P->ahead_op : 0;
   a.in0 = src;
   a.out0 = dst;
   CK(launch_tile(P->degree, mode, a, P->c, P->exec));
@@ -399,6 +400,7 @@ void fill_info(mfcg_problem* P, mfcg_solve_info* info, int status, int iteration
   info->kernel_launches = P->launches - launches0;
   info->outer_cycles = outer;
   info->reserved2 = 0;
+  info->true_residual_sq = -1.0;
 }
 
 int solve_direct(mfcg_problem* P, const double* b, double* x_user, double rtol, int maxit, mfcg_solve_info* info) {
@@ -545,11 +547,25 @@ int solve_fixed_inner(mfcg_problem* P, const double* b, double* x_user, int maxi
 }
 
 int solve_impl(mfcg_problem* P, const double* b, double* x_user, double rtol, int maxit, mfcg_solve_info* info) {
-  if (P->opt.precision == MFCG_PREC_FP32_INNER) {
-    if (rtol == 0.0) return solve_fixed_inner(P, b, x_user, maxit, info);
-    return solve_defect_correction(P, b, x_user, rtol, maxit, info);
+  int st;
+  if (P->opt.precision == MFCG_PREC_FP32_INNER)
+    st = rtol == 0.0 ? solve_fixed_inner(P, b, x_user, maxit, info) : solve_defect_correction(P, b, x_user, rtol, maxit, info);
+  else
+    st = solve_direct(P, b, x_user, rtol, maxit, info);
+  if (!P->opt.true_residual || (st != MFCG_OK && st != MFCG_NOT_CONVERGED)) return st;
+  // ||b - A x||^2 with the FP64 operator, one extra pass
+  const int st2 = run_pass(P, MODE_OPERATOR, x_user, P->work, true);
+  if (st2 != MFCG_OK) return st2;
+  CK(launch_residual_norm(b, P->work, P->nv(), P->partial, &P->state->ticket, &P->state->sums[6], P->exec));
+  double rr = 0.0;
+  CK(cudaMemcpyAsync(&rr, &P->state->sums[6], sizeof(double), cudaMemcpyDeviceToHost, P->exec));
+  CK(cudaStreamSynchronize(P->exec));
+  P->launches += 1;
+  if (info) {
+    info->true_residual_sq = rr;
+    info->kernel_launches += 3;
   }
-  return solve_direct(P, b, x_user, rtol, maxit, info);
+  return st;
 }
 
 // ------------------------------------------------------------------ tile autotuning
@@ -895,6 +911,7 @@ int setup_impl(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, con
   if (o.precision == MFCG_PREC_FP32_INNER && o.mode != MFCG_MODE_FUSED) return MFCG_INVALID_ARG;
   if (!(o.inner_rtol >= 0.0 && o.inner_rtol < 1.0)) return MFCG_INVALID_ARG;
   if (o.x_update_every_iteration != 0 && o.x_update_every_iteration != 1) return MFCG_INVALID_ARG;
+  if (o.true_residual != 0 && o.true_residual != 1) return MFCG_INVALID_ARG;
   if ((o.components != 0 && o.components != 1 && o.components != 3) || (o.components > 1 && o.mode != MFCG_MODE_FUSED))
     return MFCG_INVALID_ARG;
   if (o.operator_kind != MFCG_OP_LAPLACE && o.operator_kind != MFCG_OP_MASS) return MFCG_INVALID_ARG;

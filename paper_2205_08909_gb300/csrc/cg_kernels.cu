@@ -68,6 +68,19 @@ __device__ bool grid_sum(double (&v)[NV], double* partial, unsigned int* ticket,
   return true;
 }
 
+// ||b - ax||^2 with a fixed-order grid reduction into *out
+__global__ void residual_norm_kernel(const double* b, const double* ax, int64_t n, double* partial,
+                                     unsigned int* ticket, double* out) {
+  double v[1] = {0.0};
+  for (int64_t i = blockIdx.x * (int64_t)kVecThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVecThreads) {
+    const double r = b[i] - ax[i];
+    v[0] = fma(r, r, v[0]);
+  }
+  double tot[1];
+  if (!grid_sum<1>(v, partial, ticket, tot)) return;
+  if (threadIdx.x == 0) *out = tot[0];
+}
+
 __global__ void fill_kernel(double* v, double value, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)kVecThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVecThreads)
     v[i] = value;
@@ -301,6 +314,12 @@ __global__ void scale_kernel(const double* in, double* out, double factor, int64
 
 cudaError_t launch_scale(const double* in, double* out, double factor, int64_t n, cudaStream_t s) {
   scale_kernel<<<grid_for(n), kVecThreads, 0, s>>>(in, out, factor, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual_norm(const double* b, const double* ax, int64_t n, double* partial, unsigned int* ticket,
+                                 double* out, cudaStream_t s) {
+  residual_norm_kernel<<<grid_for(n), kVecThreads, 0, s>>>(b, ax, n, partial, ticket, out);
   return cudaGetLastError();
 }
 

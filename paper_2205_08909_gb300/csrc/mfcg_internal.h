@@ -421,6 +421,8 @@ cudaError_t launch_unfused_axpy(int which, const UnfusedArgs& a, cudaStream_t s)
 cudaError_t launch_cg_init(CGState* st, const double* b, const double* r0, int64_t n, double rtol, int maxit,
                            int fixed, double* partial, int x_every_iter, cudaStream_t s);
 cudaError_t launch_residual(const double* b, const double* ax, double* r, int64_t n, cudaStream_t s);
+cudaError_t launch_residual_norm(const double* b, const double* ax, int64_t n, double* partial, unsigned int* ticket,
+                                 double* out, cudaStream_t s);
 cudaError_t launch_scale(const double* in, double* out, double factor, int64_t n, cudaStream_t s);
 cudaError_t launch_gather_done(const CGState* const* states, int count, int* done, cudaStream_t s);
 cudaError_t launch_finalize_fused(int prec, int64_t n, CGState* st, void* x, const void* p0, const void* p1,

@@ -599,3 +599,23 @@ def test_x_update_every_iteration(mfcg, mode, precision, maxit):
         assert info["iterations"] == maxit
         assert _rel(_to_host(prob, x), ref.x) <= 1e-10
     prob.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "double_float", "fp32_inner"])
+def test_true_residual_of_the_solution(mfcg, precision):
+    # mfcg_options.true_residual: ||b - A x||^2 of the returned x with the FP64
+    # operator, against the oracle's assembled matrix applied to the same x
+    op = _oracle_problem(3, (3, 4, 3), 0.05, "sin_x")
+    A = fem.assemble(op)
+    b = fem.rhs(op)
+    prob = _gpu_problem(mfcg, 3, (3, 4, 3), 0.05, "sin_x", precision=precision, true_residual=True)
+    x, info = prob.cg_solve(_to_dev(prob, b), rtol=1e-10, maxit=5000)
+    r = np.linalg.norm(b - A @ _to_host(prob, x))
+    assert info["true_residual_sq"] >= 0.0
+    assert abs(np.sqrt(info["true_residual_sq"]) - r) <= 1e-12 * np.linalg.norm(b)
+    assert r <= 5e-10 * np.linalg.norm(b)
+    prob.close()
+    plain = _gpu_problem(mfcg, 3, (3, 4, 3), 0.05, "sin_x", precision=precision)
+    _, info = plain.cg_solve(_to_dev(plain, b), rtol=1e-10, maxit=5000)
+    assert info["true_residual_sq"] == -1.0
+    plain.close()
