@@ -795,8 +795,11 @@ __device__ __forceinline__ int64_t brick_global_index(const TileGeom& g, int tx,
   return tile_base(g, ntx, nty, ntz) + owned_offset(nli, nlj, nlk, nox, noy, noz);
 }
 
+// FP32 tiles run three CTAs per SM (their shared memory allows it): keep their
+// registers within 85 per thread
 template <int P, int MODE, int GEOM, int PREC, int NC>
-__global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs a_all, const OperatorCoeffs c) {
+__global__ void __launch_bounds__(kThreads, PREC == PREC_F32 ? 3 : 1)
+    tile_kernel(const TileArgs a_all, const OperatorCoeffs c) {
   using T = typename Num<PREC>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[8 * (kThreads / 32)];

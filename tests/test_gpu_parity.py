@@ -619,3 +619,21 @@ def test_true_residual_of_the_solution(mfcg, precision):
     _, info = plain.cg_solve(_to_dev(plain, b), rtol=1e-10, maxit=5000)
     assert info["true_residual_sq"] == -1.0
     plain.close()
+
+
+@pytest.mark.parametrize("mode,precision", [("fused", "fp64"), ("fused", "double_float"), ("semi_fused", "fp64")])
+def test_residual_estimate_follows_algorithm1_history(mfcg, mode, precision):
+    # the Eq. 8 estimate gamma_{k+1} = gamma - 2 alpha b + alpha^2 c after k
+    # iterations equals Algorithm 1's explicit ||r_k||^2 until the last
+    # iterations (here far from convergence)
+    p, cells = 3, (4, 3, 5)
+    op = _oracle_problem(p, cells)
+    A = fem.assemble(op)
+    b = inputs.boundary_zeroed(inputs.random_vector(op.n_dofs, salt=11), op.nodes_per_dim)
+    ref = ocg.pcg_algorithm1(lambda v: A @ v, b, 1.0 / A.diagonal(), 0.0, 12)
+    prob = _gpu_problem(mfcg, p, cells, mode=mode, precision=precision)
+    bd = _to_dev(prob, b)
+    for k in (1, 2, 3, 5, 8, 12):
+        _, info = prob.cg_solve(bd, rtol=0.0, maxit=k)
+        assert abs(info["residual_sq_est"] - ref.residual_sq_history[k - 1]) <= 1e-9 * ref.residual_sq_history[k - 1]
+    prob.close()
