@@ -1291,8 +1291,9 @@ __device__ inline void cg_scalar_step(CGState* st, const double (&s)[7]) {
   prepare_iteration_scalars(st);
 }
 
+// three CTAs per SM (at most 85 registers) keep more of the tail's loads in flight
 template <int P, int MODE, int PREC>
-__global__ void __launch_bounds__(kThreads) tail_kernel(const TileArgs a) {
+__global__ void __launch_bounds__(kThreads, 3) tail_kernel(const TileArgs a) {
   using T = typename Num<PREC>::T;
   __shared__ double red[8 * (kThreads / 32)];
   __shared__ int is_last;
