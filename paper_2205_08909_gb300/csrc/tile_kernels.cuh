@@ -796,9 +796,13 @@ __device__ __forceinline__ int64_t brick_global_index(const TileGeom& g, int tx,
 }
 
 // FP32 tiles run three CTAs per SM (their shared memory allows it): keep their
-// registers within 85 per thread
+// registers within 85 per thread.  The others pass 0, which leaves the register
+// target to the compiler as a bound without the argument does; a minimum of
+// one CTA per SM instead lets it use up to 255 registers, which halved the
+// resident CTAs of many degree/mode combinations (degree 5 double-float: 150
+// instead of 128 registers, 44% slower)
 template <int P, int MODE, int GEOM, int PREC, int NC>
-__global__ void __launch_bounds__(kThreads, PREC == PREC_F32 ? 3 : 1)
+__global__ void __launch_bounds__(kThreads, PREC == PREC_F32 ? 3 : 0)
     tile_kernel(const TileArgs a_all, const OperatorCoeffs c) {
   using T = typename Num<PREC>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
