@@ -77,8 +77,7 @@ struct mfcg_problem {
   int64_t fam[3] = {0, 0, 0};
   TailDiv tdiv{};
   int tail_ctas = 1;
-  int ahead_cg = 0;  // prefetch distance (tiles) of the fused CG and operator passes
-  int ahead_op = 0;
+  int ahead_op = 0;  // L2 prefetch distance (tiles) of the operator passes
   int graph_iters = 16;
   cudaGraphExec_t graph_fused = nullptr;
   cudaGraphExec_t graph_unfused = nullptr;
@@ -173,8 +172,7 @@ int run_pass(mfcg_problem* P, int mode, const double* src, double* dst, bool fp6
 // one fused CG iteration of the given parity (odd: buffers 0 -> 1)
 int enqueue_fused_iteration(mfcg_problem* P, int odd, cudaEvent_t t0, cudaEvent_t t1) {
   const int o = odd ? 0 : 1, n = odd ? 1 : 0;
-  TileArgs a = base_args(P, P->cg_prec, P->geo_cg);
-  a.prefetch_ahead = P->ahead_cg;
+  TileArgs a = base_args(P, P->cg_prec, P->geo_cg);  // no look-ahead prefetch (prefetch_ahead 0)
   a.in0 = P->r[o];
   a.in1 = P->v[o];
   a.in2 = P->p[o];
@@ -970,7 +968,6 @@ int setup_impl(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, con
   // (the fused CG kernel has no look-ahead prefetch)
   int n_sm = 0;
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, P->device);
-  P->ahead_cg = 0;
   P->ahead_op = n_sm * tile_occupancy(degree, MODE_OPERATOR, P->geom_kind, P->op_prec, P->ncomp,
                                       tile_smem_bytes(degree, P->geom_kind, P->op_prec, g, MODE_OPERATOR));
   P->tail_nodes = P->fam[0] + P->fam[1] + P->fam[2];
