@@ -311,7 +311,8 @@ def run_reference(args, world, rank):
     sample = (f"oracle Algorithm 1 (assembled CSR, scipy SpMV) on Q{w.degree} {cells}^3 Cartesian "
               f"({n} DoFs), {args.ref_iters} fixed iterations per step, same degree as {w.name}")
     return {
-        "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": 0,
+        # n_gpus: the launch configuration of this arm (the oracle itself runs on rank 0's host cores)
+        "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * sum(secs) / len(secs), 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w.name, "degree": w.degree, "cells": list(w.cells), "sample_cells": [cells] * 3},
