@@ -60,3 +60,28 @@ def test_setup_rejects_invalid_arguments_before_touching_the_gpu():
     assert lib.mfcg_setup(ctypes.byref(too_big), 2, ctypes.byref(g2), None, None, ctypes.byref(h)) == 1
     assert lib.mfcg_n_dofs(None, None) == 1
     assert lib.mfcg_destroy(None) == 0
+
+
+def test_binding_structs_match_the_c_header(tmp_path):
+    """The ctypes mirrors of mfcg_mesh, mfcg_geometry, mfcg_options and
+    mfcg_solve_info have the header's size and field offsets."""
+    from paper_2205_08909_gb300 import _binding as b
+
+    structs = {"mfcg_mesh": b.Mesh, "mfcg_geometry": b.Geometry, "mfcg_options": b.Options,
+               "mfcg_solve_info": b.SolveInfo}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "mfcg.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for field, _ in py._fields_:
+            lines.append(f'  printf("{cname} {field} %zu\\n", offsetof({cname}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", f"-I{os.path.join(ROOT, 'include')}", str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {tuple(ln.split()[:2]): int(ln.split()[2]) for ln in out if ln.strip()}
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for field, _ in py._fields_:
+            assert got[(cname, field)] == getattr(py, field).offset, (cname, field)
