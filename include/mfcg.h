@@ -190,8 +190,9 @@ int mfcg_diagonal(mfcg_problem* prob, double* diag);
 /* mfcg_rhs -- right-hand side b_i = int f phi_i for the manufactured solution
  * u = sin(pi x) sin(pi y) sin(pi z) (f = -div(a grad u)), same Gauss rule,
  * 0 on Dirichlet nodes; for MFCG_OP_MASS the right-hand side of the same u
- * (f = a u).  Not defined for MFCG_GEOM_USER (INVALID_ARG).  b: device, n doubles.  With components > 1, component c holds the
- * right-hand side of u_c = (c + 1) u.  Asynchronous. */
+ * (f = a u).  Not defined for MFCG_GEOM_USER (INVALID_ARG).  b: device, n
+ * doubles.  With components > 1, component c holds the right-hand side of
+ * u_c = (c + 1) u.  Asynchronous. */
 int mfcg_rhs(mfcg_problem* prob, double* b);
 
 /* mfcg_cg_solve -- Jacobi-preconditioned CG from the initial guess in x
@@ -212,8 +213,12 @@ int mfcg_cg_solve(mfcg_problem* prob, const double* b, double* x, double rtol, i
                   mfcg_solve_info* info);
 
 /* mfcg_cg_solve_host -- the same solve with HOST arrays (pinned memory gives
- * asynchronous copies): b is copied to a library-owned device buffer, x is
- * copied in and the solution copied back before return. */
+ * asynchronous copies): b is copied to a library-owned device buffer (allocated
+ * on the first call, freed by mfcg_destroy), x is copied in and the solution
+ * copied back before return (also after NOT_CONVERGED or BREAKDOWN).
+ *   b_host in: n doubles; x_host in/out: n doubles; info out: may be NULL.
+ * Errors: those of mfcg_cg_solve; INVALID_ARG for NULL arrays, maxit < 0 or
+ * rtol < 0; OUT_OF_MEMORY when the device buffers cannot be allocated. */
 int mfcg_cg_solve_host(mfcg_problem* prob, const double* b_host, double* x_host, double rtol, int maxit,
                        mfcg_solve_info* info);
 
