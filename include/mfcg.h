@@ -248,7 +248,12 @@ int mfcg_destroy(mfcg_problem* prob);
  * are rejected with MFCG_SCRATCH_TOO_SMALL before any GPU work.  The first call
  * on a device looks up the array's device address (cudaGetSymbolAddress) and
  * sets the kernel's shared-memory limit; make that first call before any
- * stream capture.  All calls share the array: calls that overlap on the GPU
+ * stream capture.  These per-device results are kept for the life of the
+ * process: after cudaDeviceReset (or anything else that destroys and recreates
+ * the device's primary context) the cached address is stale, so do not use
+ * this entry point across a device reset.  The launches are those of
+ * mfcg_apply_operator, including its L2 look-ahead prefetch; a tile whose
+ * shared memory exceeds the device's limit is rejected with INVALID_ARG.  All calls share the array: calls that overlap on the GPU
  * (concurrent streams, other host threads) race and give wrong results; every
  * value read from the array is written earlier in the same call, so nothing
  * needs clearing between calls.  Asynchronous on cuda_stream.  Errors:

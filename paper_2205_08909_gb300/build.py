@@ -8,7 +8,9 @@ from __future__ import annotations
 
 import concurrent.futures
 import glob
+import hashlib
 import os
+import platform
 import shutil
 import subprocess
 import sys
@@ -33,19 +35,43 @@ def _sources() -> list[str]:
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
-def _up_to_date() -> bool:
-    if not os.path.exists(LIB):
-        return False
-    t = os.path.getmtime(LIB)
+def _deps() -> list[str]:
     deps = _sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh"))
     deps.append(os.path.join(PKG, "..", "include", "mfcg.h"))
-    return all(os.path.getmtime(d) <= t for d in deps if os.path.exists(d))
+    return sorted(os.path.abspath(d) for d in deps if os.path.exists(d))
+
+
+def _source_hash() -> str:
+    """SHA-256 over the compiler flags and the name and content of every source
+    and header: the library is rebuilt whenever it differs from the hash stored
+    beside it, whatever the files' modification times (a library copied in with
+    the tree is never trusted)."""
+    h = hashlib.sha256()
+    h.update(" ".join(ARCH + FLAGS).encode())
+    for d in _deps():
+        h.update(os.path.relpath(d, PKG).encode())
+        with open(d, "rb") as fh:
+            h.update(fh.read())
+    h.update(platform.machine().encode())
+    return h.hexdigest()
+
+
+STAMP = LIB + ".sha256"
+
+
+def _up_to_date() -> bool:
+    if not os.path.exists(LIB) or not os.path.exists(STAMP):
+        return False
+    with open(STAMP) as fh:
+        return fh.read().strip() == _source_hash()
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and _up_to_date():
         return LIB
     nvcc = _nvcc()
+    if os.path.exists(STAMP):
+        os.remove(STAMP)
     os.makedirs(LIBDIR, exist_ok=True)
     os.makedirs(BUILD, exist_ok=True)
 
@@ -68,6 +94,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stderr}")
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as fh:
+        fh.write(_source_hash() + "\n")
     return LIB
 
 

@@ -33,6 +33,9 @@ static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBy
 constexpr int kMaxDevices = 64;
 void* g_scratch_addr[kMaxDevices] = {};
 size_t g_smem_set[kMaxDevices][kMaxDegree + 1] = {};
+int g_ahead[kMaxDevices][kMaxDegree + 1];  // prefetch distance per device and degree, -1 = not yet queried
+int g_max_smem[kMaxDevices] = {};
+int g_n_sm[kMaxDevices] = {};
 std::mutex g_mutex;
 
 // default tile edge per degree of affine problems (the table mfcg_setup uses)
@@ -41,15 +44,31 @@ int default_affine_tile(int p) {
   return t[p];
 }
 
+// shared memory of the kernel's launch, and whether it fits the device's opt-in limit
 template <int P>
-cudaError_t launch_static_operator(const TileArgs& a, const OperatorCoeffs& c, cudaStream_t s, size_t& smem_set) {
+size_t static_operator_smem(const TileGeom& g) {
+  return tile_smem_elems(P, GEOM_AFFINE, (int)sizeof(double), g, MODE_OPERATOR) * sizeof(double);
+}
+
+template <int P>
+cudaError_t launch_static_operator(TileArgs& a, const OperatorCoeffs& c, cudaStream_t s, size_t& smem_set,
+                                   int n_sm, int& ahead) {
   auto tile = tile_kernel<P, MODE_OPERATOR, GEOM_AFFINE, PREC_F64, 1>;
-  const size_t smem = tile_smem_elems(P, GEOM_AFFINE, (int)sizeof(double), a.g, MODE_OPERATOR) * sizeof(double);
+  const size_t smem = static_operator_smem<P>(a.g);
   if (smem > smem_set) {
     const cudaError_t e = cudaFuncSetAttribute(tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     smem_set = smem;
   }
+  if (ahead < 0) {
+    // L2 look-ahead prefetch distance of the regular operator pass: the CTAs
+    // resident in one wave (an occupancy query allocates nothing)
+    int occ = 0;
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tile, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    ahead = n_sm * occ;
+  }
+  a.prefetch_ahead = ahead;
   tile<<<(unsigned)a.g.n_tiles, kThreads, smem, s>>>(a, c);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -78,10 +97,32 @@ extern "C" int mfcg_apply_operator_static(const mfcg_mesh* mesh, int degree, con
 
   std::lock_guard<std::mutex> lock(g_mutex);
   if (!g_scratch_addr[dev]) {
-    // first call on this device: the device address of the static array
+    // first call on this device: the device address of the static array and
+    // the device limits (none of these queries allocates)
     void* ptr = nullptr;
     if (cudaGetSymbolAddress(&ptr, g_static_scratch) != cudaSuccess || !ptr) return MFCG_CUDA_ERROR;
+    if (cudaDeviceGetAttribute(&g_max_smem[dev], cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&g_n_sm[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return MFCG_CUDA_ERROR;
+    for (int q = 0; q <= kMaxDegree; ++q) g_ahead[dev][q] = -1;
     g_scratch_addr[dev] = ptr;
+  }
+  // a tile that does not fit the shared memory of one CTA is an argument
+  // error, as in mfcg_setup (the static shared arrays of the kernel included)
+  {
+    const size_t static_smem = 8 * (kThreads / 32) * sizeof(double) + 2 * kMaxColorCells * sizeof(int);
+    size_t smem = 0;
+    switch (degree) {
+      case 1: smem = static_operator_smem<1>(a.g); break;
+      case 2: smem = static_operator_smem<2>(a.g); break;
+      case 3: smem = static_operator_smem<3>(a.g); break;
+      case 4: smem = static_operator_smem<4>(a.g); break;
+      case 5: smem = static_operator_smem<5>(a.g); break;
+      case 6: smem = static_operator_smem<6>(a.g); break;
+      case 7: smem = static_operator_smem<7>(a.g); break;
+      case 8: smem = static_operator_smem<8>(a.g); break;
+    }
+    if (smem + static_smem > (size_t)g_max_smem[dev]) return MFCG_INVALID_ARG;
   }
   a.tail_nodes = a.fam[0] + a.fam[1] + a.fam[2];
   const int64_t ctas = (a.tail_nodes + 4 * kThreads - 1) / (4 * kThreads);
@@ -100,16 +141,18 @@ extern "C" int mfcg_apply_operator_static(const mfcg_mesh* mesh, int degree, con
   build_coeffs(degree, h, 0.0, MFCG_COEF_CONSTANT, c);
   const cudaStream_t s = (cudaStream_t)cuda_stream;
   size_t& smem_set = g_smem_set[dev][degree];
+  int& ahead = g_ahead[dev][degree];
+  const int n_sm = g_n_sm[dev];
   cudaError_t e = cudaErrorInvalidValue;
   switch (degree) {
-    case 1: e = launch_static_operator<1>(a, c, s, smem_set); break;
-    case 2: e = launch_static_operator<2>(a, c, s, smem_set); break;
-    case 3: e = launch_static_operator<3>(a, c, s, smem_set); break;
-    case 4: e = launch_static_operator<4>(a, c, s, smem_set); break;
-    case 5: e = launch_static_operator<5>(a, c, s, smem_set); break;
-    case 6: e = launch_static_operator<6>(a, c, s, smem_set); break;
-    case 7: e = launch_static_operator<7>(a, c, s, smem_set); break;
-    case 8: e = launch_static_operator<8>(a, c, s, smem_set); break;
+    case 1: e = launch_static_operator<1>(a, c, s, smem_set, n_sm, ahead); break;
+    case 2: e = launch_static_operator<2>(a, c, s, smem_set, n_sm, ahead); break;
+    case 3: e = launch_static_operator<3>(a, c, s, smem_set, n_sm, ahead); break;
+    case 4: e = launch_static_operator<4>(a, c, s, smem_set, n_sm, ahead); break;
+    case 5: e = launch_static_operator<5>(a, c, s, smem_set, n_sm, ahead); break;
+    case 6: e = launch_static_operator<6>(a, c, s, smem_set, n_sm, ahead); break;
+    case 7: e = launch_static_operator<7>(a, c, s, smem_set, n_sm, ahead); break;
+    case 8: e = launch_static_operator<8>(a, c, s, smem_set, n_sm, ahead); break;
   }
   return e == cudaSuccess ? MFCG_OK : MFCG_CUDA_ERROR;
 }

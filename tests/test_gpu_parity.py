@@ -334,10 +334,11 @@ def test_defect_correction_on_deformed_mesh(mfcg):
     ref.close()
 
 
-@pytest.mark.parametrize("precision", ["fp32_inner", "double_float"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32_inner", "double_float"])
 def test_full_size_q4_128cube_solve(mfcg, precision):
-    # FP32-inner defect correction (and the double-float CG) at 135M unknowns
-    # against the exact discrete solution by fast diagonalisation
+    # the fused FP64 CG, the FP32-inner defect correction and the double-float
+    # CG at 135M unknowns against the exact discrete solution by fast
+    # diagonalisation
     w = inputs.WORKLOADS["q4_128cube"]
     op = _oracle_problem(w.degree, w.cells)
     prob = mfcg.Problem(w.degree, w.cells, precision=precision)
@@ -353,8 +354,89 @@ def test_full_size_q4_128cube_solve(mfcg, precision):
     # the defect correction meets the tolerance on the true FP64 residual; the
     # double-float recurrence stops at rtol on its own residual, whose true
     # counterpart sits above it by the ~2^-44 rounding of the pair arithmetic
-    bound = 1.5e-10 if precision == "fp32_inner" else 5e-10
+    bound = 5e-10 if precision == "double_float" else 1.5e-10
     assert np.linalg.norm(r) <= bound * np.linalg.norm(bh)
+
+
+def _q6_48_rows(op, count):
+    """Random rows plus nodes on tile faces, edges and corners (tiles of 2
+    cells, 12 nodes) and next to the Dirichlet boundary."""
+    n1 = op.nodes_per_dim[0]
+    rows = list(inputs.random_rows(op.n_dofs, count, salt=7))
+    for (i, j, k) in ((12, 12, 12), (12, 13, 14), (24, 12, 7), (1, 1, 12), (287, 12, 24), (1, 1, 1),
+                      (287, 287, 287), (144, 144, 12), (36, 48, 60), (11, 12, 13), (13, 11, 12)):
+        rows.append(i + n1 * (j + n1 * k))
+    return np.unique(np.array(rows))
+
+
+def test_full_size_q6_48cube_deformed_solve(mfcg):
+    # Q6 on the deformed 48^3 mesh with the variable coefficient (24.1M
+    # unknowns): the fused FP64 CG to rtol 1e-10.  Its true residual is formed
+    # with the FP64 operator, whose rows are checked against the oracle's
+    # (sampled, >= 200 rows including tile faces, edges and corners); the
+    # double-float CG and the FP32-inner defect correction reach the same
+    # solution.
+    w = inputs.WORKLOADS["q6_48cube_deformed"]
+    op = _oracle_problem(w.degree, w.cells, w.amplitude, w.coefficient)
+    prob = _gpu_problem(mfcg, w.degree, w.cells, w.amplitude, w.coefficient, true_residual=1)
+    b = prob.rhs()
+    x, info = prob.cg_solve(b, rtol=1e-10, maxit=20000)
+    assert info["converged"]
+    assert info["true_residual_sq"] <= (1.5e-10) ** 2 * info["rhs_norm_sq"]
+    ax = _to_host(prob, prob.apply_operator(x))
+    xh = _to_host(prob, x)
+    bh = _to_host(prob, b)
+    rows = _q6_48_rows(op, 220)
+    assert len(rows) >= 200
+    ref = fem.apply_rows(op, xh, rows)
+    # A x ~ b is a sum of much larger terms of both signs: the operator's
+    # rounding is measured against the size of the terms (diagonal x max |x|)
+    term = np.abs(fem.diagonal_rows(op, rows)).max() * np.abs(xh).max()
+    assert np.abs(ax[rows] - ref).max() <= OP_TOL * term
+    # the sampled rows of the residual stay within the norm bound
+    assert np.abs(bh[rows] - ref).max() <= 1.5e-10 * np.linalg.norm(bh)
+    prob.close()
+    for precision in ("double_float", "fp32_inner"):
+        other = _gpu_problem(mfcg, w.degree, w.cells, w.amplitude, w.coefficient, precision=precision)
+        xo, info_o = other.cg_solve(other.rhs(), rtol=1e-10, maxit=20000)
+        assert info_o["converged"]
+        assert _rel(_to_host(other, xo), xh) <= SOL_TOL
+        other.close()
+
+
+RANDOM_RHS_CASES = [
+    (2, (6, 5, 7), 0.0, "constant"),
+    (4, (4, 5, 3), 0.0, "constant"),
+    (3, (3, 4, 3), 0.05, "sin_x"),
+    (5, (2, 3, 2), 0.08, "constant"),
+]
+
+
+@pytest.mark.parametrize("mode,precision", SOLVER_VARIANTS)
+@pytest.mark.parametrize("p,cells,amp,coef", RANDOM_RHS_CASES)
+def test_random_rhs_solve_matches_algorithm1(mfcg, mode, precision, p, cells, amp, coef):
+    # a standard-normal right-hand side (zero on the boundary) excites every
+    # mode, so the solve takes many iterations and exercises the recurrences
+    # of Algorithm 5 (Eqs. 7-8) throughout; iterates are compared with
+    # Algorithm 1's after the same number of products A p
+    op = _oracle_problem(p, cells, amp, coef)
+    A = fem.assemble(op)
+    b = inputs.boundary_zeroed(inputs.random_vector(op.n_dofs, salt=17 + p), op.nodes_per_dim)
+    dinv = 1.0 / A.diagonal()
+    ref = ocg.pcg_algorithm1(lambda v: A @ v, b, dinv, 1e-10, 5000)
+    assert ref.converged and ref.iterations >= 20
+    prob = _gpu_problem(mfcg, p, cells, amp, coef, mode=mode, precision=precision)
+    x, info = prob.cg_solve(_to_dev(prob, b), rtol=1e-10, maxit=5000)
+    assert info["converged"] == 1
+    xh = _to_host(prob, x)
+    if precision == "fp32_inner":
+        assert np.linalg.norm(b - A @ xh) < 1e-10 * np.linalg.norm(b)
+        assert _rel(xh, ref.x) <= SOL_TOL
+    else:
+        assert abs(info["iterations"] - ref.iterations) <= 1
+        same = ocg.pcg_algorithm1(lambda v: A @ v, b, dinv, 0.0, info["iterations"])
+        assert _rel(xh, same.x) <= SOL_TOL
+    prob.close()
 
 
 BATCH_SPECS = [
