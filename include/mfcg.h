@@ -113,6 +113,19 @@ typedef enum mfcg_precision {
                                  inner_rtol per cycle, x updated in FP64; FUSED mode only             */
 } mfcg_precision;
 
+/* How FP64 operator contractions run on Cartesian (MFCG_GEOM_AFFINE) problems. */
+typedef enum mfcg_fp64_contraction {
+  MFCG_FP64_TENSOR_CORES = 0, /* default: the even-odd blocks of the cell matrix of Eq. 5 as dense products
+                                 on the FP16 tensor cores, FP64 data and matrix split exactly into 8-bit
+                                 digits of 64-bit fixed-point integers (one exponent per tile), the digit
+                                 products summed exactly and recombined in 64-bit integers; results
+                                 within a few units of 2^-53 of each tile's largest entry, as native FP64.
+                                 Used at degrees 1-5 and 7 where its shared-memory staging fits (always
+                                 with the default tiles); the FP64 sweeps serve degrees 6 and 8 and
+                                 tiles too large for the staging                                        */
+  MFCG_FP64_PIPE = 1          /* whole-brick sum-factorisation sweeps in native FP64 on the FP64 pipe      */
+} mfcg_fp64_contraction;
+
 typedef struct mfcg_options {
   int32_t mode;             /* mfcg_mode                                                            */
   int32_t graph_iterations; /* CG iterations per captured CUDA graph (even; 0 = 16)                   */
@@ -135,6 +148,9 @@ typedef struct mfcg_options {
                                iteration (FUSED and SEMI_FUSED; the same iterates in exact arithmetic) */
   int32_t true_residual;    /* 1: after a solve, form ||b - A x||^2 with the FP64 operator
                                (mfcg_solve_info.true_residual_sq)                                     */
+  int32_t fp64_contraction; /* mfcg_fp64_contraction: the FP64 operator of Cartesian problems (the FP64
+                               precision's operator and fused iterations, and the FP64 residuals of the
+                               other precisions); ignored on deformed meshes                          */
 } mfcg_options;
 
 typedef struct mfcg_solve_info {
@@ -244,7 +260,7 @@ int mfcg_destroy(mfcg_problem* prob);
  * The call allocates nothing: its only scratch, the partial sums of the nodes
  * shared between tiles, lives in one fixed 16 MiB array of device memory that
  * every GPU loading the library holds until the process exits.  Meshes whose
- * scratch exceeds it (for example Q4 beyond about 42^3 cells, Q2 beyond 84^3)
+ * scratch exceeds it (for example Q4 beyond about 40^3 cells, Q2 beyond 84^3)
  * are rejected with MFCG_SCRATCH_TOO_SMALL before any GPU work.  The first call
  * on a device looks up the array's device address (cudaGetSymbolAddress) and
  * sets the kernel's shared-memory limit; make that first call before any
@@ -252,8 +268,10 @@ int mfcg_destroy(mfcg_problem* prob);
  * process: after cudaDeviceReset (or anything else that destroys and recreates
  * the device's primary context) the cached address is stale, so do not use
  * this entry point across a device reset.  The launches are those of
- * mfcg_apply_operator, including its L2 look-ahead prefetch; a tile whose
- * shared memory exceeds the device's limit is rejected with INVALID_ARG.  All calls share the array: calls that overlap on the GPU
+ * mfcg_apply_operator with mfcg_options.fp64_contraction = MFCG_FP64_PIPE (the
+ * FP64 sweeps), including its L2 look-ahead prefetch; a tile whose shared
+ * memory exceeds the device's limit is rejected with INVALID_ARG.  All calls
+ * share the array: calls that overlap on the GPU
  * (concurrent streams, other host threads) race and give wrong results; every
  * value read from the array is written earlier in the same call, so nothing
  * needs clearing between calls.  Asynchronous on cuda_stream.  Errors:

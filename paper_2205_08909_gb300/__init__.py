@@ -55,7 +55,7 @@ class Problem:
                  preconditioner: str = "jacobi", inner_rtol: float = 0.0, graph_iterations: int = 0,
                  instrument: bool = False, tile=None, components: int = 1, operator: str = "laplace",
                  user_data=None, x_every_iteration: bool = False, true_residual: bool = False,
-                 stream: torch.cuda.Stream | None = None):
+                 fp64_contraction: str = "tensor_cores", stream: torch.cuda.Stream | None = None):
         if not torch.cuda.is_available():
             raise RuntimeError("paper_2205_08909_gb300 needs a CUDA device (no CPU fallback)")
         self._lib = _binding.load()
@@ -84,6 +84,7 @@ class Problem:
         opt.operator_kind = _binding.OPERATOR[operator]
         opt.x_update_every_iteration = 1 if x_every_iteration else 0
         opt.true_residual = 1 if true_residual else 0
+        opt.fp64_contraction = _binding.FP64_CONTRACTION[fp64_contraction]
         self.components = int(components)
         if tile is not None:
             for d in range(3):

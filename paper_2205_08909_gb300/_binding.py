@@ -25,6 +25,7 @@ MODE = {"fused": 0, "unfused": 1, "semi_fused": 2}
 PRECONDITIONER = {"jacobi": 0, "none": 1}
 PRECISION = {"fp64": 0, "double_float": 1, "fp32_inner": 2}
 OPERATOR = {"laplace": 0, "mass": 1}
+FP64_CONTRACTION = {"tensor_cores": 0, "fp64_pipe": 1}
 
 
 class Mesh(ctypes.Structure):
@@ -39,7 +40,8 @@ class Options(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("graph_iterations", ctypes.c_int32), ("instrument", ctypes.c_int32),
                 ("tile", ctypes.c_int32 * 3), ("precision", ctypes.c_int32), ("preconditioner", ctypes.c_int32),
                 ("inner_rtol", ctypes.c_double), ("components", ctypes.c_int32), ("operator_kind", ctypes.c_int32),
-                ("x_update_every_iteration", ctypes.c_int32), ("true_residual", ctypes.c_int32)]
+                ("x_update_every_iteration", ctypes.c_int32), ("true_residual", ctypes.c_int32),
+                ("fp64_contraction", ctypes.c_int32)]
 
 
 class SolveInfo(ctypes.Structure):

@@ -21,6 +21,7 @@
 
 #include "mfcg_internal.h"
 #include "precision.cuh"
+#include "tc_operator.cuh"
 
 struct mfcg_problem;
 int setup_impl(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, const mfcg_options* opt,
@@ -49,6 +50,12 @@ struct mfcg_problem {
   int op_kind = OP_LAPLACE;
   int op_prec = PREC_F64;  // apply_operator and FP64-accurate residuals
   int cg_prec = PREC_F64;  // fused CG iterations
+  // FP64 operator passes and fused iterations of Cartesian problems with the
+  // contractions on the tensor cores (PREC_F64TC in place of PREC_F64)
+  bool tc = false;
+  uint2* tc_frag = nullptr;
+  int tc_g2 = 0;
+  int tc_r = 64;
   // fused CG vectors in the storage type of cg_prec (ping-pong r, p, v), x, M^{-1}
   void* r[2] = {nullptr, nullptr};
   void* p[2] = {nullptr, nullptr};
@@ -134,8 +141,17 @@ int default_tile(int p, int geom, int precision = MFCG_PREC_FP64) {
   return geom == GEOM_AFFINE ? affine[p] : deformed[p];
 }
 
-TileArgs base_args(const mfcg_problem* P, int prec, const void* geo) {
+// arguments of a tile / tail launch in precision prec; the operator passes and
+// fused iterations of FP64 run on the tensor-core operator when the problem has
+// it (the set-up passes, MODE_RHS and MODE_DIAG, stay on PREC_F64)
+TileArgs base_args(const mfcg_problem* P, int prec, const void* geo, int mode) {
   TileArgs a{};
+  if (prec == PREC_F64 && P->tc && (mode == MODE_OPERATOR || mode == MODE_CG)) {
+    prec = PREC_F64TC;
+    a.tc_frag = P->tc_frag;
+    a.tc_g2 = P->tc_g2;
+    a.tc_r = P->tc_r;
+  }
   a.g = P->g;
   a.shell = P->shell;
   a.partial = P->partial;
@@ -158,7 +174,7 @@ TileArgs base_args(const mfcg_problem* P, int prec, const void* geo) {
 // forces the FP64 operator (true residuals) whatever the operator precision
 int run_pass(mfcg_problem* P, int mode, const double* src, double* dst, bool fp64_operator = false) {
   const int prec = mode == MODE_OPERATOR && !fp64_operator ? P->op_prec : PREC_F64;
-  TileArgs a = base_args(P, prec, mode == MODE_OPERATOR && !fp64_operator ? P->geo_op : P->geo);
+  TileArgs a = base_args(P, prec, mode == MODE_OPERATOR && !fp64_operator ? P->geo_op : P->geo, mode);
   if (mode != MODE_OPERATOR) a.ncomp = 1;  // diagonal and right-hand side of the scalar operator
   a.prefetch_ahead = mode == MODE_OPERATOR && prec == P->op_prec ? P->ahead_op : 0;
   a.in0 = src;
@@ -172,7 +188,7 @@ int run_pass(mfcg_problem* P, int mode, const double* src, double* dst, bool fp6
 // one fused CG iteration of the given parity (odd: buffers 0 -> 1)
 int enqueue_fused_iteration(mfcg_problem* P, int odd, cudaEvent_t t0, cudaEvent_t t1) {
   const int o = odd ? 0 : 1, n = odd ? 1 : 0;
-  TileArgs a = base_args(P, P->cg_prec, P->geo_cg);  // no look-ahead prefetch (prefetch_ahead 0)
+  TileArgs a = base_args(P, P->cg_prec, P->geo_cg, MODE_CG);  // no look-ahead prefetch (prefetch_ahead 0)
   a.in0 = P->r[o];
   a.in1 = P->v[o];
   a.in2 = P->p[o];
@@ -206,7 +222,7 @@ int enqueue_unfused_iteration(mfcg_problem* P, cudaEvent_t t0, cudaEvent_t t1) {
   UnfusedArgs u = unfused_args(P);
   if (t0) CK(cudaEventRecord(t0, P->exec));
   // v = A p
-  TileArgs a = base_args(P, P->op_prec, P->geo_op);
+  TileArgs a = base_args(P, P->op_prec, P->geo_op, MODE_OPERATOR);
   a.prefetch_ahead = P->ahead_op;
   a.in0 = u.p;
   a.out0 = u.v;
@@ -227,7 +243,7 @@ int enqueue_unfused_iteration(mfcg_problem* P, cudaEvent_t t0, cudaEvent_t t1) {
 int enqueue_semi_iteration(mfcg_problem* P, cudaEvent_t t0, cudaEvent_t t1) {
   const int64_t n = P->nv();
   CK(launch_semi_pre(n, P->state, P->x, P->ur, P->up, P->uv, P->diag_inv, P->exec));
-  TileArgs a = base_args(P, P->op_prec, P->geo_op);
+  TileArgs a = base_args(P, P->op_prec, P->geo_op, MODE_OPERATOR);
   a.prefetch_ahead = P->ahead_op;
   a.in0 = P->up;
   a.out0 = P->uv;
@@ -914,6 +930,7 @@ int setup_impl(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, con
     return MFCG_INVALID_ARG;
   if (o.operator_kind != MFCG_OP_LAPLACE && o.operator_kind != MFCG_OP_MASS) return MFCG_INVALID_ARG;
   if (o.operator_kind == MFCG_OP_MASS && geom->kind == MFCG_GEOM_DEFORMED_TENSOR) return MFCG_INVALID_ARG;
+  if (o.fp64_contraction != MFCG_FP64_TENSOR_CORES && o.fp64_contraction != MFCG_FP64_PIPE) return MFCG_INVALID_ARG;
   if (o.tile[0] == -1 && o.tile[1] == -1 && o.tile[2] == -1) return setup_autotuned(mesh, degree, geom, o, cuda_stream, out);
   for (int d = 0; d < 3; ++d)
     if (o.tile[d] < 0 || o.tile[d] > 16) return MFCG_INVALID_ARG;
@@ -954,13 +971,22 @@ int setup_impl(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, con
     T[d] = o.tile[d] ? o.tile[d] : default_tile(degree, P->geom_kind, o.precision);
     if (degree == 1 && T[d] < 2) T[d] = 2;
   }
+  // FP64 on the tensor cores at degree 4: 4 x 4 x 3-cell tiles, whose bricks
+  // and staging fit two CTAs per SM (4^3 fits one)
+  if (degree == 4 && P->geom_kind == GEOM_AFFINE && o.precision == MFCG_PREC_FP64 &&
+      o.fp64_contraction == MFCG_FP64_TENSOR_CORES && o.tile[2] == 0)
+    T[2] = 3;
   init_tile_geom(degree, N, T, g, P->fam, &P->tdiv);
   int max_smem = 0;
   cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device);
-  const int precs[3] = {PREC_F64, P->op_prec, P->cg_prec};
+  const size_t static_smem = 8 * (kThreads / 32) * sizeof(double) + 2 * 512 * sizeof(int);
+  // the tensor-core contractions where their staging fits next to the node
+  // bricks (with the default tiles: degrees 1 to 7), else the FP64 sweeps
+  P->tc = P->geom_kind == GEOM_AFFINE && o.fp64_contraction == MFCG_FP64_TENSOR_CORES && tc::tc_degree(degree) &&
+          tile_smem_bytes(degree, P->geom_kind, PREC_F64TC, g) + static_smem <= (size_t)max_smem;
+  const int precs[4] = {PREC_F64, P->op_prec, P->cg_prec, P->tc ? PREC_F64TC : PREC_F64};
   for (int pr : precs) {
     const size_t smem = tile_smem_bytes(degree, P->geom_kind, pr, g);
-    const size_t static_smem = 8 * (kThreads / 32) * sizeof(double) + 2 * 512 * sizeof(int);
     if (smem + static_smem > (size_t)max_smem) return fail(MFCG_INVALID_ARG);
     if (prepare_tile(degree, P->geom_kind, pr, smem) != cudaSuccess) return fail(MFCG_CUDA_ERROR);
   }
@@ -968,14 +994,23 @@ int setup_impl(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, con
   // (the fused CG kernel has no look-ahead prefetch)
   int n_sm = 0;
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, P->device);
-  P->ahead_op = n_sm * tile_occupancy(degree, MODE_OPERATOR, P->geom_kind, P->op_prec, P->ncomp,
-                                      tile_smem_bytes(degree, P->geom_kind, P->op_prec, g, MODE_OPERATOR));
+  const int op_launch_prec = P->tc && P->op_prec == PREC_F64 ? PREC_F64TC : P->op_prec;
+  P->ahead_op = n_sm * tile_occupancy(degree, MODE_OPERATOR, P->geom_kind, op_launch_prec, P->ncomp,
+                                      tile_smem_bytes(degree, P->geom_kind, op_launch_prec, g, MODE_OPERATOR));
   P->tail_nodes = P->fam[0] + P->fam[1] + P->fam[2];
   // about four shared-face nodes per tail thread (two iterations of two)
   P->tail_ctas = (int)std::min<int64_t>(std::max<int64_t>((P->tail_nodes + 4 * kThreads - 1) / (4 * kThreads), 1), 152 * 16);
 
   const double h[3] = {1.0 / N[0], 1.0 / N[1], 1.0 / N[2]};
   build_coeffs(degree, h, mesh->amplitude, geom->coefficient, P->c);
+  if (P->tc) {
+    // digit fragments of the cell matrix for the tensor-core operator
+    std::vector<uint2> frag;
+    if (build_tc_fragments(degree, P->c, P->op_kind, frag, P->tc_g2, P->tc_r) != 0) return fail(MFCG_INVALID_ARG);
+    if ((st = alloc_bytes(P, &P->tc_frag, (int64_t)(frag.size() * sizeof(uint2)))) != MFCG_OK) return fail(st);
+    if (cudaMemcpy(P->tc_frag, frag.data(), frag.size() * sizeof(uint2), cudaMemcpyHostToDevice) != cudaSuccess)
+      return fail(MFCG_CUDA_ERROR);
+  }
 
   const int64_t n = g.n_dofs;     // nodes (scalar set-up passes)
   const int64_t n8 = P->nv() * 8; // bytes of an FP64 vector of the ABI

@@ -76,7 +76,7 @@ int tile_occupancy(int degree, int mode, int geom, int prec, int ncomp, size_t s
 }
 
 size_t tile_smem_bytes(int degree, int geom, int prec, const TileGeom& g, int mode) {
-  return tile_smem_elems(degree, geom, prec_bytes(prec), g, mode) * prec_bytes(prec);
+  return tile_smem_elems(degree, geom, prec_bytes(prec), g, mode, prec) * prec_bytes(prec);
 }
 
 }  // namespace mfcg

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/mfcg.h"
 
 namespace mfcg {
@@ -386,7 +388,17 @@ struct TileArgs {
   int prefetch_ahead;    // operator passes: during its cell phase, a CTA prefetches into L2 the
                          // owned input block (and geometry) of tile blockIdx + prefetch_ahead
                          // (the CTAs resident in one wave); 0 = off
+  const uint2* tc_frag;  // PREC_F64TC: digit fragments of the even-odd cell-matrix blocks (tc_tables.cu)
+  int tc_g2;             // PREC_F64TC: the blocks are Bint 2^-tc_g2
+  int tc_r;              // PREC_F64TC: right shift of the recombined digit products (56..72)
 };
+
+// tensor-core cell operator (tc_tables.cu): B-fragment table, fixed-point
+// exponent g2 and result shift r of the degree-p Cartesian cell matrix (0 on
+// success), and the shared-memory elements of its staging areas for row tiles
+// of up to mx x my cells
+int build_tc_fragments(int p, const OperatorCoeffs& c, int op_kind, std::vector<uint2>& frag, int& g2, int& r);
+size_t tc_staging_elems(int p, int mx, int my);
 
 // launchers (one set per degree, see tile_kernels.cuh)
 cudaError_t launch_tile(int degree, int mode, const TileArgs& a, const OperatorCoeffs& c, cudaStream_t s);

@@ -26,7 +26,7 @@ using namespace mfcg;
 
 namespace {
 
-// 16 MiB of face partials: for example Q4 on up to about 42^3 cells, Q2 on 84^3.
+// 16 MiB of face partials: for example Q4 on up to about 40^3 cells, Q2 on 84^3.
 constexpr size_t kStaticScratchBytes = size_t(16) << 20;
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
@@ -88,6 +88,9 @@ extern "C" int mfcg_apply_operator_static(const mfcg_mesh* mesh, int degree, con
     if ((int64_t)degree * N[d] + 1 > (1 << 20)) return MFCG_INVALID_ARG;
   int T[3];
   for (int d = 0; d < 3; ++d) T[d] = default_affine_tile(degree);
+  // mfcg_setup's default FP64 tiles at degree 4 are 4 x 4 x 3 cells (the
+  // shape of its tensor-core operator): the same vector order here
+  if (degree == 4) T[2] = 3;
   TileArgs a{};
   init_tile_geom(degree, N, T, a.g, a.fam, &a.tdiv);
   if ((size_t)a.g.n_tiles * (size_t)a.g.face_stride * sizeof(double) > kStaticScratchBytes)

@@ -20,7 +20,15 @@
 
 namespace mfcg {
 
-enum Prec { PREC_F64 = 0, PREC_DD = 1, PREC_F32 = 2 };
+//   PREC_F64TC: FP64 like PREC_F64 (every stored value, update and inner
+//             product in FP64), with the contractions of the Cartesian cell
+//             operator on the FP16 tensor cores by an exact 8-bit digit split
+//             of 64-bit fixed-point data (tc_operator.cuh); only the affine
+//             operator passes and the fused CG iterations use it.
+enum Prec { PREC_F64 = 0, PREC_DD = 1, PREC_F32 = 2, PREC_F64TC = 3 };
+
+// FP64 arithmetic in the vector work (PREC_F64 and PREC_F64TC)
+__host__ __device__ constexpr bool is_f64(int prec) { return prec == PREC_F64 || prec == PREC_F64TC; }
 
 // bytes of one stored value
 inline size_t prec_bytes(int prec) { return prec == PREC_F32 ? 4 : 8; }
@@ -119,6 +127,10 @@ template <>
 struct Num<PREC_F32> {
   using T = float;
 };
+template <>
+struct Num<PREC_F64TC> {
+  using T = double;
+};
 
 template <int PREC>
 __device__ __forceinline__ typename Num<PREC>::T t_zero() {
@@ -206,6 +218,8 @@ struct DotAcc<PREC_F64> {
   __device__ void madd(double x, double y) { v = fma(x, y, v); }
   __device__ double get() const { return v; }
 };
+template <>
+struct DotAcc<PREC_F64TC> : DotAcc<PREC_F64> {};
 template <>
 struct DotAcc<PREC_F32> {
   float v = 0.f;

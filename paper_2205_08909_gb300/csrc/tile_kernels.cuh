@@ -30,6 +30,7 @@
 
 #include "mfcg_internal.h"
 #include "precision.cuh"
+#include "tc_operator.cuh"
 
 namespace mfcg {
 
@@ -699,7 +700,7 @@ __device__ __forceinline__ dd dot_to_dd(const DotAcc<PREC>& a) {
 // stores this CTA's seven sums into row `row` of the partial buffer
 template <int PREC>
 __device__ __forceinline__ void store_cta_sums(DotAcc<PREC> (&sm)[7], double* red, double* partial, int64_t row) {
-  if constexpr (PREC == PREC_F64) {
+  if constexpr (is_f64(PREC)) {
     double s[7];
 #pragma unroll
     for (int m = 0; m < 7; ++m) s[m] = sm[m].get();
@@ -724,7 +725,7 @@ __device__ __forceinline__ void store_cta_sums(DotAcc<PREC> (&sm)[7], double* re
 // fixed-order sum of rows [0, nrows) of the partial buffer; valid in thread 0
 template <int PREC>
 __device__ __forceinline__ void reduce_partials(const double* partial, int64_t nrows, double* red, double (&out)[7]) {
-  if constexpr (PREC == PREC_F64) {
+  if constexpr (is_f64(PREC)) {
 #pragma unroll
     for (int m = 0; m < 7; ++m) out[m] = 0.0;
     for (int64_t t = threadIdx.x; t < nrows; t += kThreads) {
@@ -807,8 +808,9 @@ __global__ void __launch_bounds__(kThreads, PREC == PREC_F32 ? 3 : 0)
   using T = typename Num<PREC>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[8 * (kThreads / 32)];
-  __shared__ int s_org[kMaxColorCells];
-  __shared__ int s_cell[kMaxColorCells];
+  // cell tables of the colour / batch loops (unused by the tensor-core operator)
+  __shared__ int s_org[PREC == PREC_F64TC ? 1 : kMaxColorCells];
+  __shared__ int s_cell[PREC == PREC_F64TC ? 1 : kMaxColorCells];
   const TileGeom& g = a_all.g;
 
   T alpha_m = t_zero<PREC>(), beta_t = t_zero<PREC>(), xa = t_zero<PREC>(), xr = t_zero<PREC>();
@@ -818,7 +820,7 @@ __global__ void __launch_bounds__(kThreads, PREC == PREC_F32 ? 3 : 0)
     if (st->done) return;
     const int k = st->k;
     xupd = (k > 1) && ((k & 1) || st->x_every_iter);
-    if constexpr (PREC == PREC_F64) {
+    if constexpr (is_f64(PREC)) {
       alpha_m = -st->alpha_prev;
       beta_t = st->beta_prev;
       xa = st->alpha_prev;
@@ -1095,7 +1097,12 @@ __global__ void __launch_bounds__(kThreads, PREC == PREC_F32 ? 3 : 0)
   }
 
   // ---------------- phase 2: cell integrals ----------------
-  if constexpr (GEOM == GEOM_AFFINE && (MODE == MODE_CG || MODE == MODE_OPERATOR)) {
+  if constexpr (PREC == PREC_F64TC && GEOM == GEOM_AFFINE && (MODE == MODE_CG || MODE == MODE_OPERATOR)) {
+    __syncthreads();  // phase 1 finished with U
+    tc::brick_op_affine_tc<P>(U, V, reinterpret_cast<long long*>(U + 2 * Bmax), bx, by, bz, ncx, ncy, ncz,
+                              min(4, g.T[0]), min(4, g.T[1]), a.tc_frag, a.tc_g2, a.tc_r,
+                              reinterpret_cast<int*>(red));
+  } else if constexpr (GEOM == GEOM_AFFINE && (MODE == MODE_CG || MODE == MODE_OPERATOR)) {
     __syncthreads();  // phase 1 finished with U
     brick_op_affine<PREC, P>(c, U, V, bx, by, bz, ncx, ncy, ncz, a.op_kind);
   } else if constexpr (GEOM != GEOM_AFFINE && (MODE == MODE_CG || MODE == MODE_OPERATOR)) {
@@ -1408,8 +1415,11 @@ __global__ void __launch_bounds__(kThreads, 3) tail_kernel(const TileArgs a) {
 // modes): node bricks U and V, and the cell scratch -- none for the
 // whole-brick affine operator, one colour of cells for the set-up passes, one
 // batch of cells for the deformed operator
-inline size_t tile_smem_elems(int P, int geom, int elem_bytes, const TileGeom& g, int mode = -1) {
+inline size_t tile_smem_elems(int P, int geom, int elem_bytes, const TileGeom& g, int mode = -1, int prec = -1) {
   const size_t Bmax = (size_t)(P * g.T[0] + 1) * (P * g.T[1] + 1) * (P * g.T[2] + 1);
+  // tensor-core operator: the two bricks and the row-tile staging
+  if (prec == PREC_F64TC && geom == GEOM_AFFINE && (mode == MODE_CG || mode == MODE_OPERATOR || mode == -1))
+    return 2 * Bmax + tc_staging_elems(P, std::min(4, g.T[0]), std::min(4, g.T[1]));
   const size_t colour = (size_t)((g.T[0] + 1) / 2) * ((g.T[1] + 1) / 2) * ((g.T[2] + 1) / 2);
   const bool iter = mode == MODE_CG || mode == MODE_OPERATOR;
   const bool setup = mode == MODE_RHS || mode == MODE_DIAG;
@@ -1431,10 +1441,15 @@ template <int P, int GEOM, int NC>
 TileFn<P> tile_fn_gn(int mode, int prec) {
   switch (mode) {
     case MODE_CG:
+      if constexpr (GEOM == GEOM_AFFINE && tc::tc_degree(P))
+        if (prec == PREC_F64TC) return tile_kernel<P, MODE_CG, GEOM, PREC_F64TC, NC>;
       return prec == PREC_F64 ? tile_kernel<P, MODE_CG, GEOM, PREC_F64, NC>
                               : (prec == PREC_DD ? tile_kernel<P, MODE_CG, GEOM, PREC_DD, NC>
-                                                 : tile_kernel<P, MODE_CG, GEOM, PREC_F32, NC>);
+                                                 : (prec == PREC_F32 ? tile_kernel<P, MODE_CG, GEOM, PREC_F32, NC>
+                                                                     : nullptr));
     case MODE_OPERATOR:
+      if constexpr (GEOM == GEOM_AFFINE && tc::tc_degree(P))
+        if (prec == PREC_F64TC) return tile_kernel<P, MODE_OPERATOR, GEOM, PREC_F64TC, NC>;
       return prec == PREC_F64 ? tile_kernel<P, MODE_OPERATOR, GEOM, PREC_F64, NC>
                               : (prec == PREC_DD ? tile_kernel<P, MODE_OPERATOR, GEOM, PREC_DD, NC> : nullptr);
     case MODE_RHS:
@@ -1493,7 +1508,7 @@ template <int P>
 cudaError_t launch_tile_p(int mode, const TileArgs& a, const OperatorCoeffs& c, cudaStream_t s) {
   TileFn<P> fn = tile_fn<P>(mode, a.geom, a.prec, a.ncomp);
   if (!fn) return cudaErrorInvalidValue;
-  const size_t smem = tile_smem_elems(P, a.geom, prec_bytes(a.prec), a.g, mode) * prec_bytes(a.prec);
+  const size_t smem = tile_smem_elems(P, a.geom, prec_bytes(a.prec), a.g, mode, a.prec) * prec_bytes(a.prec);
   fn<<<(unsigned)a.g.n_tiles, kThreads, smem, s>>>(a, c);
   return cudaGetLastError();
 }
@@ -1501,13 +1516,14 @@ cudaError_t launch_tile_p(int mode, const TileArgs& a, const OperatorCoeffs& c, 
 template <int P>
 cudaError_t launch_tail_p(int mode, const TileArgs& a, cudaStream_t s) {
   const unsigned grid = (unsigned)(a.tail_ctas > 0 ? a.tail_ctas : 1);
+  // the tensor-core operator's shell partials and sums are FP64 like PREC_F64's
   if (mode == MODE_CG) {
-    if (a.prec == PREC_F64) tail_kernel<P, MODE_CG, PREC_F64><<<grid, kThreads, 0, s>>>(a);
+    if (is_f64(a.prec)) tail_kernel<P, MODE_CG, PREC_F64><<<grid, kThreads, 0, s>>>(a);
     else if (a.prec == PREC_DD) tail_kernel<P, MODE_CG, PREC_DD><<<grid, kThreads, 0, s>>>(a);
     else tail_kernel<P, MODE_CG, PREC_F32><<<grid, kThreads, 0, s>>>(a);
   } else {
     if (a.prec == PREC_DD) tail_kernel<P, MODE_OPERATOR, PREC_DD><<<grid, kThreads, 0, s>>>(a);
-    else if (a.prec == PREC_F64) tail_kernel<P, MODE_OPERATOR, PREC_F64><<<grid, kThreads, 0, s>>>(a);
+    else if (is_f64(a.prec)) tail_kernel<P, MODE_OPERATOR, PREC_F64><<<grid, kThreads, 0, s>>>(a);
     else return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

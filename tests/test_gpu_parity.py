@@ -719,3 +719,76 @@ def test_residual_estimate_follows_algorithm1_history(mfcg, mode, precision):
         _, info = prob.cg_solve(bd, rtol=0.0, maxit=k)
         assert abs(info["residual_sq_est"] - ref.residual_sq_history[k - 1]) <= 1e-9 * ref.residual_sq_history[k - 1]
     prob.close()
+
+
+# ----------------------------------------------------------------- FP64 contractions: tensor cores / FP64 pipe
+
+
+AFFINE_OPERATOR_CASES = [c for c in OPERATOR_CASES if c[2] == 0.0 and c[3] == "constant"]
+
+
+@pytest.mark.parametrize("p,cells,amp,coef,tile", AFFINE_OPERATOR_CASES)
+def test_fp64_pipe_sweeps_match_oracle(mfcg, p, cells, amp, coef, tile):
+    # the native FP64 whole-brick sweeps (mfcg_options.fp64_contraction = FP64_PIPE)
+    op = _oracle_problem(p, cells, amp, coef)
+    A = fem.assemble(op)
+    u = inputs.random_vector(op.n_dofs, salt=5)
+    prob = _gpu_problem(mfcg, p, cells, amp, coef, tile=tile, fp64_contraction="fp64_pipe")
+    got = _to_host(prob, prob.apply_operator(_to_dev(prob, u)))
+    assert _rel(got, A @ u) <= OP_TOL
+    prob.close()
+
+
+@pytest.mark.parametrize("mode", ["fused", "unfused", "semi_fused"])
+def test_fp64_pipe_solve_matches_oracle(mfcg, mode):
+    op = _oracle_problem(4, (5, 6, 4))
+    A = fem.assemble(op)
+    b = inputs.boundary_zeroed(inputs.random_vector(op.n_dofs, salt=31), op.nodes_per_dim)
+    dinv = 1.0 / A.diagonal()
+    ref = ocg.pcg_algorithm1(lambda v: A @ v, b, dinv, 1e-10, 5000)
+    prob = _gpu_problem(mfcg, 4, (5, 6, 4), mode=mode, fp64_contraction="fp64_pipe")
+    x, info = prob.cg_solve(_to_dev(prob, b), rtol=1e-10, maxit=5000)
+    assert info["converged"] and abs(info["iterations"] - ref.iterations) <= 1
+    same = ocg.pcg_algorithm1(lambda v: A @ v, b, dinv, 0.0, info["iterations"])
+    assert _rel(_to_host(prob, x), same.x) <= SOL_TOL
+    prob.close()
+
+
+@pytest.mark.parametrize("p,cells", [(1, (7, 6, 5)), (2, (8, 8, 8)), (3, (5, 4, 7)), (4, (9, 5, 6)), (5, (3, 4, 3)),
+                                     (7, (2, 3, 2))])
+def test_tensor_core_operator_is_fp64_accurate(mfcg, p, cells):
+    # inputs spanning e^-6 .. e^6 in magnitude; the tensor-core operator stays
+    # within the FP64 rounding level of the oracle's FP64 CSR product (which is
+    # itself about 1e-15 from the exact product of its 1D matrices), and agrees
+    # with the FP64 sweeps
+    op = _oracle_problem(p, cells)
+    A = fem.assemble(op)
+    rng = np.random.default_rng(700 + p)
+    u = rng.standard_normal(op.n_dofs) * np.exp(rng.uniform(-6, 6, op.n_dofs))
+    ref = A @ u
+    tc = _gpu_problem(mfcg, p, cells)
+    pipe = _gpu_problem(mfcg, p, cells, fp64_contraction="fp64_pipe")
+    got = _to_host(tc, tc.apply_operator(_to_dev(tc, u)))
+    got_pipe = _to_host(pipe, pipe.apply_operator(_to_dev(pipe, u)))
+    assert _rel(got, ref) <= (5e-15 if p <= 4 else 2e-14)
+    assert _rel(got, got_pipe) <= (5e-15 if p <= 4 else 2e-14)
+    # Dirichlet rows are the identity, bit for bit
+    bnd = fem.boundary_mask(op)
+    assert np.array_equal(got[bnd], u[bnd])
+    tc.close()
+    pipe.close()
+
+
+def test_tensor_core_operator_vector_and_mass(mfcg):
+    # the tensor-core contractions serve the mass operator and the
+    # vector-valued form on Cartesian meshes too
+    for operator, comps in (("mass", 1), ("laplace", 3), ("mass", 3)):
+        op = fem.Problem(3, (4, 3, 5), 0.0, fem.COEF_CONSTANT, fem.OP_MASS if operator == "mass" else fem.OP_LAPLACE)
+        A = fem.assemble(op)
+        n = op.n_dofs
+        u = inputs.random_vector(n * comps, salt=77)
+        tc = _gpu_problem(mfcg, 3, (4, 3, 5), operator=operator, components=comps)
+        got = _to_host(tc, tc.apply_operator(_to_dev(tc, u)))
+        ref = np.concatenate([A @ u[c * n:(c + 1) * n] for c in range(comps)])
+        assert _rel(got, ref) <= OP_TOL
+        tc.close()
