@@ -132,30 +132,28 @@ __host__ __device__ constexpr Plan make_plan(int kmax) {
   return pl;
 }
 
-// work items of one 16-cell row tile: (block, n-tile) pairs, the two-k-step
-// items first, dealt round-robin to the warps
+// Work item `it` of one 16-cell row tile: a (block, n-tile) pair, items with
+// more k steps first (dealt round-robin to the warps).  Evaluated with
+// compile-time loop bounds, so a run-time `it` needs no table in local memory.
 template <int P>
-struct Items {
-  int b[Shape<P>::kItems];
-  int nt[Shape<P>::kItems];
-};
-
-template <int P>
-__host__ __device__ constexpr Items<P> make_items() {
+__host__ __device__ __forceinline__ void item_of(int it, int& b, int& nt) {
   using S = Shape<P>;
-  Items<P> it{};
   int n = 0;
-  int maxk = 0;
-  for (int b = 0; b < 8; ++b) maxk = S::ksteps(b) > maxk ? S::ksteps(b) : maxk;
-  for (int k = maxk; k >= 1; --k)
-    for (int b = 0; b < 8; ++b)
-      if (S::ksteps(b) == k)
-        for (int t = 0; t < S::ntiles(b); ++t) {
-          it.b[n] = b;
-          it.nt[n] = t;
-          ++n;
+  b = 0;
+  nt = 0;
+#pragma unroll
+  for (int k = 8; k >= 1; --k) {
+#pragma unroll
+    for (int bb = 0; bb < 8; ++bb) {
+      if (S::ksteps(bb) == k) {
+        if (it >= n && it < n + S::ntiles(bb)) {
+          b = bb;
+          nt = it - n;
         }
-  return it;
+        n += S::ntiles(bb);
+      }
+    }
+  }
 }
 
 // ------------------------------------------------------------------------------------
@@ -421,7 +419,6 @@ __device__ void brick_op_affine_tc(double* U, double* V, long long* stage, int b
   constexpr int XS = S::XS;
   constexpr Plan pl = make_plan(S::kPlanK);
   constexpr int NACC = pl.nacc;
-  constexpr Items<P> items = make_items<P>();
   const int nbrick = bx * by * bz;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   long long* UX = reinterpret_cast<long long*>(U);
@@ -470,7 +467,8 @@ __device__ void brick_op_affine_tc(double* U, double* V, long long* stage, int b
     __syncthreads();
     // products: items (block, n-tile) dealt round-robin to the warps
     for (int it = warp; it < S::kItems; it += kThreads / 32) {
-      const int b = items.b[it], nt = items.nt[it];
+      int b, nt;
+      item_of<P>(it, b, nt);
       const int ksb = S::ksteps(b), bev = S::bev(b), bo = S::boff(b);
       long long out[4] = {0, 0, 0, 0};
       for (int kc = 0; kc < ksb; kc += 2) {

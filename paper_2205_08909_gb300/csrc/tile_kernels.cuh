@@ -801,9 +801,13 @@ __device__ __forceinline__ int64_t brick_global_index(const TileGeom& g, int tx,
 // target to the compiler as a bound without the argument does; a minimum of
 // one CTA per SM instead lets it use up to 255 registers, which halved the
 // resident CTAs of many degree/mode combinations (degree 5 double-float: 150
-// instead of 128 registers, 44% slower)
+// instead of 128 registers, 44% slower).  The tensor-core FP64 tiles are
+// bounded to two CTAs per SM (their shared memory allows two): unbounded they
+// take 160 registers (one CTA), and a run-time indexed table had put them at
+// 128 with a 400-byte stack whose spills to L2 and DRAM doubled the kernel's
+// DRAM writes.
 template <int P, int MODE, int GEOM, int PREC, int NC>
-__global__ void __launch_bounds__(kThreads, PREC == PREC_F32 ? 3 : 0)
+__global__ void __launch_bounds__(kThreads, PREC == PREC_F32 ? 3 : (PREC == PREC_F64TC ? 2 : 0))
     tile_kernel(const TileArgs a_all, const OperatorCoeffs c) {
   using T = typename Num<PREC>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
