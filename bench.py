@@ -38,7 +38,7 @@ UNIT = "GDoF-it/s"
 FP64_PEAK_TFLOPS = 1.25          # nominal FP64 rate of GB300 (dense, FMA = 2 flops)
 FALLBACK_HBM_GBS = 6800.0
 KERNEL_SOURCES = ["paper_2205_08909_gb300/csrc/tile_kernels.cuh", "paper_2205_08909_gb300/csrc/mfcg_internal.h",
-                  "paper_2205_08909_gb300/csrc/precision.cuh"]
+                  "paper_2205_08909_gb300/csrc/precision.cuh", "paper_2205_08909_gb300/csrc/tc_operator.cuh"]
 
 
 def measured_peaks():
@@ -182,6 +182,51 @@ def algorithmic_flops_per_iteration(degree: int, n_cells: int, n_dofs: int, geom
 
 
 ALGORITHMIC_BYTES_PER_DOF = 64.0  # r, p, v read+write, D^-1 read, x read+write every other iteration
+
+# Tensor-core FP64 operator (tc_operator.cuh): degrees with it, digit pairs kept
+# (k + l >= 6 of 8 x 8), and the tiles the library picks for it
+TC_DEGREES = (1, 2, 3, 4, 5, 7)
+TC_DIGIT_PAIRS = 43
+
+
+def effective_tile(degree: int, geometry: str, precision: str, contraction: str, tile=None):
+    """Tile of cells the library uses: the given one, else its default (4 x 4 x 3
+    cells for the tensor-core FP64 operator at degree 4)."""
+    if tile:
+        return tuple(tile)
+    t = DEFAULT_TILE["affine" if geometry == "affine" else "deformed"][degree]
+    if geometry == "affine" and precision == "fp64" and contraction == "tensor_cores" and degree == 4:
+        return (t, t, 3)
+    return (t, t, t)
+
+
+def tc_mma_per_row_tile(degree: int) -> int:
+    """mma.m16n8k16 instructions of one 16-cell row tile: per even-odd block
+    ceil(size/16) k steps x ceil(size/8) n tiles, times the digit pairs."""
+    n1 = degree + 1
+    no, ne = n1 // 2, n1 - n1 // 2
+    total = 0
+    for b in range(8):
+        size = 1
+        for d in range(3):
+            size *= no if (b >> d) & 1 else ne
+        total += -(-size // 16) * -(-size // 8)
+    return total * TC_DIGIT_PAIRS
+
+
+def tc_digit_flops(degree: int, cells, tile) -> float:
+    """FP16 tensor-core flops of one operator pass (2 x 16 x 8 x 16 per mma):
+    row tiles of up to 4 x 4 x 1 cells per tile, summed over the tiles."""
+    rows = 0
+    ext = []
+    for d in range(3):
+        n, t = cells[d], tile[d]
+        ext.append([t] * (n // t) + ([n % t] if n % t else []))
+    for nz in ext[2]:
+        for ny in ext[1]:
+            for nx in ext[0]:
+                rows += -(-nx // 4) * -(-ny // 4) * nz
+    return float(rows) * tc_mma_per_row_tile(degree) * 2 * 16 * 8 * 16
 
 
 # ------------------------------------------------------------------------------ clocks
@@ -422,10 +467,10 @@ def run_ours(args, world, rank, local):
             raise SystemExit("--geometry applies to deformed workloads only")
         geometry = args.geometry
 
-    def make(mode, precision, instrument=False):
+    def make(mode, precision, instrument=False, contraction="tensor_cores"):
         return mfcg.Problem(w.degree, w.cells, amplitude=w.amplitude, geometry=geometry,
                             coefficient=w.coefficient, mode=mode, precision=precision, instrument=instrument,
-                            tile=tile)
+                            tile=tile, fp64_contraction=contraction)
 
     def timed_steps(prob, b, K, W):
         xs = [torch.zeros(prob.n_dofs, dtype=torch.float64, device="cuda") for _ in range(max(K, W, 1))]
@@ -480,24 +525,28 @@ def run_ours(args, world, rank, local):
     form_bytes = {"fused": 64, "semi_fused": 104, "unfused": 152}
     forms = []
     for f in (("unfused", main_prec), ("fused", "fp64"), ("unfused", "fp64"), ("semi_fused", "fp64"),
-              ("fused", "double_float"), ("unfused", "double_float")):
+              ("fused", "fp64_pipe"), ("fused", "double_float"), ("unfused", "double_float")):
         if f not in forms:
             forms.append(f)
-    for mode, prec in forms:
+    for mode, prec_name in forms:
+        # "fp64_pipe": FP64 with the operator's sweeps on the FP64 pipe (Cartesian meshes)
+        prec = "fp64" if prec_name == "fp64_pipe" else prec_name
+        if prec_name == "fp64_pipe" and geometry != "affine":
+            continue
         if mode != "fused" and prec == "fp32_inner":
             continue  # the FP32 inner solver exists in fused form only
         if args.skip_unfused and mode == "unfused":
             continue
         if args.skip_variants and (mode, prec) != ("unfused", main_prec):
             continue
-        if prec == main_prec and mode == "fused":
+        if prec_name == main_prec and mode == "fused":
             continue
-        prob = make(mode, prec)
+        prob = make(mode, prec, contraction="fp64_pipe" if prec_name == "fp64_pipe" else "tensor_cores")
         bv = prob.rhs()  # each problem's own tile-blocked order
         ms_v, _ = timed_steps(prob, bv, K, W)
         v = dof_its / (ms_v / 1e3) / 1e9
         vb = form_bytes[mode] + geo_bytes_per_dof
-        variants[f"{mode}_{prec}"] = {"value": round(v, 4), "ms_per_step": round(ms_v / K, 3),
+        variants[f"{mode}_{prec_name}"] = {"value": round(v, 4), "ms_per_step": round(ms_v / K, 3),
                                       "hbm_roofline_frac": round(v / world * vb / hbm, 4),
                                       "algorithmic_bytes_per_dof": round(vb, 2),
                                       "solve_rtol_1e-10": converged_solve(prob, bv)}
@@ -524,8 +573,25 @@ def run_ours(args, world, rank, local):
     inst.close()
     hbm_gbs = kernel_bytes_per_dof * w.n_dofs / (kernel_ms / 1e3) / 1e9
     traffic = stored_traffic(w.name, main_prec)
-    if main_prec == "fp64":
-        flops = algorithmic_flops_per_iteration(w.degree, n_cells, w.n_dofs, geometry, w.cells, tile)
+    eff_tile = effective_tile(w.degree, geometry, main_prec, "tensor_cores", tile)
+    tc_main = main_prec == "fp64" and geometry == "affine" and w.degree in TC_DEGREES
+    if tc_main:
+        # FP64 on the tensor cores: the HBM roofline that the fused method aims at,
+        # with the tensor-pipe and FP64-equivalent views beside it
+        tflops = tc_digit_flops(w.degree, w.cells, eff_tile)
+        bf16 = float(peaks.get("bf16_tflops", 1900.0))
+        f64_flops = algorithmic_flops_per_iteration(w.degree, n_cells, w.n_dofs, geometry, w.cells, eff_tile)
+        roofline = {"bound": "hbm", "achieved": round(hbm_gbs, 1), "peak": hbm, "unit": "GB/s",
+                    "frac": round(hbm_gbs / hbm, 4), "traffic": traffic, "peak_kind": peak_kind,
+                    "tensor_view": {"digit_product_tflops": round(tflops / (kernel_ms / 1e3) / 1e12, 2),
+                                    "peak_tflops": bf16, "peak_kind": "measured bf16 dense burst (FP16 same rate)",
+                                    "frac": round(tflops / (kernel_ms / 1e3) / 1e12 / bf16, 4),
+                                    "flops_per_launch": tflops},
+                    "fp64_equivalent_view": {"tflops": round(f64_flops / (kernel_ms / 1e3) / 1e12, 4),
+                                             "peak_tflops": FP64_PEAK_TFLOPS, "peak_kind": "nominal FP64",
+                                             "frac": round(f64_flops / (kernel_ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS, 4)}}
+    elif main_prec == "fp64":
+        flops = algorithmic_flops_per_iteration(w.degree, n_cells, w.n_dofs, geometry, w.cells, eff_tile)
         achieved = flops / (kernel_ms / 1e3) / 1e12
         roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": traffic,
@@ -541,7 +607,8 @@ def run_ours(args, world, rank, local):
         achieved = hbm_gbs
         roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                     "frac": round(achieved / hbm, 4), "traffic": traffic, "peak_kind": peak_kind}
-    roofline.update({"kernel": f"tile_kernel<{w.degree}, MODE_CG, GEOM_{ {'affine': 'AFFINE', 'deformed': 'DEFORMED', 'deformed_tensor': 'TENSOR'}[geometry]}, {main_prec}>",
+    roofline.update({"kernel": f"tile_kernel<{w.degree}, MODE_CG, GEOM_{ {'affine': 'AFFINE', 'deformed': 'DEFORMED', 'deformed_tensor': 'TENSOR'}[geometry]}, {'fp64, tensor-core contractions' if tc_main else main_prec}>",
+                     "tile": list(eff_tile),
                      "kernel_ms": round(kernel_ms, 4),
                      "hbm_view": {"achieved_gbs": round(hbm_gbs, 1), "peak_gbs": hbm, "peak_kind": peak_kind,
                                   "frac": round(hbm_gbs / hbm, 4),
@@ -576,7 +643,10 @@ def run_ours(args, world, rank, local):
         "data": "synthetic: manufactured right-hand side of u = sin(pi x) sin(pi y) sin(pi z), x0 = 0",
         "config": {"workload": w.name, "degree": w.degree, "cells": list(w.cells), "n_dofs": w.n_dofs,
                    "geometry": geometry, "precision": main_prec, "iterations_per_step": iters,
-                   "tile": list(tile) if tile else "default",
+                   "tile": list(eff_tile),
+                   "arithmetic": ("FP64 vectors, updates and inner products; operator contractions as exact "
+                                  "8-bit digit products of 64-bit fixed-point data on the FP16 tensor cores, "
+                                  "recombined in 64-bit integers (FP64-level results)") if tc_main else main_prec,
                    "parallelism": f"replicas x{world}",
                    "l2": f"inputs larger than L2: {8 * w.n_dofs / 1e6:.0f} MB per vector, 8 vectors"},
         "hbm_roofline_frac": round(value / world * kernel_bytes_per_dof / hbm, 4),

@@ -287,8 +287,9 @@ __device__ __forceinline__ void eo_backward(const long long (&o)[P + 1], long lo
 // T1[z][y][cxl N1 + out], y pass into T2[z][cyl N1 + out][xt], z pass into the
 // Xs rows (cxl + 4 cyl) at the block positions; rows of absent cells zero.
 template <int P, int CMX, int CMY>
-__device__ __forceinline__ void forward_passes(const long long* u0, int bx, int by, int mx_rt, int my_rt,
-                                               long long* T1, long long* T2, long long* Xs) {
+__device__ __forceinline__ void forward_passes(const long long* __restrict__ u0, int bx, int by, int mx_rt, int my_rt,
+                                               long long* __restrict__ T1, long long* __restrict__ T2,
+                                               long long* __restrict__ Xs) {
   using S = Shape<P>;
   constexpr int N1 = S::N1, NE = S::NE, XS = S::XS;
   const int mx = CMX ? CMX : mx_rt, my = CMY ? CMY : my_rt;
@@ -342,8 +343,8 @@ __device__ __forceinline__ void forward_passes(const long long* u0, int bx, int 
 // nodes shared by two cell segments summed in registers) -> added to the
 // brick accumulator at origin v0 (x back, each node of the slab by one thread).
 template <int P, int CMX, int CMY>
-__device__ __forceinline__ void backward_passes(long long* v0, int bx, int by, int mx_rt, int my_rt,
-                                                const long long* Ys, long long* T1, long long* T2) {
+__device__ __forceinline__ void backward_passes(long long* __restrict__ v0, int bx, int by, int mx_rt, int my_rt,
+                                                const long long* Ys, long long* T1, long long* __restrict__ T2) {
   using S = Shape<P>;
   constexpr int N1 = S::N1, NE = S::NE, XS = S::XS;
   const int mx = CMX ? CMX : mx_rt, my = CMY ? CMY : my_rt;
@@ -550,20 +551,34 @@ __device__ void brick_op_affine_tc(double* U, double* V, long long* stage, int b
           }
         }
         // recombination: out += sum_a 2^(8 s_a - R) D_a; with 56 <= R <= 72
-        // weights s >= 9 shift left and s <= 7 right
-#pragma unroll
-        for (int a = 0; a < NACC; ++a) {
-          const int sh = 8 * pl.s[a] - R;
+        // weights s >= 9 shift left and s <= 7 right.  With one accumulator
+        // per weight (the plan for balanced digits), two adjacent weights are
+        // first combined in 32 bits, D_s + 2^8 D_(s+1) (|D| < 2^22).
+        auto add_shifted = [&](long long& o, long long v, int s) {
+          const int sh = 8 * s - R;
+          if (s >= 9)
+            o += v << sh;
+          else if (s <= 7)
+            o += v >> -sh;
+          else
+            o += sh >= 0 ? (v << sh) : (v >> -sh);
+        };
+        constexpr bool kOnePerWeight = NACC == 2 * kDigits - 1 - kSmin;
+        if constexpr (kOnePerWeight) {
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
-            const long long v = (long long)acc_to_int(acc[a][i]);
-            if (pl.s[a] >= 9)
-              out[i] += v << sh;
-            else if (pl.s[a] <= 7)
-              out[i] += v >> -sh;
-            else
-              out[i] += sh >= 0 ? (v << sh) : (v >> -sh);
+#pragma unroll
+            for (int a = 0; a < NACC; a += 2) {
+              int v = acc_to_int(acc[a][i]);
+              if (a + 1 < NACC) v += acc_to_int(acc[a + 1][i]) << 8;
+              add_shifted(out[i], (long long)v, pl.s[a]);
+            }
           }
+        } else {
+#pragma unroll
+          for (int a = 0; a < NACC; ++a)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) add_shifted(out[i], (long long)acc_to_int(acc[a][i]), pl.s[a]);
         }
       }
       // C fragment: (row g, cols n0, n0+1) and (row g + 8, same columns)

@@ -263,14 +263,25 @@ def tc_brick_operator(p, cells, u_lex):
                     acc_out = np.zeros(blocks[key].shape[0], dtype=np.int64)
                     for k0 in range(0, kb, K_CHUNK):
                         ks = slice(k0, min(kb, k0 + K_CHUNK))
-                        for s, group in accumulator_plan(min(kb, K_CHUNK)):
+                        plan = accumulator_plan(min(kb, K_CHUNK))
+                        accs = []
+                        for s, group in plan:
                             D = np.zeros(blocks[key].shape[0], dtype=np.int64)
                             bound = np.zeros(blocks[key].shape[0], dtype=np.int64)
                             for (k, l) in group:
                                 D += bdig[key][l][:, ks] @ dd[k][ks]
                                 bound += np.abs(bdig[key][l][:, ks]) @ np.abs(dd[k][ks])
                             worst = max(worst, int(bound.max()))
-                            # weights s >= 9 shift left, s <= 7 right (|delta| <= 8)
+                            accs.append((s, D))
+                        # one accumulator per weight: adjacent weights combine in
+                        # 32 bits first, D_s + 2^8 D_(s+1); weights s >= 9 shift
+                        # left, s <= 7 right (|delta| <= 8)
+                        assert [a[0] for a in accs] == list(range(S_MIN, 2 * DIGITS - 1))
+                        for i in range(0, len(accs), 2):
+                            s, D = accs[i]
+                            if i + 1 < len(accs):
+                                D = D + (accs[i + 1][1] << 8)
+                            assert np.abs(D).max() < 2 ** 31
                             acc_out += (D << (8 * s - R)) if 8 * s >= R else (D >> (R - 8 * s))
                     Y[key] = acc_out
                 V[sl] += backward_butterfly(Y, n).reshape(n, n, n)
