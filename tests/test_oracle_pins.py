@@ -232,6 +232,35 @@ def test_l2_convergence_rate(p, amp, coef):
     assert rate > p + 1 - 0.35, (errs, rate)
 
 
+@pytest.mark.parametrize("p", [4, 5, 6])
+def test_l2_convergence_rate_high_degree_cartesian(p):
+    # the exact discrete solution by fast diagonalisation (independent of the
+    # assembled matrix) converges at the rate p + 1 in L2, within +-0.1
+    errs = []
+    Ns = (2, 4, 8)
+    for N in Ns:
+        prob = fem.Problem(p, (N, N, N))
+        u = fastdiag.solve(prob, fem.rhs(prob))
+        errs.append(fem.l2_error(prob, u))
+    rate = math.log(errs[-2] / errs[-1]) / math.log(Ns[-1] / Ns[-2])
+    assert abs(rate - (p + 1)) <= 0.1, (errs, rate)
+
+
+def test_l2_convergence_rate_degree4_deformed():
+    # deformed mesh with the variable coefficient at degree 4: rate 5 within
+    # +-0.1 between N = 4 and 6 (higher degrees on this unit-wavelength
+    # deformation are still pre-asymptotic below N = 8)
+    errs = []
+    Ns = (2, 4, 6)
+    for N in Ns:
+        prob = fem.Problem(4, (N, N, N), 0.05, fem.COEF_SIN_X)
+        A = fem.assemble(prob)
+        u = spla.spsolve(A.tocsc(), fem.rhs(prob))
+        errs.append(fem.l2_error(prob, u))
+    rate = math.log(errs[-2] / errs[-1]) / math.log(Ns[-1] / Ns[-2])
+    assert abs(rate - 5) <= 0.1, (errs, rate)
+
+
 def test_apply_rows_matches_assembled_matrix():
     rng = np.random.default_rng(5)
     for prob in (fem.Problem(2, (3, 2, 3)), fem.Problem(3, (2, 2, 2), 0.05, fem.COEF_SIN_X)):
