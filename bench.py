@@ -521,11 +521,13 @@ def run_ours(args, world, rank, local):
     # ---------------- comparators on the same workload
     variants = {}
     # algorithmic bytes per unknown of each form: fused 64; semi-fused (the GPU form of Sec. 6.4:
-    # pre 56, operator 16, post 32) 104; unfused Algorithm 1 152
-    form_bytes = {"fused": 64, "semi_fused": 104, "unfused": 152}
+    # pre 56, operator 16, post 32) 104; Algorithm 1 with loop fusion inside its regions (operator 16,
+    # p.v 16, x/r/r.r 48, z/r.z 24, p 24) 128; unfused Algorithm 1 152
+    form_bytes = {"fused": 64, "semi_fused": 104, "loop_fused": 128, "unfused": 152}
     forms = []
-    for f in (("unfused", main_prec), ("fused", "fp64"), ("unfused", "fp64"), ("semi_fused", "fp64"),
-              ("fused", "fp64_pipe"), ("fused", "double_float"), ("unfused", "double_float")):
+    for f in (("unfused", main_prec), ("loop_fused", main_prec), ("fused", "fp64"), ("unfused", "fp64"),
+              ("loop_fused", "fp64"), ("semi_fused", "fp64"), ("fused", "fp64_pipe"), ("fused", "double_float"),
+              ("unfused", "double_float")):
         if f not in forms:
             forms.append(f)
     for mode, prec_name in forms:
@@ -537,7 +539,7 @@ def run_ours(args, world, rank, local):
             continue  # the FP32 inner solver exists in fused form only
         if args.skip_unfused and mode == "unfused":
             continue
-        if args.skip_variants and (mode, prec) != ("unfused", main_prec):
+        if args.skip_variants and (mode, prec) not in (("unfused", main_prec), ("loop_fused", main_prec)):
             continue
         if prec_name == main_prec and mode == "fused":
             continue
@@ -551,8 +553,9 @@ def run_ours(args, world, rank, local):
                                       "algorithmic_bytes_per_dof": round(vb, 2),
                                       "solve_rtol_1e-10": converged_solve(prob, bv)}
         prob.close()
-    unf_key = f"unfused_{main_prec}"
+    unf_key, loop_key = f"unfused_{main_prec}", f"loop_fused_{main_prec}"
     fused_over_unfused = round(value / variants[unf_key]["value"], 4) if unf_key in variants else None
+    fused_over_loop_fused = round(value / variants[loop_key]["value"], 4) if loop_key in variants else None
 
     # ---------------- FP64 defect correction around the FP32 fused CG (time to rtol 1e-10)
     dc = None
@@ -634,6 +637,16 @@ def run_ours(args, world, rank, local):
                "h2d_bytes_per_step": 2 * 8 * w.n_dofs, "d2h_bytes_per_step": 8 * w.n_dofs}
     fused.close()
 
+    # ---------------- batched forms (short runs): a batch of independent problems and a block of
+    # right-hand sides sharing one mesh's operator data
+    batched = None
+    if not args.skip_batch:
+        bprec = "fp64" if main_prec == "fp64" else "double_float"
+        batched = {}
+        for key, blk in (("batch_of_8_problems", False), ("block_of_8_rhs_q5_48cube", True)):
+            batched[key] = measure_batch(batch_specs(8, blk), bprec, 2, 1, iters, world, local)
+            batched[key]["precision"] = bprec
+
     dtype = {"fp64": "f64", "double_float": "f32x2 (double-float, ~48-bit; FP64 scalars and reductions)",
              "fp32_inner": "f32"}[main_prec]
     line = {
@@ -652,9 +665,11 @@ def run_ours(args, world, rank, local):
         "hbm_roofline_frac": round(value / world * kernel_bytes_per_dof / hbm, 4),
         "algorithmic_bytes_per_dof": round(kernel_bytes_per_dof, 2),
         "fused_over_unfused": fused_over_unfused,
+        "fused_over_loop_fused": fused_over_loop_fused,
         "solve_rtol_1e-10": solve_main,
         "variants": variants,
         "defect_correction_fp32_inner": dc,
+        "batched": batched,
         "roofline": roofline,
         "e2e": e2e,
         "gpu_launches": launches_f,
@@ -673,26 +688,15 @@ def run_ours(args, world, rank, local):
     return line if rank == 0 else None
 
 
-def run_batch(args, world, rank, local):
-    """Batched form: args.batch independent seeded problems (degree U{2..8},
-    cells U{4..32}^3, deformation U[0, 0.08], final-tensor geometry, random
-    right-hand sides), args.iters fixed iterations each, solved as one batch
+def measure_batch(specs, prec, K, W, iters, world, local):
+    """Times the problems of specs (fixed iterations each) solved as one batch
     (one CUDA graph branch per member) and, for comparison, one after another
     as single problems."""
     import torch
 
     import paper_2205_08909_gb300 as mfcg
-    from paper_2205_08909_gb300 import build, inputs
+    from paper_2205_08909_gb300 import inputs
 
-    build.build()
-    torch.cuda.set_device(local)
-    K, W, iters = args.steps, args.warmup, args.iters
-    prec = args.precision if args.precision != "fp32_inner" else "double_float"
-    if args.rhs_block:
-        # a block of right-hand sides on one mesh: identical members share the operator data
-        specs = [{"degree": 5, "cells": (48, 48, 48)}] * args.batch
-    else:
-        specs = inputs.batch_problems(args.batch)
     rhs = inputs.batch_rhs(specs)
     batch = mfcg.Batch(specs, precision=prec)
     bs = [m.from_lexicographic(torch.from_numpy(r).cuda()) for m, r in zip(batch.members, rhs)]
@@ -733,27 +737,59 @@ def run_batch(args, world, rank, local):
     ms_s = timed(sequential)
     _, conv = batch.cg_solve(bs, [torch.zeros_like(b) for b in bs], rtol=1e-10, maxit=100000)
     batch.close()
-    value = dofs * iters * K * world / (ms_b / 1e3) / 1e9
-    degrees = [sp["degree"] for sp in specs]
     return {
-        "metric": "batched CG GDoF-iterations/s", "value": round(value, 4), "unit": UNIT, "n_gpus": world,
-        "steps": K, "warmup": W, "ms_per_step": round(ms_b / K, 3), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {"fp64": "f64", "double_float": "f32x2 (double-float)"}[prec],
-        "data": "synthetic: seeded problems and standard-normal right-hand sides, zero on the boundary",
-        "config": {"workload": (f"block of {args.batch} right-hand sides on Q5 48^3" if args.rhs_block
-                                else f"batch of {args.batch} problems"), "total_dofs": dofs,
-                   "degrees": {str(p): degrees.count(p) for p in sorted(set(degrees))},
-                   "iterations_per_step": iters, "precision": prec,
-                   "geometry": "affine" if args.rhs_block else "deformed_tensor",
-                   "parallelism": f"replicas x{world}"},
+        "value": round(dofs * iters * K * world / (ms_b / 1e3) / 1e9, 4), "ms_per_step": round(ms_b / K, 3),
+        "total_dofs": dofs, "iterations_per_step": iters, "steps": K, "warmup": W,
         "sequential_single_solves": {"value": round(dofs * iters * K * world / (ms_s / 1e3) / 1e9, 4),
                                      "ms_per_step": round(ms_s / K, 3)},
         "batched_over_sequential": round(ms_s / ms_b, 4),
         "solve_rtol_1e-10": {"iterations_min": min(i["iterations"] for i in conv),
                              "iterations_max": max(i["iterations"] for i in conv),
                              "converged": sum(i["converged"] for i in conv)},
-        "gpu_launches": launches,
-        "clocks": clocks,
+        "gpu_launches": launches, "clocks": clocks,
+    }
+
+
+def batch_specs(count: int, rhs_block: bool):
+    from paper_2205_08909_gb300 import inputs
+
+    if rhs_block:
+        # a block of right-hand sides on one mesh: identical members share the operator data
+        return [{"degree": 5, "cells": (48, 48, 48)}] * count
+    return inputs.batch_problems(count)
+
+
+def run_batch(args, world, rank, local):
+    """Batched form: args.batch independent seeded problems (degree U{2..8},
+    cells U{4..32}^3, deformation U[0, 0.08], final-tensor geometry, random
+    right-hand sides) or, with --rhs-block, args.batch right-hand sides on one
+    Q5 48^3 mesh; args.iters fixed iterations each."""
+    import torch
+
+    from paper_2205_08909_gb300 import build
+
+    build.build()
+    torch.cuda.set_device(local)
+    prec = args.precision if args.precision != "fp32_inner" else "double_float"
+    specs = batch_specs(args.batch, args.rhs_block)
+    m = measure_batch(specs, prec, args.steps, args.warmup, args.iters, world, local)
+    degrees = [sp["degree"] for sp in specs]
+    return {
+        "metric": "batched CG GDoF-iterations/s", "value": m["value"], "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "double_float": "f32x2 (double-float)"}[prec],
+        "data": "synthetic: seeded problems and standard-normal right-hand sides, zero on the boundary",
+        "config": {"workload": (f"block of {args.batch} right-hand sides on Q5 48^3" if args.rhs_block
+                                else f"batch of {args.batch} problems"), "total_dofs": m["total_dofs"],
+                   "degrees": {str(p): degrees.count(p) for p in sorted(set(degrees))},
+                   "iterations_per_step": args.iters, "precision": prec,
+                   "geometry": "affine" if args.rhs_block else "deformed_tensor",
+                   "parallelism": f"replicas x{world}"},
+        "sequential_single_solves": m["sequential_single_solves"],
+        "batched_over_sequential": m["batched_over_sequential"],
+        "solve_rtol_1e-10": m["solve_rtol_1e-10"],
+        "gpu_launches": m["gpu_launches"],
+        "clocks": m["clocks"],
     }
 
 
@@ -772,6 +808,7 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-dc", action="store_true", help="skip the FP32-inner defect-correction solve")
     ap.add_argument("--skip-variants", action="store_true", help="skip the FP64 comparators")
+    ap.add_argument("--skip-batch", action="store_true", help="skip the short batched and block runs")
     ap.add_argument("--geometry", default="", choices=["", "deformed", "deformed_tensor"],
                     help="storage of the deformed map: J^{-1} and JxW (10 values per point) or the final tensor (6)")
     ap.add_argument("--batch", type=int, default=0,

@@ -86,8 +86,12 @@ typedef struct mfcg_geometry {
 typedef enum mfcg_mode {
   MFCG_MODE_FUSED = 0,      /* Algorithm 5 with pre/post inside the operator pass (Sec. 5)        */
   MFCG_MODE_UNFUSED = 1,    /* Algorithm 1 with a separate operator, axpy, Jacobi and dot kernel   */
-  MFCG_MODE_SEMI_FUSED = 2  /* Algorithm 5 as separate "pre", operator and "post" kernels, the GPU
+  MFCG_MODE_SEMI_FUSED = 2, /* Algorithm 5 as separate "pre", operator and "post" kernels, the GPU
                                form of Sec. 6.4; FP64 vectors                                      */
+  MFCG_MODE_LOOP_FUSED = 3  /* Algorithm 1 with loop fusion inside its vector regions (Sec. 3.1, as
+                               compared in Sec. 5.4): operator, p.v, one pass for x, r and r.r, one
+                               for z = M^-1 r and r.z, the p update; FP64 vectors, the same iterates
+                               as MFCG_MODE_UNFUSED                                                  */
 } mfcg_mode;
 
 typedef enum mfcg_preconditioner {

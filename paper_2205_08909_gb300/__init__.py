@@ -39,7 +39,8 @@ class Problem:
     in every iteration instead of Algorithm 5's delayed update;
     coefficient: "constant" (a = 1) or "sin_x"
     (a = 1 + 0.5 sin(pi x)); mode: "fused" (Algorithm 5 inside the operator
-    pass), "unfused" (Algorithm 1, one kernel per vector operation) or
+    pass), "unfused" (Algorithm 1, one kernel per vector operation),
+    "loop_fused" (Algorithm 1 with loop fusion inside its vector regions) or
     "semi_fused" (Algorithm 5 as separate pre / operator / post kernels);
     preconditioner: "jacobi" or "none" (Algorithm 4);
     precision: "fp64", "double_float" (FP32 pairs, ~48 bits) or "fp32_inner"

@@ -89,6 +89,7 @@ struct mfcg_problem {
   cudaGraphExec_t graph_fused = nullptr;
   cudaGraphExec_t graph_unfused = nullptr;
   cudaGraphExec_t graph_semi = nullptr;
+  cudaGraphExec_t graph_loop = nullptr;
   int64_t launches = 0;
   std::vector<void*> owned;  // every device allocation
   int64_t nv() const { return ncomp * g.n_dofs; }  // length of every vector of the ABI
@@ -239,6 +240,25 @@ int enqueue_unfused_iteration(mfcg_problem* P, cudaEvent_t t0, cudaEvent_t t1) {
   return MFCG_OK;
 }
 
+// Algorithm 1 with loop fusion in its vector regions: operator (tile + tail),
+// p.v, one pass for x, r and r.r, one for z = M^-1 r and r.z, the p update
+int enqueue_loop_fused_iteration(mfcg_problem* P, cudaEvent_t t0, cudaEvent_t t1) {
+  UnfusedArgs u = unfused_args(P);
+  if (t0) CK(cudaEventRecord(t0, P->exec));
+  TileArgs a = base_args(P, P->op_prec, P->geo_op, MODE_OPERATOR);
+  a.prefetch_ahead = P->ahead_op;
+  a.in0 = u.p;
+  a.out0 = u.v;
+  CK(launch_tile(P->degree, MODE_OPERATOR, a, P->c, P->exec));
+  if (t1) CK(cudaEventRecord(t1, P->exec));
+  CK(launch_tail(P->degree, MODE_OPERATOR, a, P->exec));
+  CK(launch_unfused_dot(0, u, P->exec));   // alpha = e / p.v
+  CK(launch_loop_fused(0, u, P->exec));    // x += alpha p, r -= alpha v, gamma = r.r, convergence
+  CK(launch_loop_fused(1, u, P->exec));    // z = M^-1 r, beta = r.z / e
+  CK(launch_unfused_axpy(3, u, P->exec));  // p = z + beta p
+  return MFCG_OK;
+}
+
 // semi-fused Algorithm 5: "pre" kernel, operator (tile + tail), "post" kernel
 int enqueue_semi_iteration(mfcg_problem* P, cudaEvent_t t0, cudaEvent_t t1) {
   const int64_t n = P->nv();
@@ -255,12 +275,13 @@ int enqueue_semi_iteration(mfcg_problem* P, cudaEvent_t t0, cudaEvent_t t1) {
   return MFCG_OK;
 }
 
-enum IterKind { ITER_FUSED = 0, ITER_UNFUSED = 1, ITER_SEMI = 2 };
-constexpr int kLaunchesPerIter[3] = {2, 9, 4};
+enum IterKind { ITER_FUSED = 0, ITER_UNFUSED = 1, ITER_SEMI = 2, ITER_LOOP_FUSED = 3 };
+constexpr int kLaunchesPerIter[4] = {2, 9, 4, 6};
 
 int enqueue_iteration(mfcg_problem* P, int kind, int odd, cudaEvent_t t0, cudaEvent_t t1) {
   if (kind == ITER_FUSED) return enqueue_fused_iteration(P, odd, t0, t1);
   if (kind == ITER_UNFUSED) return enqueue_unfused_iteration(P, t0, t1);
+  if (kind == ITER_LOOP_FUSED) return enqueue_loop_fused_iteration(P, t0, t1);
   return enqueue_semi_iteration(P, t0, t1);
 }
 
@@ -329,7 +350,8 @@ int run_iterations(mfcg_problem* P, int kind, int maxit, IterStats& stats) {
     }
     return MFCG_OK;
   }
-  cudaGraphExec_t* gexec = kind == ITER_FUSED ? &P->graph_fused : (kind == ITER_UNFUSED ? &P->graph_unfused : &P->graph_semi);
+  cudaGraphExec_t* const graphs[4] = {&P->graph_fused, &P->graph_unfused, &P->graph_semi, &P->graph_loop};
+  cudaGraphExec_t* gexec = graphs[kind];
   if (!*gexec && (st = capture_graph(P, kind, gexec)) != MFCG_OK) return st;
   const int G = P->graph_iters;
   const int n_graphs = (maxit + G - 1) / G;
@@ -454,7 +476,8 @@ int solve_direct(mfcg_problem* P, const double* b, double* x_user, double rtol, 
     UnfusedArgs u = unfused_args(P);
     CK(launch_unfused_dot(3, u, P->exec));  // z0 = M^-1 r0, p0 = z0, e0 = r0.z0
     P->launches += 2;
-    if ((st = run_iterations(P, ITER_UNFUSED, maxit, stats)) != MFCG_OK) return st;
+    const int kind = P->opt.mode == MFCG_MODE_LOOP_FUSED ? ITER_LOOP_FUSED : ITER_UNFUSED;
+    if ((st = run_iterations(P, kind, maxit, stats)) != MFCG_OK) return st;
     CK(cudaMemcpyAsync(x_user, P->x, n * sizeof(double), cudaMemcpyDeviceToDevice, P->exec));
   }
   CK(cudaMemcpyAsync(P->h_state, P->state, sizeof(CGState), cudaMemcpyDeviceToHost, P->exec));
@@ -881,6 +904,7 @@ int mfcg_destroy(mfcg_problem* P) {
   if (P->graph_fused) cudaGraphExecDestroy(P->graph_fused);
   if (P->graph_unfused) cudaGraphExecDestroy(P->graph_unfused);
   if (P->graph_semi) cudaGraphExecDestroy(P->graph_semi);
+  if (P->graph_loop) cudaGraphExecDestroy(P->graph_loop);
   for (void* q : P->owned) cudaFree(q);
   if (P->h_state) cudaFreeHost(P->h_state);
   if (P->ev_in) cudaEventDestroy(P->ev_in);
@@ -917,7 +941,8 @@ int setup_impl(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, con
     return MFCG_INVALID_ARG;
   mfcg_options o{};
   if (opt) o = *opt;
-  if (o.mode != MFCG_MODE_FUSED && o.mode != MFCG_MODE_UNFUSED && o.mode != MFCG_MODE_SEMI_FUSED)
+  if (o.mode != MFCG_MODE_FUSED && o.mode != MFCG_MODE_UNFUSED && o.mode != MFCG_MODE_SEMI_FUSED &&
+      o.mode != MFCG_MODE_LOOP_FUSED)
     return MFCG_INVALID_ARG;
   if (o.preconditioner != MFCG_PRECOND_JACOBI && o.preconditioner != MFCG_PRECOND_NONE) return MFCG_INVALID_ARG;
   if (o.graph_iterations < 0 || (o.graph_iterations & 1)) return MFCG_INVALID_ARG;

@@ -223,30 +223,10 @@ __global__ void from_prec_kernel(const void* inv, double* out, int64_t n, int ac
 }
 
 // ---------------------------- unfused Algorithm 1 ----------------------------------
-// which: 0 a = p.v -> alpha = e/a; 1 gamma = r.r -> convergence; 2 e' = r.z -> beta;
-//        3 start: z = M^-1 r, p = z, e = r.z
-__global__ void unfused_dot_kernel(UnfusedArgs a, int which) {
-  CGState* st = a.state;
-  if (which != 3 && st->done) return;
-  double v[1] = {0.0};
-  for (int64_t i = blockIdx.x * (int64_t)kVecThreads + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * kVecThreads) {
-    if (which == 0) v[0] = fma(a.p[i], a.v[i], v[0]);
-    else if (which == 1) v[0] = fma(a.r[i], a.r[i], v[0]);
-    else if (which == 2) v[0] = fma(a.r[i], a.z[i], v[0]);
-    else {
-      const double z = a.diag_inv[i] * a.r[i];
-      a.p[i] = z;
-      v[0] = fma(a.r[i], z, v[0]);
-    }
-  }
-  double tot[1];
-  if (!grid_sum<1>(v, a.partial, &st->ticket, tot)) return;
-  if (threadIdx.x != 0) return;
-  const double s = tot[0];
-  if (which == 3) {
-    st->e_cur = s;
-    return;
-  }
+// Scalar step after the grid reduction s of one of the dot products of
+// Algorithm 1 (thread 0 of the last CTA).  which: 0 s = p.v -> alpha = e / s;
+// 1 s = r.r -> convergence test; 2 s = r.z -> beta = s / e, next iteration.
+__device__ void unfused_scalars(CGState* st, int which, double s) {
   if (which == 0) {
     if (!(s > 0.0) || !isfinite(s)) {
       st->done = 3;
@@ -270,6 +250,59 @@ __global__ void unfused_dot_kernel(UnfusedArgs a, int which) {
     st->e_cur = s;
     st->k += 1;
   }
+}
+
+// which: 0 a = p.v -> alpha = e/a; 1 gamma = r.r -> convergence; 2 e' = r.z -> beta;
+//        3 start: z = M^-1 r, p = z, e = r.z
+__global__ void unfused_dot_kernel(UnfusedArgs a, int which) {
+  CGState* st = a.state;
+  if (which != 3 && st->done) return;
+  double v[1] = {0.0};
+  for (int64_t i = blockIdx.x * (int64_t)kVecThreads + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * kVecThreads) {
+    if (which == 0) v[0] = fma(a.p[i], a.v[i], v[0]);
+    else if (which == 1) v[0] = fma(a.r[i], a.r[i], v[0]);
+    else if (which == 2) v[0] = fma(a.r[i], a.z[i], v[0]);
+    else {
+      const double z = a.diag_inv[i] * a.r[i];
+      a.p[i] = z;
+      v[0] = fma(a.r[i], z, v[0]);
+    }
+  }
+  double tot[1];
+  if (!grid_sum<1>(v, a.partial, &st->ticket, tot)) return;
+  if (threadIdx.x != 0) return;
+  if (which == 3) st->e_cur = tot[0];
+  else unfused_scalars(st, which, tot[0]);
+}
+
+// Algorithm 1 with loop fusion inside its vector regions (Sec. 3.1; the
+// "basic loop fusion" of the comparisons of Sec. 5.4 and Sec. 6): each pass
+// ends in the reduction of its region.  which: 0 x += alpha p, r -= alpha v
+// with gamma = r.r (convergence); 1 z = M^-1 r with e' = r.z (beta).  The
+// products and the reduction order are those of the one-operation kernels, so
+// both forms give bitwise the same iterates.
+__global__ void loop_fused_kernel(UnfusedArgs a, int which) {
+  CGState* st = a.state;
+  if (st->done) return;
+  const double alpha = st->alpha_cur;
+  double v[1] = {0.0};
+  for (int64_t i = blockIdx.x * (int64_t)kVecThreads + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * kVecThreads) {
+    if (which == 0) {
+      a.x[i] = fma(alpha, a.p[i], a.x[i]);
+      const double r = fma(-alpha, a.v[i], a.r[i]);
+      a.r[i] = r;
+      v[0] = fma(r, r, v[0]);
+    } else {
+      const double r = a.r[i];
+      const double z = a.diag_inv[i] * r;
+      a.z[i] = z;
+      v[0] = fma(r, z, v[0]);
+    }
+  }
+  double tot[1];
+  if (!grid_sum<1>(v, a.partial, &st->ticket, tot)) return;
+  if (threadIdx.x != 0) return;
+  unfused_scalars(st, which + 1, tot[0]);
 }
 
 // which: 0 x += alpha p; 1 r -= alpha v; 2 z = M^-1 r; 3 p = z + beta p
@@ -395,6 +428,11 @@ cudaError_t launch_unfused_dot(int which, const UnfusedArgs& a, cudaStream_t s) 
 
 cudaError_t launch_unfused_axpy(int which, const UnfusedArgs& a, cudaStream_t s) {
   unfused_axpy_kernel<<<grid_for(a.n), kVecThreads, 0, s>>>(a, which);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_loop_fused(int which, const UnfusedArgs& a, cudaStream_t s) {
+  loop_fused_kernel<<<grid_for(a.n), kVecThreads, 0, s>>>(a, which);
   return cudaGetLastError();
 }
 

@@ -430,6 +430,7 @@ struct UnfusedArgs {
 };
 cudaError_t launch_unfused_dot(int which, const UnfusedArgs& a, cudaStream_t s);
 cudaError_t launch_unfused_axpy(int which, const UnfusedArgs& a, cudaStream_t s);
+cudaError_t launch_loop_fused(int which, const UnfusedArgs& a, cudaStream_t s);
 cudaError_t launch_cg_init(CGState* st, const double* b, const double* r0, int64_t n, double rtol, int maxit,
                            int fixed, double* partial, int x_every_iter, cudaStream_t s);
 cudaError_t launch_residual(const double* b, const double* ax, double* r, int64_t n, cudaStream_t s);

@@ -38,6 +38,9 @@ WORKLOADS = {
     "q2_8cube": Workload("q2_8cube", 2, (8, 8, 8)),
     "q4_64cube": Workload("q4_64cube", 4, (64, 64, 64)),
     "q6_48cube_deformed": Workload("q6_48cube_deformed", 6, (48, 48, 48), 0.05, "sin_x"),
+    # the same deformed problem on a smaller mesh (7.2 M unknowns, about 1.5 GB of
+    # vectors and geometry): the case for multi-pass profiles of its kernel
+    "q6_32cube_deformed": Workload("q6_32cube_deformed", 6, (32, 32, 32), 0.05, "sin_x"),
     "q4_128cube": Workload("q4_128cube", 4, (128, 128, 128)),
 }
 

@@ -123,7 +123,8 @@ CG_CASES = [
 
 
 SOLVER_VARIANTS = [("fused", "fp64"), ("unfused", "fp64"), ("fused", "double_float"), ("unfused", "double_float"),
-                   ("fused", "fp32_inner"), ("semi_fused", "fp64"), ("semi_fused", "double_float")]
+                   ("fused", "fp32_inner"), ("semi_fused", "fp64"), ("semi_fused", "double_float"),
+                   ("loop_fused", "fp64"), ("loop_fused", "double_float")]
 FIXED_VARIANTS = [v for v in SOLVER_VARIANTS if v[1] != "fp32_inner"]
 
 
@@ -219,6 +220,27 @@ def test_initial_guess_and_host_arrays(mfcg):
     xh, info_h = prob.cg_solve_host(bh, xh, rtol=1e-10)
     assert torch.equal(xh, xd.cpu())
     prob.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "double_float"])
+@pytest.mark.parametrize("p,cells,rtol,maxit", [(4, (6, 5, 4), 1e-10, 2000), (2, (9, 7, 8), 0.0, 13),
+                                                (3, (4, 3, 5), 0.0, 1)])
+def test_loop_fused_gives_the_unfused_iterates(mfcg, precision, p, cells, rtol, maxit):
+    # loop fusion changes neither a product nor the reduction order of
+    # Algorithm 1: both forms stop at the same iteration with identical x
+    nn = tuple(p * c + 1 for c in cells)
+    out = {}
+    for mode in ("unfused", "loop_fused"):
+        prob = mfcg.Problem(p, cells, mode=mode, precision=precision)
+        b = _to_dev(prob, inputs.boundary_zeroed(inputs.random_vector(prob.n_dofs, salt=23), nn))
+        x, info = prob.cg_solve(b, rtol=rtol, maxit=maxit)
+        out[mode] = (x.cpu(), info)
+        prob.close()
+    (xu, iu), (xl, il) = out["unfused"], out["loop_fused"]
+    assert il["iterations"] == iu["iterations"]
+    assert il["converged"] == iu["converged"]
+    assert il["residual_sq_est"] == iu["residual_sq_est"]
+    assert torch.equal(xl, xu)
 
 
 @pytest.mark.parametrize("mode,precision", SOLVER_VARIANTS)
@@ -739,7 +761,7 @@ def test_fp64_pipe_sweeps_match_oracle(mfcg, p, cells, amp, coef, tile):
     prob.close()
 
 
-@pytest.mark.parametrize("mode", ["fused", "unfused", "semi_fused"])
+@pytest.mark.parametrize("mode", ["fused", "unfused", "semi_fused", "loop_fused"])
 def test_fp64_pipe_solve_matches_oracle(mfcg, mode):
     op = _oracle_problem(4, (5, 6, 4))
     A = fem.assemble(op)
