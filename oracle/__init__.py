@@ -7,7 +7,8 @@ never calls it and shares no code with it.
 Contents
 --------
 * ``fem``      -- 1D Gauss-Lobatto / Gauss rules, Lagrange tables, geometry
-                  (Cartesian or the sine-deformed map), element matrices of the
+                  (Cartesian, the sine-deformed map or its tri-quadratic
+                  interpolant per cell), element matrices of the
                   Laplacian (Eq. 5), element-by-element assembly into a sparse
                   matrix (Eq. 4), Dirichlet identity rows, the manufactured
                   right-hand side, sampled operator rows and the L2 error.

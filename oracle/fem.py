@@ -116,13 +116,17 @@ class Problem:
 
     cells = (N_x, N_y, N_z); ``amplitude`` A deforms the mesh by
     x -> X + A sin(2 pi X) sin(2 pi Y) sin(2 pi Z) on each component (A = 0 is
-    the Cartesian mesh); ``coef`` selects a(x); ``op`` the operator."""
+    the Cartesian mesh); ``coef`` selects a(x); ``op`` the operator;
+    ``geometry_degree`` 0 uses that map itself, 2 its tri-quadratic
+    interpolant in every cell through the 3^3 points {0, 1/2, 1}^3 of the
+    reference cell (the "quadratic geometry" of Sec. 2.2)."""
 
     p: int
     cells: tuple[int, int, int]
     amplitude: float = 0.0
     coef: int = COEF_CONSTANT
     op: int = OP_LAPLACE
+    geometry_degree: int = 0
 
     @property
     def nodes_per_dim(self) -> tuple[int, int, int]:
@@ -175,18 +179,27 @@ def local_to_global(prob: Problem, cell_ids: np.ndarray | None = None) -> np.nda
     return gi + nx * (gj + ny * gk)
 
 
+QUADRATIC_SUPPORT = np.array([0.0, 0.5, 1.0])
+
+
 def quadrature_geometry(prob: Problem, cell_ids: np.ndarray | None = None, n_q1d: int | None = None):
     """Physical points, Jacobians, determinants and weights at the tensor Gauss
     points of the requested cells.
 
     Returns (x[e,q,3], J[e,q,3,3], detJ[e,q], w[q]).  J_ij = d x_i / d xhat_j
-    of the map xhat -> X = h (c + xhat) -> x = X + A s(X) (1,1,1)."""
+    of the map xhat -> X = h (c + xhat) -> x = X + A s(X) (1,1,1), or of its
+    tri-quadratic interpolant (geometry_degree 2)."""
     n = prob.p + 1 if n_q1d is None else n_q1d
     g, w1 = gauss_rule(n)
     qa = np.tile(np.arange(n), n * n)
     qb = np.tile(np.repeat(np.arange(n), n), n)
     qc = np.repeat(np.arange(n), n * n)
     w = w1[qa] * w1[qb] * w1[qc]
+    if prob.geometry_degree == 2:
+        x, J = quadratic_geometry(quadratic_support_points(prob, cell_ids), g)
+        return x, J, np.linalg.det(J), w
+    if prob.geometry_degree != 0:
+        raise ValueError("geometry_degree is 0 (exact map) or 2 (tri-quadratic)")
     h = np.array([1.0 / c for c in prob.cells])
     cx, cy, cz = cell_index_arrays(prob, cell_ids)
     X = h[0] * (cx[:, None] + g[qa][None, :])
@@ -199,6 +212,37 @@ def quadrature_geometry(prob: Problem, cell_ids: np.ndarray | None = None, n_q1d
     J = dPhi * h[None, None, None, :]
     detJ = np.linalg.det(J)
     return x, J, detJ, w
+
+
+def quadratic_support_points(prob: Problem, cell_ids: np.ndarray | None = None) -> np.ndarray:
+    """pts[e, a, b, c, d]: coordinate d of the exact map at the reference point
+    (s_a, s_b, s_c), s = (0, 1/2, 1), of each requested cell -- the 27 x 3
+    values per cell that define the tri-quadratic geometry."""
+    h = np.array([1.0 / c for c in prob.cells])
+    cx, cy, cz = cell_index_arrays(prob, cell_ids)
+    s3 = QUADRATIC_SUPPORT
+    X = h[0] * (cx[:, None, None, None] + s3[:, None, None][None])
+    Y = h[1] * (cy[:, None, None, None] + s3[None, :, None][None])
+    Z = h[2] * (cz[:, None, None, None] + s3[None, None, :][None])
+    X, Y, Z = np.broadcast_arrays(X, Y, Z)
+    s, _ = _sine_bump(X, Y, Z)
+    return np.stack([X, Y, Z], axis=-1) + prob.amplitude * s[..., None]
+
+
+def quadratic_geometry(pts: np.ndarray, g: np.ndarray):
+    """x[e,q,3] and J[e,q,3,3] of the tri-quadratic map
+    x(xhat) = sum_abc pts[e,a,b,c] L_a(xhat_1) L_b(xhat_2) L_c(xhat_3)
+    (L the quadratic Lagrange polynomials through 0, 1/2, 1) at the tensor
+    points of the 1D points g (q = qa + n (qb + n qc))."""
+    n = len(g)
+    V = lagrange_values(QUADRATIC_SUPPORT, g)       # [q1, a]
+    D = lagrange_derivatives(QUADRATIC_SUPPORT, g)  # [q1, a]
+    e = pts.shape[0]
+    x = np.einsum("eabcd,xa,yb,zc->ezyxd", pts, V, V, V).reshape(e, n ** 3, 3)
+    j0 = np.einsum("eabcd,xa,yb,zc->ezyxd", pts, D, V, V).reshape(e, n ** 3, 3)
+    j1 = np.einsum("eabcd,xa,yb,zc->ezyxd", pts, V, D, V).reshape(e, n ** 3, 3)
+    j2 = np.einsum("eabcd,xa,yb,zc->ezyxd", pts, V, V, D).reshape(e, n ** 3, 3)
+    return x, np.stack([j0, j1, j2], axis=-1)
 
 
 def coefficient(prob: Problem, x: np.ndarray) -> np.ndarray:

@@ -153,18 +153,20 @@ def test_q1_27_point_stencil():
                 assert abs(row[c + dx + nx * (dy + nx * dz)] - vals[cls] * h) < 1e-14
 
 
-@pytest.mark.parametrize("amp,coef", [(0.0, fem.COEF_CONSTANT), (0.05, fem.COEF_SIN_X), (0.08, fem.COEF_CONSTANT)])
-def test_symmetric_positive_definite(amp, coef):
-    prob = fem.Problem(3, (2, 3, 2), amp, coef)
+@pytest.mark.parametrize("amp,coef,gdeg", [(0.0, fem.COEF_CONSTANT, 0), (0.05, fem.COEF_SIN_X, 0),
+                                           (0.08, fem.COEF_CONSTANT, 0), (0.08, fem.COEF_SIN_X, 2)])
+def test_symmetric_positive_definite(amp, coef, gdeg):
+    prob = fem.Problem(3, (2, 3, 2), amp, coef, geometry_degree=gdeg)
     A = fem.assemble(prob).toarray()
     assert np.abs(A - A.T).max() < 1e-14 * np.abs(A).max()
     np.linalg.cholesky(A)
     assert np.linalg.eigvalsh(A).min() > 0
 
 
-@pytest.mark.parametrize("amp,coef", [(0.0, fem.COEF_CONSTANT), (0.05, fem.COEF_SIN_X), (0.08, fem.COEF_SIN_X)])
-def test_neumann_constant_null_space(amp, coef):
-    prob = fem.Problem(4, (2, 2, 3), amp, coef)
+@pytest.mark.parametrize("amp,coef,gdeg", [(0.0, fem.COEF_CONSTANT, 0), (0.05, fem.COEF_SIN_X, 0),
+                                           (0.08, fem.COEF_SIN_X, 0), (0.08, fem.COEF_SIN_X, 2)])
+def test_neumann_constant_null_space(amp, coef, gdeg):
+    prob = fem.Problem(4, (2, 2, 3), amp, coef, geometry_degree=gdeg)
     A = fem.assemble(prob, dirichlet=False)
     r = A @ np.ones(prob.n_dofs)
     assert np.abs(r).max() < 1e-14 * abs(A).max() * 10
@@ -194,6 +196,93 @@ def test_deformed_jacobian_matches_finite_differences():
             np.testing.assert_allclose(J[e, q], Jfd, atol=1e-8)
             np.testing.assert_allclose(x[e, q], phys(xh), atol=1e-15)
             assert detJ[e, q] > 0
+
+
+# ---------------------------------------------------------------- tri-quadratic geometry
+
+
+def test_quadratic_geometry_is_exact_for_triquadratic_maps():
+    # a map of degree <= 2 in each reference coordinate is its own interpolant:
+    # its values and derivatives at the Gauss points come out exactly
+    rng = np.random.default_rng(17)
+    C = rng.standard_normal((3, 3, 3, 3))  # C[d, i, j, k]: coefficient of u^i v^j w^k in component d
+
+    def f(u, v, w):
+        return np.array([sum(C[d, i, j, k] * u ** i * v ** j * w ** k
+                             for i in range(3) for j in range(3) for k in range(3)) for d in range(3)])
+
+    def df(u, v, w, e):
+        out = np.zeros(3)
+        for d in range(3):
+            for i in range(3):
+                for j in range(3):
+                    for k in range(3):
+                        ex = [i, j, k]
+                        if ex[e] == 0:
+                            continue
+                        fac = ex[e]
+                        ex[e] -= 1
+                        out[d] += C[d, i, j, k] * fac * u ** ex[0] * v ** ex[1] * w ** ex[2]
+        return out
+
+    s3 = fem.QUADRATIC_SUPPORT
+    pts = np.array([[[f(s3[a], s3[b], s3[c]) for c in range(3)] for b in range(3)] for a in range(3)])[None]
+    g, _ = fem.gauss_rule(4)
+    x, J = fem.quadratic_geometry(pts, g)
+    for q in (0, 7, 21, 42, 63):
+        qa, qb, qc = q % 4, (q // 4) % 4, q // 16
+        u, v, w = g[qa], g[qb], g[qc]
+        np.testing.assert_allclose(x[0, q], f(u, v, w), atol=1e-13)
+        for e in range(3):
+            np.testing.assert_allclose(J[0, q, :, e], df(u, v, w, e), atol=1e-12)
+
+
+@pytest.mark.parametrize("p", [1, 3, 5])
+def test_quadratic_geometry_of_cartesian_cells_is_exact(p):
+    # the interpolant of an affine map is the map: same element matrices
+    pe = fem.Problem(p, (3, 2, 4))
+    pq = fem.Problem(p, (3, 2, 4), geometry_degree=2)
+    ids = np.array([0, 5, 23])
+    Ae, Aq = fem.element_matrices(pe, ids), fem.element_matrices(pq, ids)
+    np.testing.assert_allclose(Aq, Ae, atol=1e-13 * np.abs(Ae).max())
+
+
+def test_quadratic_geometry_interpolates_the_deformed_map():
+    # through the 27 support points of every cell, and within O(h^3) of the
+    # map (positions and d x / d xhat, which carries a factor h) between them
+    prob = fem.Problem(2, (3, 4, 3), 0.07, geometry_degree=2)
+    ids = np.array([0, 11, 35])
+    x, _ = fem.quadratic_geometry(fem.quadratic_support_points(prob, ids), fem.QUADRATIC_SUPPORT)
+    exact = fem.Problem(2, (3, 4, 3), 0.07)
+    h = np.array([1 / 3, 1 / 4, 1 / 3])
+    cx, cy, cz = fem.cell_index_arrays(exact, ids)
+    s3 = fem.QUADRATIC_SUPPORT
+    for t in range(len(ids)):
+        for q in range(27):
+            a, b, c = q % 3, (q // 3) % 3, q // 9
+            X = h * (np.array([cx[t], cy[t], cz[t]]) + np.array([s3[a], s3[b], s3[c]]))
+            sb = np.prod(np.sin(2 * np.pi * X))
+            np.testing.assert_allclose(x[t, q], X + 0.07 * sb, atol=1e-15)
+    errs = []
+    for N in (8, 16):
+        x0, J0, _, _ = fem.quadrature_geometry(fem.Problem(2, (N, N, N), 0.05))
+        x2, J2, _, _ = fem.quadrature_geometry(fem.Problem(2, (N, N, N), 0.05, geometry_degree=2))
+        errs.append((np.abs(x0 - x2).max(), np.abs(J0 - J2).max()))
+    for m in range(2):
+        assert abs(math.log2(errs[0][m] / errs[1][m]) - 3) < 0.15, errs
+
+
+def test_l2_convergence_rate_quadratic_geometry():
+    # the tri-quadratic cells tile the unit cube exactly (the map fixes the
+    # boundary), so the discrete solution keeps the rate p + 1
+    for p, Ns, tol in ((2, (2, 4, 8), 0.1), (3, (4, 8), 0.4)):
+        errs = []
+        for N in Ns:
+            prob = fem.Problem(p, (N, N, N), 0.05, fem.COEF_SIN_X, geometry_degree=2)
+            u = spla.spsolve(fem.assemble(prob).tocsc(), fem.rhs(prob))
+            errs.append(fem.l2_error(prob, u))
+        rate = math.log(errs[-2] / errs[-1]) / math.log(Ns[-1] / Ns[-2])
+        assert abs(rate - (p + 1)) <= tol, (p, errs, rate)
 
 
 def test_forcing_matches_finite_difference_operator():
