@@ -84,7 +84,15 @@ def stored_traffic(workload: str, precision: str):
 
 def geometry_values(geometry: str) -> int:
     """Values stored per quadrature point: J^{-1} and JxW a (10) or the final tensor (6)."""
-    return {"affine": 0, "deformed": 10, "deformed_tensor": 6}[geometry]
+    return {"affine": 0, "deformed": 10, "deformed_tensor": 6, "deformed_quadratic": 0}[geometry]
+
+
+def geometry_bytes_per_dof(geometry: str, degree: int, n_cells: int, n_dofs: int) -> float:
+    """Stored geometry read per iteration and unknown: the per-point values, or
+    the 27 x 3 support-point coordinates per cell of the tri-quadratic map."""
+    if geometry == "deformed_quadratic":
+        return 81 * 8.0 * n_cells / n_dofs
+    return geometry_values(geometry) * 8.0 * n_cells * (degree + 1) ** 3 / n_dofs
 
 
 DEFAULT_TILE = {"affine": [0, 16, 8, 5, 4, 3, 3, 2, 2], "deformed": [0, 8, 4, 4, 3, 2, 2, 2, 2]}
@@ -155,9 +163,20 @@ def deformed_cell_cost(n1: int, unit: str, geometry: str) -> float:
     pencils = n1 * n1
     sweeps = 6 * pencils * eo_product_cost(n1, unit) + 6 * pencils * eo_product_cost(n1, unit, anti=True)
     if unit == "flop":
+        if geometry == "deformed_quadratic":
+            # per point: Jacobian and position 50, cofactors 27, det 5, the
+            # factor w a / det ~5 (sine not counted), C^T (f C g) 33; per cell
+            # the line sums, 48 flops for each of 9 (p+1)^2 (d, a, line) items
+            return sweeps + (2 + 120 + 1) * n1 ** 3 + 48 * 9 * n1 ** 2
         metric = 42 if geometry == "deformed" else 18
         return sweeps + (2 + metric + 1) * n1 ** 3
     dot3 = 4 + 12 * 2 + 3
+    axby = 4 + 12 + 3
+    if geometry == "deformed_quadratic":
+        # 17 three-term sums, 9 cofactor pairs, 3 pair products per point; per
+        # (d, a, line) item 6 three-term sums and 9 accumulations
+        metric = 17 * dot3 + 9 * axby + 3 * 7
+        return sweeps + (2 * 11 + metric + 11) * n1 ** 3 + (6 * dot3 + 9 * axby) * 9 * n1 ** 2
     metric = 3 * dot3 if geometry == "deformed_tensor" else 6 * dot3 + 3 * 7
     return sweeps + (2 * 11 + metric + 11) * n1 ** 3
 
@@ -503,8 +522,7 @@ def run_ours(args, world, rank, local):
 
     dof_its = w.n_dofs * iters * K * world
     # algorithmic bytes per unknown: the vectors, plus the stored geometry of deformed meshes
-    n_qp = n_cells * (w.degree + 1) ** 3
-    geo_bytes_per_dof = geometry_values(geometry) * 8.0 * n_qp / w.n_dofs
+    geo_bytes_per_dof = geometry_bytes_per_dof(geometry, w.degree, n_cells, w.n_dofs)
     bytes_per_dof = ALGORITHMIC_BYTES_PER_DOF + geo_bytes_per_dof
     # stored values are 8 bytes (FP64, double-float pairs) or 4 bytes (FP32)
     kernel_bytes_per_dof = bytes_per_dof / 2 if main_prec == "fp32_inner" else bytes_per_dof
@@ -610,7 +628,7 @@ def run_ours(args, world, rank, local):
         achieved = hbm_gbs
         roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                     "frac": round(achieved / hbm, 4), "traffic": traffic, "peak_kind": peak_kind}
-    roofline.update({"kernel": f"tile_kernel<{w.degree}, MODE_CG, GEOM_{ {'affine': 'AFFINE', 'deformed': 'DEFORMED', 'deformed_tensor': 'TENSOR'}[geometry]}, {'fp64, tensor-core contractions' if tc_main else main_prec}>",
+    roofline.update({"kernel": f"tile_kernel<{w.degree}, MODE_CG, GEOM_{ {'affine': 'AFFINE', 'deformed': 'DEFORMED', 'deformed_tensor': 'TENSOR', 'deformed_quadratic': 'QUAD'}[geometry]}, {'fp64, tensor-core contractions' if tc_main else main_prec}>",
                      "tile": list(eff_tile),
                      "kernel_ms": round(kernel_ms, 4),
                      "hbm_view": {"achieved_gbs": round(hbm_gbs, 1), "peak_gbs": hbm, "peak_kind": peak_kind,
@@ -809,8 +827,9 @@ def main():
     ap.add_argument("--skip-dc", action="store_true", help="skip the FP32-inner defect-correction solve")
     ap.add_argument("--skip-variants", action="store_true", help="skip the FP64 comparators")
     ap.add_argument("--skip-batch", action="store_true", help="skip the short batched and block runs")
-    ap.add_argument("--geometry", default="", choices=["", "deformed", "deformed_tensor"],
-                    help="storage of the deformed map: J^{-1} and JxW (10 values per point) or the final tensor (6)")
+    ap.add_argument("--geometry", default="", choices=["", "deformed", "deformed_tensor", "deformed_quadratic"],
+                    help="storage of the deformed map: J^{-1} and JxW (10 values per point), the final tensor (6), "
+                         "or the tri-quadratic map (27 x 3 coordinates per cell, metric computed per point)")
     ap.add_argument("--batch", type=int, default=0,
                     help="run the batched form on this many seeded problems instead of the headline workload")
     ap.add_argument("--rhs-block", action="store_true",

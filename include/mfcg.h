@@ -62,9 +62,14 @@ typedef enum mfcg_geometry_kind {
                                "inverse Jacobian load" variant (10 values per point)                        */
   MFCG_GEOM_DEFORMED_TENSOR = 2, /* the same mesh with the symmetric tensor J^{-1} (w det J a) J^{-T}
                                stored per point, Sec. 2.2 "final tensor load" variant (6 values per point) */
-  MFCG_GEOM_USER = 3        /* per-point data supplied by the caller (mfcg_geometry.user_data), stored
+  MFCG_GEOM_USER = 3,       /* per-point data supplied by the caller (mfcg_geometry.user_data), stored
                                like MFCG_GEOM_DEFORMED: any cell geometry and coefficient whose
                                mesh is logically the Nx x Ny x Nz box of cells                       */
+  MFCG_GEOM_DEFORMED_QUADRATIC = 4 /* the deformed mesh represented per cell by the tri-quadratic
+                               interpolant of its map through the reference points {0, 1/2, 1}^3:
+                               27 x 3 coordinates stored per cell, the Jacobian, its inverse and
+                               a(x) computed at every quadrature point, Sec. 2.2 "quadratic geometry
+                               compute" variant (scalar operator: components = 1)                */
 } mfcg_geometry_kind;
 
 typedef enum mfcg_coefficient_kind {

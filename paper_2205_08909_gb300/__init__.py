@@ -33,7 +33,9 @@ class Problem:
 
     degree: 1..8; cells: (Nx, Ny, Nz); amplitude: sine deformation of the mesh
     (needs geometry="deformed", which stores J^{-1} and JxW per quadrature
-    point, or "deformed_tensor", which stores the symmetric J^{-1} JxW a J^{-T});
+    point, "deformed_tensor", which stores the symmetric J^{-1} JxW a J^{-T}, or
+    "deformed_quadratic", the tri-quadratic interpolant of the map per cell with
+    the metric computed at each point);
     geometry="user" takes those ten values per point from user_data (host array,
     cells x 10 x (degree+1)^3, cells lexicographic); x_every_iteration: update x
     in every iteration instead of Algorithm 5's delayed update;

@@ -19,7 +19,7 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED_DEGREE", 3: "OUT_OF_MEMORY"
           5: "NOT_CONVERGED", 6: "BREAKDOWN", 7: "DEVICE_TIMEOUT", 8: "SCRATCH_TOO_SMALL"}
 OK, NOT_CONVERGED, BREAKDOWN = 0, 5, 6
 
-GEOM = {"affine": 0, "deformed": 1, "deformed_tensor": 2, "user": 3}
+GEOM = {"affine": 0, "deformed": 1, "deformed_tensor": 2, "user": 3, "deformed_quadratic": 4}
 COEF = {"constant": 0, "sin_x": 1}
 MODE = {"fused": 0, "unfused": 1, "semi_fused": 2, "loop_fused": 3}
 PRECONDITIONER = {"jacobi": 0, "none": 1}

@@ -113,6 +113,14 @@ struct mfcg_batch {
 
 namespace {
 
+// internal geometry kind of an mfcg_geometry_kind (MFCG_GEOM_USER data is stored like MFCG_GEOM_DEFORMED)
+int geom_kind_of(int kind) {
+  if (kind == MFCG_GEOM_AFFINE) return GEOM_AFFINE;
+  if (kind == MFCG_GEOM_DEFORMED_TENSOR) return GEOM_TENSOR;
+  if (kind == MFCG_GEOM_DEFORMED_QUADRATIC) return GEOM_QUAD;
+  return GEOM_DEFORMED;
+}
+
 #define CK(call)                                   \
   do {                                             \
     cudaError_t e_ = (call);                       \
@@ -225,6 +233,7 @@ int enqueue_unfused_iteration(mfcg_problem* P, cudaEvent_t t0, cudaEvent_t t1) {
   // v = A p
   TileArgs a = base_args(P, P->op_prec, P->geo_op, MODE_OPERATOR);
   a.prefetch_ahead = P->ahead_op;
+  a.stop_on_done = 1;
   a.in0 = u.p;
   a.out0 = u.v;
   CK(launch_tile(P->degree, MODE_OPERATOR, a, P->c, P->exec));
@@ -247,6 +256,7 @@ int enqueue_loop_fused_iteration(mfcg_problem* P, cudaEvent_t t0, cudaEvent_t t1
   if (t0) CK(cudaEventRecord(t0, P->exec));
   TileArgs a = base_args(P, P->op_prec, P->geo_op, MODE_OPERATOR);
   a.prefetch_ahead = P->ahead_op;
+  a.stop_on_done = 1;
   a.in0 = u.p;
   a.out0 = u.v;
   CK(launch_tile(P->degree, MODE_OPERATOR, a, P->c, P->exec));
@@ -265,6 +275,7 @@ int enqueue_semi_iteration(mfcg_problem* P, cudaEvent_t t0, cudaEvent_t t1) {
   CK(launch_semi_pre(n, P->state, P->x, P->ur, P->up, P->uv, P->diag_inv, P->exec));
   TileArgs a = base_args(P, P->op_prec, P->geo_op, MODE_OPERATOR);
   a.prefetch_ahead = P->ahead_op;
+  a.stop_on_done = 1;
   a.in0 = P->up;
   a.out0 = P->uv;
   if (t0) CK(cudaEventRecord(t0, P->exec));
@@ -629,8 +640,7 @@ std::vector<std::array<int, 3>> tile_candidates(int degree, int geom_kind, int p
 
 int setup_autotuned(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, mfcg_options o,
                     void* cuda_stream, mfcg_problem** out) {
-  const int kind = geom->kind == MFCG_GEOM_AFFINE ? GEOM_AFFINE
-                   : (geom->kind == MFCG_GEOM_DEFORMED_TENSOR ? GEOM_TENSOR : GEOM_DEFORMED);
+  const int kind = geom_kind_of(geom->kind);
   std::array<int, 3> best{0, 0, 0};
   double best_s = 1e300;
   for (const auto& t : tile_candidates(degree, kind, o.precision)) {
@@ -933,7 +943,7 @@ int setup_impl(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, con
   if (mesh->nx < 1 || mesh->ny < 1 || mesh->nz < 1) return MFCG_INVALID_ARG;
   if (!(std::fabs(mesh->amplitude) < 0.1)) return MFCG_INVALID_ARG;
   if (geom->kind != MFCG_GEOM_AFFINE && geom->kind != MFCG_GEOM_DEFORMED && geom->kind != MFCG_GEOM_DEFORMED_TENSOR &&
-      geom->kind != MFCG_GEOM_USER)
+      geom->kind != MFCG_GEOM_USER && geom->kind != MFCG_GEOM_DEFORMED_QUADRATIC)
     return MFCG_INVALID_ARG;
   if (geom->kind == MFCG_GEOM_USER && !geom->user_data) return MFCG_INVALID_ARG;
   if (geom->coefficient != MFCG_COEF_CONSTANT && geom->coefficient != MFCG_COEF_SIN_X) return MFCG_INVALID_ARG;
@@ -953,6 +963,7 @@ int setup_impl(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, con
   if (o.true_residual != 0 && o.true_residual != 1) return MFCG_INVALID_ARG;
   if ((o.components != 0 && o.components != 1 && o.components != 3) || (o.components > 1 && o.mode != MFCG_MODE_FUSED))
     return MFCG_INVALID_ARG;
+  if (o.components > 1 && geom->kind == MFCG_GEOM_DEFORMED_QUADRATIC) return MFCG_INVALID_ARG;
   if (o.operator_kind != MFCG_OP_LAPLACE && o.operator_kind != MFCG_OP_MASS) return MFCG_INVALID_ARG;
   if (o.operator_kind == MFCG_OP_MASS && geom->kind == MFCG_GEOM_DEFORMED_TENSOR) return MFCG_INVALID_ARG;
   if (o.fp64_contraction != MFCG_FP64_TENSOR_CORES && o.fp64_contraction != MFCG_FP64_PIPE) return MFCG_INVALID_ARG;
@@ -977,8 +988,7 @@ int setup_impl(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, con
   P->opt = o;
   P->ncomp = o.components ? o.components : 1;
   P->op_kind = o.operator_kind == MFCG_OP_MASS ? OP_MASS : OP_LAPLACE;
-  P->geom_kind = geom->kind == MFCG_GEOM_AFFINE ? GEOM_AFFINE
-                  : (geom->kind == MFCG_GEOM_DEFORMED_TENSOR ? GEOM_TENSOR : GEOM_DEFORMED);
+  P->geom_kind = geom_kind_of(geom->kind);
   P->geom.user_data = nullptr;  // read during set-up only
   // the defect correction forms its outer residual with the native FP64
   // operator: its true-residual floor is 2^5 lower than the double-float one
@@ -1062,8 +1072,7 @@ int setup_impl(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, con
   if (st == MFCG_OK) st = alloc_bytes(P, &P->shell, P->ncomp * g.n_tiles * g.face_stride * 8);
   const int64_t nparts = std::max<int64_t>(g.n_tiles + P->tail_ctas, 152 * 8);
   if (st == MFCG_OK) st = alloc_bytes(P, &P->partial, nparts * 8 * 8);
-  const int64_t ngeo =
-      (int64_t)N[0] * N[1] * N[2] * geo_values(P->geom_kind) * (degree + 1) * (degree + 1) * (degree + 1);
+  const int64_t ngeo = (int64_t)N[0] * N[1] * N[2] * geo_per_cell(P->geom_kind, degree);
   if (share) {
     P->geo = share->geo;
     P->geo_op = share->geo_op;

@@ -111,7 +111,25 @@ __global__ void reorder_kernel(const TileGeom g, const double* in, double* out, 
 // det J = h_x h_y h_z (1 + A sum grad s).  GEOM_DEFORMED stores [cell][10][nq]:
 // J^{-1} row-major, then w_q det J a(x_q); GEOM_TENSOR stores [cell][6][nq]:
 // the upper triangle of C = (w_q det J a) J^{-1} J^{-T}.
+// GEOM_QUAD stores [cell][3][27]: the map at the reference points (a, b, c) / 2.
 __global__ void geometry_kernel(const TileGeom g, const OperatorCoeffs c, int geom, double* geo) {
+  if (geom == GEOM_QUAD) {
+    const int64_t total = (int64_t)g.N[0] * g.N[1] * g.N[2] * 27;
+    const double twopi = 6.28318530717958647692;
+    for (int64_t t = blockIdx.x * (int64_t)kVecThreads + threadIdx.x; t < total; t += (int64_t)gridDim.x * kVecThreads) {
+      const int64_t cell = t / 27;
+      const int m = (int)(t - cell * 27);
+      const int cx = (int)(cell % g.N[0]), cy = (int)((cell / g.N[0]) % g.N[1]), cz = (int)(cell / ((int64_t)g.N[0] * g.N[1]));
+      const double X = c.h[0] * (cx + 0.5 * (m % 3)), Y = c.h[1] * (cy + 0.5 * ((m / 3) % 3)),
+                   Z = c.h[2] * (cz + 0.5 * (m / 9));
+      const double s = c.amplitude * sin(twopi * X) * sin(twopi * Y) * sin(twopi * Z);
+      double* out = geo + cell * 81 + m;
+      out[0] = X + s;
+      out[27] = Y + s;
+      out[54] = Z + s;
+    }
+    return;
+  }
   const int n1 = g.p + 1, nq = n1 * n1 * n1;
   const int nv = geo_values(geom);
   const int64_t total = (int64_t)g.N[0] * g.N[1] * g.N[2] * nq;
@@ -372,7 +390,7 @@ cudaError_t launch_reorder(const TileGeom& g, const double* in, double* out, int
 }
 
 cudaError_t launch_geometry(const TileGeom& g, const OperatorCoeffs& c, int geom, double* geo, cudaStream_t s) {
-  const int64_t total = (int64_t)g.N[0] * g.N[1] * g.N[2] * (g.p + 1) * (g.p + 1) * (g.p + 1);
+  const int64_t total = (int64_t)g.N[0] * g.N[1] * g.N[2] * (geom == GEOM_QUAD ? 27 : (g.p + 1) * (g.p + 1) * (g.p + 1));
   geometry_kernel<<<grid_for(total), kVecThreads, 0, s>>>(g, c, geom, geo);
   return cudaGetLastError();
 }

@@ -314,10 +314,19 @@ __host__ __device__ inline void prepare_iteration_scalars(CGState* st) {
 
 enum TileMode { MODE_OPERATOR = 0, MODE_CG = 1, MODE_RHS = 2, MODE_DIAG = 3 };
 
-enum GeomKind { GEOM_AFFINE = 0, GEOM_DEFORMED = 1, GEOM_TENSOR = 2 };
+// GEOM_QUAD: the tri-quadratic geometry of Sec. 2.2, 27 x 3 point
+// coordinates per cell with the metric computed at each quadrature point
+enum GeomKind { GEOM_AFFINE = 0, GEOM_DEFORMED = 1, GEOM_TENSOR = 2, GEOM_QUAD = 3 };
 
-// values stored per quadrature point by the deformed geometry kinds
+// values stored per quadrature point by the geometry kinds with per-point data
 __host__ __device__ constexpr int geo_values(int geom) { return geom == GEOM_TENSOR ? 6 : 10; }
+
+// values stored per cell: the per-point data of (p+1)^3 points, or the 81
+// support-point coordinates of the tri-quadratic geometry ([3][27], point
+// a + 3 (b + 3 c) at the reference coordinates (a, b, c) / 2)
+__host__ __device__ constexpr int geo_per_cell(int geom, int p) {
+  return geom == GEOM_QUAD ? 81 : geo_values(geom) * (p + 1) * (p + 1) * (p + 1);
+}
 
 enum MatId { MAT_M = 0, MAT_K0 = 1, MAT_K1 = 2, MAT_K2 = 3, MAT_S = 4, MAT_DC = 5, MAT_MV = 6, MAT_ST = 7, MAT_DCT = 8, NMAT = 9 };
 
@@ -351,6 +360,10 @@ struct OperatorCoeffs {
   float eol[NMAT][kMat];
   double w[kMaxDegree + 1];  // Gauss weights on [0,1]
   double g[kMaxDegree + 1];  // Gauss points on [0,1]
+  // quadratic Lagrange polynomials through 0, 1/2, 1 (the tri-quadratic
+  // geometry) and their derivatives at the Gauss points: [q][a]
+  double q2v[kMaxDegree + 1][3];
+  double q2d[kMaxDegree + 1][3];
   double h[3];               // cell sizes
   double amplitude;
   int coef;
@@ -374,6 +387,8 @@ struct TileArgs {
   const void* geo;       // deformed: [cell][10][nq] = J^{-1} row-major, JxW*a; tensor: [cell][6][nq]
                          // = C00 C01 C02 C11 C12 C22 of J^{-1} (JxW a) J^{-T} (precision's type)
   CGState* state;
+  int stop_on_done;      // operator passes inside CG iterations: return at once when state->done is
+                         // set (the remaining iterations of a CUDA graph after convergence)
   int64_t tail_nodes;    // number of shared-face nodes handled by the tail kernel
   int64_t fam[3];        // tail enumeration: nodes in the x / y / z boundary-plane families
   TailDiv tdiv;          // divisors of the tail enumeration

@@ -173,6 +173,14 @@ __device__ __forceinline__ typename Num<PREC>::T t_sub(typename Num<PREC>::T a, 
 }
 
 template <int PREC>
+__device__ __forceinline__ typename Num<PREC>::T t_neg(typename Num<PREC>::T a) {
+  if constexpr (PREC == PREC_DD)
+    return dd{-a.hi, -a.lo};
+  else
+    return -a;
+}
+
+template <int PREC>
 __device__ __forceinline__ typename Num<PREC>::T t_mul(typename Num<PREC>::T a, typename Num<PREC>::T b) {
   if constexpr (PREC == PREC_DD)
     return dd_mul(a, b);

@@ -164,9 +164,11 @@ void build_coeffs(int p, const double h[3], double amplitude, int coef, Operator
       c.eol[m][i] = (float)(c.eo[m][i] - (double)hi);
     }
   }
+  const double support[3] = {0.0, 0.5, 1.0};
   for (int q = 0; q < n1; ++q) {
     c.w[q] = w[q];
     c.g[q] = g[q];
+    for (int a = 0; a < 3; ++a) lagrange_eval(support, 3, a, g[q], c.q2v[q][a], c.q2d[q][a]);
   }
   for (int d = 0; d < 3; ++d) c.h[d] = h[d];
   c.amplitude = amplitude;

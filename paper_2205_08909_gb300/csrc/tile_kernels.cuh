@@ -45,15 +45,26 @@ __host__ __device__ constexpr int cell_stride(int P, int ns) {
          ((((P + 1) * (P + 1) - ns * (P + 1) * (P + 1) * (P + 1)) % 32) + 32) % 32;
 }
 
+// Tri-quadratic geometry: the per-cell partial sums of the support points
+// along y and z at every line (qb, qc) of Gauss points (quad_lines), 27 per
+// line, kept after the four arrays of a cell's scratch (a multiple of 32
+// elements, so the bank offset of the stride is unchanged)
+__host__ __device__ constexpr int quad_line_elems(int P) { return (27 * (P + 1) * (P + 1) + 31) / 32 * 32; }
+
+// per-cell scratch stride of the deformed cell operator
+__host__ __device__ constexpr int deformed_stride(int P, int geom) {
+  return cell_stride(P, 4) + (geom == GEOM_QUAD ? quad_line_elems(P) : 0);
+}
+
 // Cells of a tile that the deformed cell operator processes at once: as many
 // as fit next to the two node bricks in kDeformedSmemBytes of shared memory
 // (two CTAs per SM), balanced over the batches of a full tile.
 constexpr int kDeformedSmemBytes = 110 * 1024;
 
-__host__ __device__ inline int deformed_batch_cells(int P, int elem_bytes, const TileGeom& g) {
+__host__ __device__ inline int deformed_batch_cells(int P, int elem_bytes, const TileGeom& g, int geom) {
   const int ncell = g.T[0] * g.T[1] * g.T[2];
   const int64_t bricks = 2LL * (P * g.T[0] + 1) * (P * g.T[1] + 1) * (P * g.T[2] + 1) * elem_bytes;
-  int64_t nb = (kDeformedSmemBytes - bricks) / ((int64_t)cell_stride(P, 4) * elem_bytes);
+  int64_t nb = (kDeformedSmemBytes - bricks) / ((int64_t)deformed_stride(P, geom) * elem_bytes);
   if (nb < 1) nb = 1;
   if (nb > ncell) nb = ncell;
   if (nb > kMaxColorCells) nb = kMaxColorCells;
@@ -390,10 +401,127 @@ __device__ void brick_op_affine(const OperatorCoeffs& c, typename Num<PREC>::T* 
   __syncthreads();
 }
 
-// Deformed cells ("inverse Jacobian load" variant of Sec. 2.2): values at the
-// Gauss points by three sweeps with the interpolation matrix S, reference
-// gradients by three sweeps with the Gauss collocation derivative Dc, the
-// per-point metric J^{-1} (JxW a) J^{-T}, and the transposed sweeps back.
+// ------------------------------------------------------------------------------------
+// Tri-quadratic geometry (GEOM_QUAD, Sec. 2.2): per cell the 27 x 3 coordinates
+// X[d][a + 3 (b + 3 c)] of the mapped points (a, b, c) / 2 of the reference
+// cell; the map is x_d(xi) = sum_abc X[d][abc] L_a(xi_1) L_b(xi_2) L_c(xi_3)
+// with the quadratic Lagrange polynomials L through 0, 1/2, 1.
+// ------------------------------------------------------------------------------------
+// the partial sums of a cell's support points over (b, c) on each line (qb, qc)
+// of Gauss points, for every coordinate d and first index a:
+//   G[(3 (3 d + a) + k) N2 + qb + N1 qc] = sum_bc X[d][abc] Lb Lc   (k = 0),
+//   sum_bc X[d][abc] Lb' Lc (k = 1),  sum_bc X[d][abc] Lb Lc' (k = 2),
+// with the polynomials at (g_qb, g_qc); one more sum over a gives a point's
+// position (k = 0 with La) and Jacobian column 0 (k = 0 with La'), 1 (k = 1
+// with La) and 2 (k = 2 with La).
+template <int PREC, int P>
+__device__ void quad_lines(const OperatorCoeffs& c, const typename Num<PREC>::T* __restrict__ geo,
+                           typename Num<PREC>::T* S, int stride, const ColorCells& cc) {
+  using T = typename Num<PREC>::T;
+  constexpr int N1 = P + 1, N2 = N1 * N1;
+  const int nc = cc.count();
+  for (int t = threadIdx.x; t < nc * 9 * N2; t += kThreads) {
+    const int ci = t / (9 * N2), r = t - ci * 9 * N2;
+    const int da = r / N2, l = r - da * N2, qb = l % N1, qc = l / N1;
+    const T* X = geo + (int64_t)cc.cell[ci] * 81 + (da / 3) * 27 + da % 3;
+    T s0 = t_zero<PREC>(), s1 = t_zero<PREC>(), s2 = t_zero<PREC>();
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const T x0 = X[3 * b], x1 = X[3 * b + 9], x2 = X[3 * b + 18];
+      const T e0 = dot3<PREC>(x0, t_from_double<PREC>(c.q2v[qc][0]), x1, t_from_double<PREC>(c.q2v[qc][1]), x2,
+                              t_from_double<PREC>(c.q2v[qc][2]));
+      const T e1 = dot3<PREC>(x0, t_from_double<PREC>(c.q2d[qc][0]), x1, t_from_double<PREC>(c.q2d[qc][1]), x2,
+                              t_from_double<PREC>(c.q2d[qc][2]));
+      s0 = t_axpy<PREC>(t_from_double<PREC>(c.q2v[qb][b]), e0, s0);
+      s1 = t_axpy<PREC>(t_from_double<PREC>(c.q2d[qb][b]), e0, s1);
+      s2 = t_axpy<PREC>(t_from_double<PREC>(c.q2v[qb][b]), e1, s2);
+    }
+    T* G = S + ci * stride + cell_stride(P, 4) + 3 * da * N2 + l;
+    G[0] = s0;
+    G[N2] = s1;
+    G[2 * N2] = s2;
+  }
+}
+
+// position x_0 (the coefficient's argument) and Jacobian J[d][e] = d x_d / d xi_e
+// at Gauss point q of a cell from its line sums G
+template <int PREC, int P>
+__device__ __forceinline__ void quad_jacobian(const OperatorCoeffs& c, const typename Num<PREC>::T* G, int q,
+                                              typename Num<PREC>::T (&J)[3][3], typename Num<PREC>::T& x0) {
+  using T = typename Num<PREC>::T;
+  constexpr int N1 = P + 1, N2 = N1 * N1;
+  const int qa = q % N1, l = q / N1;
+  const T v0 = t_from_double<PREC>(c.q2v[qa][0]), v1 = t_from_double<PREC>(c.q2v[qa][1]),
+          v2 = t_from_double<PREC>(c.q2v[qa][2]);
+  const T d0 = t_from_double<PREC>(c.q2d[qa][0]), d1 = t_from_double<PREC>(c.q2d[qa][1]),
+          d2 = t_from_double<PREC>(c.q2d[qa][2]);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const T* g = G + 9 * d * N2 + l;  // (3 (3 d + a) + k) N2
+    const T a00 = g[0], a01 = g[N2], a02 = g[2 * N2];
+    const T a10 = g[3 * N2], a11 = g[4 * N2], a12 = g[5 * N2];
+    const T a20 = g[6 * N2], a21 = g[7 * N2], a22 = g[8 * N2];
+    J[d][0] = dot3<PREC>(d0, a00, d1, a10, d2, a20);
+    J[d][1] = dot3<PREC>(v0, a01, v1, a11, v2, a21);
+    J[d][2] = dot3<PREC>(v0, a02, v1, a12, v2, a22);
+    if (d == 0) x0 = dot3<PREC>(v0, a00, v1, a10, v2, a20);
+  }
+}
+
+// tensor Gauss weight of point q
+__device__ __forceinline__ double quad_weight(const OperatorCoeffs& c, int q, int n1) {
+  return c.w[q % n1] * c.w[(q / n1) % n1] * c.w[q / (n1 * n1)];
+}
+
+// w a(x) / det J (Laplacian, divide) or w a(x) det J (mass): FP32 in the FP32
+// kernels, FP64 otherwise (double-float rounds the FP64 result)
+template <int PREC>
+__device__ __forceinline__ typename Num<PREC>::T quad_factor(double w, int coef, typename Num<PREC>::T det,
+                                                            typename Num<PREC>::T x0, bool divide) {
+  if constexpr (PREC == PREC_F32) {
+    const float a = coef == MFCG_COEF_SIN_X ? 1.0f + 0.5f * sinf(3.14159265358979f * x0) : 1.0f;
+    return divide ? (float)w * a / det : (float)w * a * det;
+  } else {
+    const double xd = t_to_double<PREC>(x0), dd_ = t_to_double<PREC>(det);
+    const double a = coef == MFCG_COEF_SIN_X ? 1.0 + 0.5 * sin(3.14159265358979323846 * xd) : 1.0;
+    return t_from_double<PREC>(divide ? w * a / dd_ : w * a * dd_);
+  }
+}
+
+// FP64 position and Jacobian of the tri-quadratic map at Gauss point
+// (qa, qb, qc) directly from the cell's 81 coordinates (set-up passes)
+__device__ inline void quad_point(const OperatorCoeffs& c, const double* __restrict__ X, int qa, int qb, int qc,
+                                  double (&x)[3], double (&J)[3][3]) {
+  for (int d = 0; d < 3; ++d) {
+    x[d] = J[d][0] = J[d][1] = J[d][2] = 0.0;
+    for (int cz = 0; cz < 3; ++cz)
+      for (int b = 0; b < 3; ++b)
+        for (int a = 0; a < 3; ++a) {
+          const double v = __ldg(X + d * 27 + a + 3 * (b + 3 * cz));
+          x[d] = fma(v, c.q2v[qa][a] * c.q2v[qb][b] * c.q2v[qc][cz], x[d]);
+          J[d][0] = fma(v, c.q2d[qa][a] * c.q2v[qb][b] * c.q2v[qc][cz], J[d][0]);
+          J[d][1] = fma(v, c.q2v[qa][a] * c.q2d[qb][b] * c.q2v[qc][cz], J[d][1]);
+          J[d][2] = fma(v, c.q2v[qa][a] * c.q2v[qb][b] * c.q2d[qc][cz], J[d][2]);
+        }
+  }
+}
+
+// cofactor matrix and determinant of a 3 x 3 matrix (FP64)
+__device__ inline double cofactors(const double (&J)[3][3], double (&C)[3][3]) {
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      const int i1 = (i + 1) % 3, i2 = (i + 2) % 3, j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+      C[i][j] = J[i1][j1] * J[i2][j2] - J[i1][j2] * J[i2][j1];
+    }
+  return J[0][0] * C[0][0] + J[0][1] * C[0][1] + J[0][2] * C[0][2];
+}
+
+// Deformed cells ("inverse Jacobian load", "final tensor load" and "quadratic
+// geometry compute" variants of Sec. 2.2): values at the Gauss points by three
+// sweeps with the interpolation matrix S, reference gradients by three sweeps
+// with the Gauss collocation derivative Dc, the per-point metric
+// J^{-1} (JxW a) J^{-T} (loaded, or computed from the cell's tri-quadratic
+// map), and the transposed sweeps back.
 // The results of the cells stay in their scratch (element (a,b,c) of cell ci
 // at S[ci*stride + cidx(a,b,c)]); gather_cell_results sums them into V.
 template <int PREC, int P, int GEOM>
@@ -403,22 +531,34 @@ __device__ void cell_op_deformed(const OperatorCoeffs& c, const typename Num<PRE
   using T = typename Num<PREC>::T;
   constexpr int N1 = P + 1, N2 = N1 * N1, N3 = N2 * N1;
   const int nc = cc.count();
-  const int stride = cell_stride(P, 4);
+  const int stride = deformed_stride(P, GEOM);
   // gather u into s0
   for (int t = threadIdx.x; t < nc * N3; t += kThreads) {
     const int ci = t / N3, e = t - ci * N3, a = e % N1, b = (e / N1) % N1, cz = e / N2;
     S[ci * stride + e] = U[cc.org[ci] + a + bx * (b + by * cz)];
   }
+  if constexpr (GEOM == GEOM_QUAD) quad_lines<PREC, P>(c, geo, S, stride, cc);
   __syncthreads();
 #pragma unroll 1
   for (int dir = 0; dir < 3; ++dir) sweep_inplace<PREC, P, false, MAT_S>(S, stride, nc, dir, c);
-  if constexpr (GEOM == GEOM_DEFORMED) {
+  if constexpr (GEOM == GEOM_DEFORMED || GEOM == GEOM_QUAD) {
     if (op_kind == OP_MASS) {
       // mass operator: values at the Gauss points times JxW a, transposed interpolation
       for (int t = threadIdx.x; t < nc * N3; t += kThreads) {
         const int ci = t / N3, q = t - ci * N3;
         T* s = S + ci * stride;
-        s[q] = t_mul<PREC>(geo[(int64_t)cc.cell[ci] * 10 * N3 + 9 * N3 + q], s[q]);
+        T jxw;
+        if constexpr (GEOM == GEOM_QUAD) {
+          T J[3][3], x0;
+          quad_jacobian<PREC, P>(c, s + cell_stride(P, 4), q, J, x0);
+          const T det = dot3<PREC>(J[0][0], t_axby<PREC>(J[1][1], J[2][2], t_neg<PREC>(J[1][2]), J[2][1]), J[0][1],
+                                   t_axby<PREC>(J[1][2], J[2][0], t_neg<PREC>(J[1][0]), J[2][2]), J[0][2],
+                                   t_axby<PREC>(J[1][0], J[2][1], t_neg<PREC>(J[1][1]), J[2][0]));
+          jxw = quad_factor<PREC>(quad_weight(c, q, N1), c.coef, det, x0, false);
+        } else {
+          jxw = geo[(int64_t)cc.cell[ci] * 10 * N3 + 9 * N3 + q];
+        }
+        s[q] = t_mul<PREC>(jxw, s[q]);
       }
       __syncthreads();
 #pragma unroll 1
@@ -448,7 +588,29 @@ __device__ void cell_op_deformed(const OperatorCoeffs& c, const typename Num<PRE
     const int ci = t / N3, q = t - ci * N3;
     T* s = S + ci * stride;
     const T g0 = s[N3 + q], g1 = s[2 * N3 + q], g2 = s[3 * N3 + q];
-    if constexpr (GEOM == GEOM_TENSOR) {
+    if constexpr (GEOM == GEOM_QUAD) {
+      // tri-quadratic geometry: J at the point, its cofactors C (J^{-1} =
+      // C^T / det J), physical gradient C g / det J, and the reference flux
+      // J^{-1} (w det J a) J^{-T} g = (w a / det J) C^T (C g)
+      T J[3][3], x0;
+      quad_jacobian<PREC, P>(c, s + cell_stride(P, 4), q, J, x0);
+      T C[3][3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          const int i1 = (i + 1) % 3, i2 = (i + 2) % 3, j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+          C[i][j] = t_axby<PREC>(J[i1][j1], J[i2][j2], t_neg<PREC>(J[i1][j2]), J[i2][j1]);
+        }
+      const T det = dot3<PREC>(J[0][0], C[0][0], J[0][1], C[0][1], J[0][2], C[0][2]);
+      const T f = quad_factor<PREC>(quad_weight(c, q, N1), c.coef, det, x0, true);
+      const T y0 = t_mul<PREC>(f, dot3<PREC>(C[0][0], g0, C[0][1], g1, C[0][2], g2));
+      const T y1 = t_mul<PREC>(f, dot3<PREC>(C[1][0], g0, C[1][1], g1, C[1][2], g2));
+      const T y2 = t_mul<PREC>(f, dot3<PREC>(C[2][0], g0, C[2][1], g1, C[2][2], g2));
+      s[N3 + q] = dot3<PREC>(C[0][0], y0, C[1][0], y1, C[2][0], y2);
+      s[2 * N3 + q] = dot3<PREC>(C[0][1], y0, C[1][1], y1, C[2][1], y2);
+      s[3 * N3 + q] = dot3<PREC>(C[0][2], y0, C[1][2], y1, C[2][2], y2);
+    } else if constexpr (GEOM == GEOM_TENSOR) {
       // stored symmetric tensor C = J^{-1} (JxW a) J^{-T}: flux = C grad_ref
       const T* gq = geo + (int64_t)cc.cell[ci] * 6 * N3 + q;
       const T c00 = gq[0], c01 = gq[N3], c02 = gq[2 * N3], c11 = gq[3 * N3], c12 = gq[4 * N3], c22 = gq[5 * N3];
@@ -531,15 +693,23 @@ __device__ inline double manufactured_forcing(double x, double y, double z, int 
   return a * 3.0 * pi * pi * u - 0.5 * pi * pi * cx * cx * sin(pi * y) * sin(pi * z);
 }
 
-template <int P>
+template <int P, int GEOM>
 __device__ void cell_rhs(const OperatorCoeffs& c, double* V, double* S, int bx, int by, const ColorCells& cc,
-                         const TileGeom& g, int stride, int op_kind) {
+                         const TileGeom& g, int stride, int op_kind, const double* __restrict__ geo) {
   constexpr int N1 = P + 1, N2 = N1 * N1, N3 = N2 * N1;
   const int nc = cc.count();
   const double twopi = 6.28318530717958647692;
   for (int t = threadIdx.x; t < nc * N3; t += kThreads) {
     const int ci = t / N3, q = t - ci * N3, qa = q % N1, qb = (q / N1) % N1, qc = q / N2;
     const int cell = cc.cell[ci];
+    if constexpr (GEOM == GEOM_QUAD) {
+      // position and det J of the cell's tri-quadratic map
+      double x[3], J[3][3], C[3][3];
+      quad_point(c, geo + (int64_t)cell * 81, qa, qb, qc, x, J);
+      const double detJ = cofactors(J, C);
+      S[ci * stride + q] = c.w[qa] * c.w[qb] * c.w[qc] * detJ * manufactured_forcing(x[0], x[1], x[2], c.coef, op_kind);
+      continue;
+    }
     const int gx = cell % g.N[0], gy = (cell / g.N[0]) % g.N[1], gz = cell / (g.N[0] * g.N[1]);
     const double X = c.h[0] * (gx + c.g[qa]);
     const double Y = c.h[1] * (gy + c.g[qb]);
@@ -585,7 +755,23 @@ __device__ void cell_diag(const OperatorCoeffs& c, double* V, double* S, int bx,
     for (int t = threadIdx.x; t < nc * N3; t += kThreads) {
       const int ci = t / N3, q = t - ci * N3;
       double C;
-      if (mass) {
+      if (GEOM == GEOM_QUAD) {
+        // tri-quadratic map: JxW a (mass) or JxW a (J^{-1} J^{-T})_{d0 d1}
+        // = (w a / det J) sum_m C[m][d0] C[m][d1] with the cofactors C
+        const int qa = q % N1, qb = (q / N1) % N1, qc = q / N2;
+        double x[3], J[3][3], Cf[3][3];
+        quad_point(c, geo + (int64_t)cc.cell[ci] * 81, qa, qb, qc, x, J);
+        const double det = cofactors(J, Cf);
+        const double wa = c.w[qa] * c.w[qb] * c.w[qc] *
+                          (c.coef == MFCG_COEF_SIN_X ? 1.0 + 0.5 * sin(3.14159265358979323846 * x[0]) : 1.0);
+        if (mass) {
+          C = wa * det;
+        } else {
+          double s = 0.0;
+          for (int m = 0; m < 3; ++m) s = fma(Cf[m][d0], Cf[m][d1], s);
+          C = wa / det * s;
+        }
+      } else if (mass) {
         // mass matrix: diag_e(i) = sum_q JxW_q a_q S(q,i)^2
         if (GEOM == GEOM_AFFINE) {
           const int qa = q % N1, qb = (q / N1) % N1, qc = q / N2;
@@ -817,6 +1003,9 @@ __global__ void __launch_bounds__(kThreads, PREC == PREC_F32 ? 3 : (PREC == PREC
   __shared__ int s_cell[PREC == PREC_F64TC ? 1 : kMaxColorCells];
   const TileGeom& g = a_all.g;
 
+  // an operator pass inside CG iterations that have already stopped
+  if constexpr (MODE == MODE_OPERATOR)
+    if (a_all.stop_on_done && a_all.state->done) return;
   T alpha_m = t_zero<PREC>(), beta_t = t_zero<PREC>(), xa = t_zero<PREC>(), xr = t_zero<PREC>();
   bool xupd = false;
   if constexpr (MODE == MODE_CG) {
@@ -894,8 +1083,7 @@ __global__ void __launch_bounds__(kThreads, PREC == PREC_F32 ? 3 : (PREC == PREC
   // Deformed cells: start streaming the tile's stored geometry into L2 while
   // phase 1 runs (every prefetched line lies inside the cell's block).
   if constexpr (GEOM != GEOM_AFFINE && (MODE == MODE_CG || MODE == MODE_OPERATOR)) {
-    constexpr int N3 = (P + 1) * (P + 1) * (P + 1);
-    const int cell_bytes = geo_values(GEOM) * N3 * (int)sizeof(T);
+    const int cell_bytes = geo_per_cell(GEOM, P) * (int)sizeof(T);
     const int lines = (cell_bytes + 127) / 128;
     const int ncell = ncx * ncy * ncz;
     const char* geo = static_cast<const char*>(a_all.geo);
@@ -1085,8 +1273,7 @@ __global__ void __launch_bounds__(kThreads, PREC == PREC_F32 ? 3 : (PREC == PREC
       }
       if constexpr (GEOM != GEOM_AFFINE) {
         if (comp == 0) {
-          constexpr int N3 = (P + 1) * (P + 1) * (P + 1);
-          const int64_t cell_bytes = (int64_t)geo_values(GEOM) * N3 * (int64_t)sizeof(T);
+          const int64_t cell_bytes = (int64_t)geo_per_cell(GEOM, P) * (int64_t)sizeof(T);
           const int pcx = min(g.T[0], g.N[0] - px * g.T[0]), pcy = min(g.T[1], g.N[1] - py * g.T[1]);
           const int pcz = min(g.T[2], g.N[2] - pz * g.T[2]);
           // cells of one row of the tile are consecutive in the geometry array
@@ -1113,8 +1300,8 @@ __global__ void __launch_bounds__(kThreads, PREC == PREC_F32 ? 3 : (PREC == PREC
     // deformed cells: batches of consecutive cells, all cells of a batch at
     // once with their results in the scratch, then a fixed-order node gather
     const int ncell = ncx * ncy * ncz;
-    const int nbmax = deformed_batch_cells(P, (int)sizeof(T), g);
-    const int stride = cell_stride(P, 4);
+    const int nbmax = deformed_batch_cells(P, (int)sizeof(T), g, GEOM);
+    const int stride = deformed_stride(P, GEOM);
     const FastDiv fbx = make_fastdiv((uint32_t)bx);
     for (int c0 = 0; c0 < ncell; c0 += nbmax) {
       const int nb = min(nbmax, ncell - c0);
@@ -1146,7 +1333,8 @@ __global__ void __launch_bounds__(kThreads, PREC == PREC_F32 ? 3 : (PREC == PREC
     __syncthreads();
     const ColorCells cc{nc, s_org, s_cell};
     if constexpr (MODE == MODE_RHS) {
-      cell_rhs<P>(c, V, S, bx, by, cc, g, cell_stride(P, GEOM == GEOM_AFFINE ? 2 : 4), a.op_kind);
+      cell_rhs<P, GEOM>(c, V, S, bx, by, cc, g, cell_stride(P, GEOM == GEOM_AFFINE ? 2 : 4), a.op_kind,
+                        static_cast<const double*>(a.geo));
     } else if constexpr (MODE == MODE_DIAG) {
       cell_diag<P, GEOM>(c, V, S, bx, by, cc, static_cast<const double*>(a.geo),
                          cell_stride(P, GEOM == GEOM_AFFINE ? 2 : 4), a.op_kind);
@@ -1313,7 +1501,7 @@ __global__ void __launch_bounds__(kThreads, 3) tail_kernel(const TileArgs a) {
   __shared__ double red[8 * (kThreads / 32)];
   __shared__ int is_last;
   const TileGeom& g = a.g;
-  if (MODE == MODE_CG && a.state->done) return;
+  if ((MODE == MODE_CG || a.stop_on_done) && a.state->done) return;
   DotAcc<PREC> sm[7];
   for (int comp = 0; comp < a.ncomp; ++comp) {
   const int64_t co = comp * a.comp_stride;
@@ -1427,14 +1615,12 @@ inline size_t tile_smem_elems(int P, int geom, int elem_bytes, const TileGeom& g
   const size_t colour = (size_t)((g.T[0] + 1) / 2) * ((g.T[1] + 1) / 2) * ((g.T[2] + 1) / 2);
   const bool iter = mode == MODE_CG || mode == MODE_OPERATOR;
   const bool setup = mode == MODE_RHS || mode == MODE_DIAG;
-  size_t cells;
-  if (geom == GEOM_AFFINE) {
-    cells = iter ? 0 : colour;
-  } else {
-    const size_t batch = (size_t)deformed_batch_cells(P, elem_bytes, g);
-    cells = iter ? batch : (setup ? colour : std::max(colour, batch));
-  }
-  return 2 * Bmax + cells * (size_t)cell_stride(P, geom == GEOM_AFFINE ? 2 : 4);
+  // set-up passes: one colour of cells; deformed operator passes: one batch
+  const size_t colour_elems = colour * (size_t)cell_stride(P, geom == GEOM_AFFINE ? 2 : 4);
+  const size_t batch_elems =
+      geom == GEOM_AFFINE ? 0 : (size_t)deformed_batch_cells(P, elem_bytes, g, geom) * deformed_stride(P, geom);
+  const size_t cells = iter ? batch_elems : (setup ? colour_elems : std::max(colour_elems, batch_elems));
+  return 2 * Bmax + cells;
 }
 
 template <int P>
@@ -1468,6 +1654,8 @@ TileFn<P> tile_fn_gn(int mode, int prec) {
 
 template <int P, int GEOM>
 TileFn<P> tile_fn_g(int mode, int prec, int ncomp) {
+  // the tri-quadratic geometry has the scalar operator only
+  if constexpr (GEOM == GEOM_QUAD) return ncomp == 1 ? tile_fn_gn<P, GEOM, 1>(mode, prec) : nullptr;
   return ncomp == 3 ? tile_fn_gn<P, GEOM, 3>(mode, prec) : tile_fn_gn<P, GEOM, 1>(mode, prec);
 }
 
@@ -1475,6 +1663,7 @@ template <int P>
 TileFn<P> tile_fn(int mode, int geom, int prec, int ncomp) {
   if (geom == GEOM_AFFINE) return tile_fn_g<P, GEOM_AFFINE>(mode, prec, ncomp);
   if (geom == GEOM_TENSOR) return tile_fn_g<P, GEOM_TENSOR>(mode, prec, ncomp);
+  if (geom == GEOM_QUAD) return tile_fn_g<P, GEOM_QUAD>(mode, prec, ncomp);
   return tile_fn_g<P, GEOM_DEFORMED>(mode, prec, ncomp);
 }
 

@@ -814,3 +814,100 @@ def test_tensor_core_operator_vector_and_mass(mfcg):
         ref = np.concatenate([A @ u[c * n:(c + 1) * n] for c in range(comps)])
         assert _rel(got, ref) <= OP_TOL
         tc.close()
+
+
+# ---------------------------------------------------------------- tri-quadratic geometry (Sec. 2.2)
+
+QUAD_CASES = [
+    (1, (5, 4, 6), 0.06, "constant", None),
+    (2, (5, 4, 6), 0.05, "sin_x", None),
+    (3, (4, 3, 5), 0.08, "sin_x", (2, 2, 2)),
+    (4, (3, 4, 3), 0.08, "constant", None),
+    (5, (3, 2, 3), 0.05, "sin_x", None),
+    (6, (3, 3, 2), 0.05, "sin_x", None),
+    (7, (2, 3, 2), 0.07, "sin_x", (1, 2, 1)),
+    (8, (2, 2, 3), 0.05, "constant", (1, 1, 2)),
+    (3, (4, 3, 5), 0.0, "constant", None),
+]
+
+
+def _quad_oracle(p, cells, amp, coef, op=fem.OP_LAPLACE):
+    return fem.Problem(p, tuple(cells), amp, fem.COEF_SIN_X if coef == "sin_x" else fem.COEF_CONSTANT, op,
+                       geometry_degree=2)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "double_float"])
+@pytest.mark.parametrize("p,cells,amp,coef,tile", QUAD_CASES)
+def test_quadratic_geometry_operator_matches_oracle(mfcg, p, cells, amp, coef, tile, precision):
+    # the metric computed at each point from 27 x 3 coordinates per cell
+    op = _quad_oracle(p, cells, amp, coef)
+    A = fem.assemble(op)
+    prob = _gpu_problem(mfcg, p, cells, amp, coef, geometry="deformed_quadratic", tile=tile, precision=precision)
+    u = inputs.random_vector(op.n_dofs, salt=p + 40)
+    got = _to_host(prob, prob.apply_operator(_to_dev(prob, u)))
+    assert _rel(got, A @ u) <= (OP_TOL if precision == "fp64" else 1e-12)
+    assert _rel(_to_host(prob, prob.diagonal()), A.diagonal()) <= OP_TOL
+    assert _rel(_to_host(prob, prob.rhs()), fem.rhs(op)) <= 1e-12
+    prob.close()
+
+
+@pytest.mark.parametrize("p,cells,amp,coef", [(2, (5, 4, 6), 0.05, "sin_x"), (5, (3, 2, 3), 0.08, "constant")])
+def test_quadratic_geometry_mass_operator(mfcg, p, cells, amp, coef):
+    op = _quad_oracle(p, cells, amp, coef, fem.OP_MASS)
+    A = fem.assemble(op)
+    prob = _gpu_problem(mfcg, p, cells, amp, coef, geometry="deformed_quadratic", operator="mass")
+    u = inputs.random_vector(op.n_dofs, salt=p + 50)
+    assert _rel(_to_host(prob, prob.apply_operator(_to_dev(prob, u))), A @ u) <= OP_TOL
+    assert _rel(_to_host(prob, prob.diagonal()), A.diagonal()) <= OP_TOL
+    assert _rel(_to_host(prob, prob.rhs()), fem.rhs(op)) <= 1e-12
+    prob.close()
+
+
+@pytest.mark.parametrize("mode,precision", [("fused", "fp64"), ("unfused", "fp64"), ("loop_fused", "fp64"),
+                                            ("fused", "double_float"), ("fused", "fp32_inner")])
+@pytest.mark.parametrize("p,cells,amp,coef", [(3, (4, 3, 5), 0.05, "sin_x"), (6, (2, 3, 2), 0.08, "sin_x")])
+def test_quadratic_geometry_solve_matches_oracle(mfcg, mode, precision, p, cells, amp, coef):
+    op = _quad_oracle(p, cells, amp, coef)
+    A = fem.assemble(op)
+    b = fem.rhs(op)
+    ref = ocg.pcg_algorithm1(lambda v: A @ v, b, 1.0 / A.diagonal(), 1e-10, 5000)
+    prob = _gpu_problem(mfcg, p, cells, amp, coef, geometry="deformed_quadratic", mode=mode, precision=precision)
+    x, info = prob.cg_solve(_to_dev(prob, b), rtol=1e-10, maxit=5000)
+    assert info["converged"] == 1
+    xh = _to_host(prob, x)
+    if precision == "fp32_inner":
+        assert np.linalg.norm(b - A @ xh) < 1e-10 * np.linalg.norm(b)
+    else:
+        assert abs(info["iterations"] - ref.iterations) <= 1
+    assert _rel(xh, ref.x) <= SOL_TOL
+    prob.close()
+
+
+def test_quadratic_geometry_rejects_vector_valued_operator(mfcg):
+    with pytest.raises(mfcg.MfcgError):
+        mfcg.Problem(3, (2, 2, 2), amplitude=0.05, geometry="deformed_quadratic", components=3)
+
+
+def test_operator_passes_stop_with_the_iterations(mfcg):
+    # the unfused forms run graphs of 16 iterations; after the last iteration
+    # the remaining operator passes of the graph return at once: a solve of
+    # 17 iterations (two graphs) costs about 17/16 of one of 16 iterations
+    # (with 15 idle operator passes it would cost about 1.7 times as much)
+    prob = mfcg.Problem(4, (48, 48, 48), mode="unfused")
+    b = prob.rhs()
+    x = torch.zeros_like(b)
+    for maxit in (16, 17):
+        prob.cg_solve(b, x.zero_(), rtol=0.0, maxit=maxit)
+    times = {}
+    for maxit in (16, 17, 32):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            prob.cg_solve(b, x.zero_(), rtol=0.0, maxit=maxit)
+        e1.record()
+        torch.cuda.synchronize()
+        times[maxit] = e0.elapsed_time(e1)
+    assert times[17] < 1.3 * times[16], times
+    assert times[32] > 1.6 * times[16], times
+    prob.close()
