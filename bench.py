@@ -489,7 +489,8 @@ def run_ours(args, world, rank, local):
     def make(mode, precision, instrument=False, contraction="tensor_cores"):
         return mfcg.Problem(w.degree, w.cells, amplitude=w.amplitude, geometry=geometry,
                             coefficient=w.coefficient, mode=mode, precision=precision, instrument=instrument,
-                            tile=tile, fp64_contraction=contraction)
+                            tile=tile, fp64_contraction=contraction,
+                            x_every_iteration=args.x_update == "every_iteration")
 
     def timed_steps(prob, b, K, W):
         xs = [torch.zeros(prob.n_dofs, dtype=torch.float64, device="cuda") for _ in range(max(K, W, 1))]
@@ -673,7 +674,7 @@ def run_ours(args, world, rank, local):
         "dtype": dtype,
         "data": "synthetic: manufactured right-hand side of u = sin(pi x) sin(pi y) sin(pi z), x0 = 0",
         "config": {"workload": w.name, "degree": w.degree, "cells": list(w.cells), "n_dofs": w.n_dofs,
-                   "geometry": geometry, "precision": main_prec, "iterations_per_step": iters,
+                   "geometry": geometry, "precision": main_prec, "iterations_per_step": iters, "x_update": args.x_update,
                    "tile": list(eff_tile),
                    "arithmetic": ("FP64 vectors, updates and inner products; operator contractions as exact "
                                   "8-bit digit products of 64-bit fixed-point data on the FP16 tensor cores, "
@@ -837,6 +838,9 @@ def main():
     ap.add_argument("--tile", default="", help="cells per tile, e.g. 4,4,2 (default: chosen from the degree)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "double_float", "fp32_inner"],
                     help="arithmetic of the headline fused path")
+    ap.add_argument("--x-update", default="delayed", choices=["delayed", "every_iteration"],
+                    help="fused forms: Algorithm 5's delayed x update (every other iteration) or x += alpha p "
+                         "in every iteration")
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
