@@ -577,13 +577,23 @@ def run_ours(args, world, rank, local):
     fused_over_loop_fused = round(value / variants[loop_key]["value"], 4) if loop_key in variants else None
 
     # ---------------- FP64 defect correction around the FP32 fused CG (time to rtol 1e-10)
-    dc = None
+    # and around the double-float fused CG (each inner solve to the reduction the
+    # true residual still needs), against the fused FP64 CG's time to the same
+    # tolerance
+    dc = dc_dd = None
     if not args.skip_dc:
         dcp = make("fused", "fp32_inner")
         bdc = dcp.rhs()
         converged_solve(dcp, bdc)
         dc = converged_solve(dcp, bdc)
         dcp.close()
+        dcp = make("fused", "double_float_inner")
+        bdc = dcp.rhs()
+        converged_solve(dcp, bdc)
+        dc_dd = converged_solve(dcp, bdc)
+        dcp.close()
+        if main_prec == "fp64" and dc_dd["ms"] > 0:
+            dc_dd["fused_fp64_solve_ms_over_this"] = round(solve_main["ms"] / dc_dd["ms"], 4)
 
     # ---------------- dominant kernel: fused tile kernel, CUDA events around every launch
     inst = make("fused", main_prec, instrument=True)
@@ -688,6 +698,7 @@ def run_ours(args, world, rank, local):
         "solve_rtol_1e-10": solve_main,
         "variants": variants,
         "defect_correction_fp32_inner": dc,
+        "defect_correction_double_float_inner": dc_dd,
         "batched": batched,
         "roofline": roofline,
         "e2e": e2e,

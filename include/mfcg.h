@@ -117,9 +117,14 @@ typedef enum mfcg_precision {
   MFCG_PREC_DOUBLE_FLOAT = 1, /* operator and fused CG vectors as unevaluated pairs of FP32 numbers
                                  (about 48 significant bits) on the FP32 pipes; operator results
                                  within 1e-13 (normwise) of FP64; scalars and reductions in FP64      */
-  MFCG_PREC_FP32_INNER = 2    /* FP64 defect correction: the true residual b - A x with the FP64
+  MFCG_PREC_FP32_INNER = 2,   /* FP64 defect correction: the true residual b - A x with the FP64
                                  operator, inner fused CG in FP32 (sums reduced in FP64) to
                                  inner_rtol per cycle, x updated in FP64; FUSED mode only             */
+  MFCG_PREC_DOUBLE_FLOAT_INNER = 3 /* the same FP64 defect correction around the fused double-float
+                                 CG: each inner solve runs to the reduction the true residual still
+                                 needs (half of rtol ||b|| / ||b - A x||, at least 1e-12; inner_rtol
+                                 overrides), so one or two cycles reach rtol on the true residual;
+                                 FUSED mode only                                                      */
 } mfcg_precision;
 
 /* How FP64 operator contractions run on Cartesian (MFCG_GEOM_AFFINE) problems. */
@@ -145,7 +150,8 @@ typedef struct mfcg_options {
                                candidate tiles around the default and keeps the fastest              */
   int32_t precision;        /* mfcg_precision                                                       */
   int32_t preconditioner;   /* mfcg_preconditioner                                                  */
-  double inner_rtol;        /* MFCG_PREC_FP32_INNER: residual reduction of each inner solve (0 = 1e-3) */
+  double inner_rtol;        /* MFCG_PREC_FP32_INNER: residual reduction of each inner solve (0 = 1e-3);
+                               MFCG_PREC_DOUBLE_FLOAT_INNER: the same, 0 = what the true residual needs */
   int32_t components;       /* 0 or 1: scalar operator; 3: vector-valued operator (the BP2/BP4 form
                                of Sec. 2): every component is the scalar operator, one CG runs on the
                                coupled system, the Jacobi diagonal and the geometry are shared by the
@@ -171,7 +177,7 @@ typedef struct mfcg_solve_info {
   double rhs_norm_sq;         /* ||b||^2                                                           */
   double main_kernel_ms;      /* summed CUDA-event time of the operator-pass kernels (instrument = 1) */
   int64_t kernel_launches;    /* kernels this call enqueued, graph replays included                */
-  int32_t outer_cycles;       /* MFCG_PREC_FP32_INNER: defect-correction cycles, else 0            */
+  int32_t outer_cycles;       /* the *_INNER precisions: defect-correction cycles, else 0          */
   int32_t reserved2;
   double true_residual_sq;    /* mfcg_options.true_residual = 1: ||b - A x||^2 of the returned x with
                                  the FP64 operator (one extra operator pass); else -1               */
@@ -224,9 +230,10 @@ int mfcg_rhs(mfcg_problem* prob, double* b);
  * (Algorithm 5 in FUSED and SEMI_FUSED modes, Algorithm 1 in UNFUSED mode) until
  * ||r_k|| < rtol ||b|| (unpreconditioned residual, Sec. 3.1) or maxit products
  * A p.  rtol == 0 runs exactly maxit iterations and returns MFCG_OK.  With
- * MFCG_PREC_FP32_INNER the solve stops on the true residual ||b - A x|| <
- * rtol ||b|| and maxit counts all inner iterations; rtol == 0 there applies
- * one correction x += d with exactly maxit inner FP32 iterations.
+ * MFCG_PREC_FP32_INNER or MFCG_PREC_DOUBLE_FLOAT_INNER the solve stops on the
+ * true residual ||b - A x|| < rtol ||b|| and maxit counts all inner
+ * iterations; rtol == 0 there applies one correction x += d with exactly maxit
+ * inner iterations.
  *   b   in : device, n doubles, must be zero on Dirichlet nodes (INVALID_ARG is
  *            not checked on the device; a nonzero value there is solved as an
  *            identity row).

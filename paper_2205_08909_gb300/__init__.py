@@ -45,8 +45,10 @@ class Problem:
     "loop_fused" (Algorithm 1 with loop fusion inside its vector regions) or
     "semi_fused" (Algorithm 5 as separate pre / operator / post kernels);
     preconditioner: "jacobi" or "none" (Algorithm 4);
-    precision: "fp64", "double_float" (FP32 pairs, ~48 bits) or "fp32_inner"
-    (FP64 defect correction around an FP32 fused CG, inner_rtol per cycle);
+    precision: "fp64", "double_float" (FP32 pairs, ~48 bits), "fp32_inner"
+    (FP64 defect correction around an FP32 fused CG, inner_rtol per cycle) or
+    "double_float_inner" (the same around the double-float fused CG, each inner
+    solve to the reduction the true residual still needs);
     components: 1 (scalar) or 3 (vector-valued operator, components stored
     one after another; fused mode); operator: "laplace" (BP3/BP4) or "mass"
     (BP1/BP2; affine or geometry="deformed").

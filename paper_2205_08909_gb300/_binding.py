@@ -23,7 +23,7 @@ GEOM = {"affine": 0, "deformed": 1, "deformed_tensor": 2, "user": 3, "deformed_q
 COEF = {"constant": 0, "sin_x": 1}
 MODE = {"fused": 0, "unfused": 1, "semi_fused": 2, "loop_fused": 3}
 PRECONDITIONER = {"jacobi": 0, "none": 1}
-PRECISION = {"fp64": 0, "double_float": 1, "fp32_inner": 2}
+PRECISION = {"fp64": 0, "double_float": 1, "fp32_inner": 2, "double_float_inner": 3}
 OPERATOR = {"laplace": 0, "mass": 1}
 FP64_CONTRACTION = {"tensor_cores": 0, "fp64_pipe": 1}
 

@@ -113,6 +113,11 @@ struct mfcg_batch {
 
 namespace {
 
+// the defect-correction precisions (FP64 outer residual around an inner fused CG)
+bool inner_precision(int precision) {
+  return precision == MFCG_PREC_FP32_INNER || precision == MFCG_PREC_DOUBLE_FLOAT_INNER;
+}
+
 // internal geometry kind of an mfcg_geometry_kind (MFCG_GEOM_USER data is stored like MFCG_GEOM_DEFORMED)
 int geom_kind_of(int kind) {
   if (kind == MFCG_GEOM_AFFINE) return GEOM_AFFINE;
@@ -502,13 +507,17 @@ int solve_direct(mfcg_problem* P, const double* b, double* x_user, double rtol, 
 }
 
 // FP64 defect correction: x_{j+1} = x_j + d_j with A d_j = b - A x_j solved by
-// the FP32 fused CG to a relative reduction inner_rtol; the true residual is
-// formed with the FP64 operator and FP64 vectors.
+// the fused CG in the inner precision (FP32 or double-float) to a relative
+// reduction inner_rtol; the true residual is formed with the FP64 operator and
+// FP64 vectors.  Double-float inner solves without inner_rtol run to half the
+// reduction the true residual still needs (at least 1e-12): the first cycle
+// then usually reaches rtol, and a second one removes the rounding of the first.
 int solve_defect_correction(mfcg_problem* P, const double* b, double* x_user, double rtol, int maxit,
                             mfcg_solve_info* info) {
   const int64_t n = P->nv();
   const int64_t launches0 = P->launches;
   const double inner = P->opt.inner_rtol > 0.0 ? P->opt.inner_rtol : 1e-3;
+  const bool adaptive = P->opt.precision == MFCG_PREC_DOUBLE_FLOAT_INNER && !(P->opt.inner_rtol > 0.0);
   IterStats stats;
   int st;
   CK(cudaMemcpyAsync(P->x, x_user, n * sizeof(double), cudaMemcpyDeviceToDevice, P->exec));
@@ -540,6 +549,13 @@ int solve_defect_correction(mfcg_problem* P, const double* b, double* x_user, do
       break;
     }
     if (total_it >= maxit) break;
+    if (adaptive) {
+      // the inner tolerance for this cycle: the start-up again with it
+      const double need = std::min(0.5, std::max(1e-12, 0.5 * rtol * std::sqrt(bb / rr)));
+      CK(launch_cg_init(P->state, P->work, P->work, n, need, std::max(maxit - total_it, 1), 0, P->partial,
+                        P->opt.x_update_every_iteration, P->exec));
+      P->launches += 1;
+    }
     // inner FP32 solve of A d = r from d = 0 (its scalars were set by cg_init above)
     const size_t es = prec_bytes(P->cg_prec);
     CK(launch_to_prec(P->cg_prec, P->work, P->r[0], n, P->exec));
@@ -596,7 +612,7 @@ int solve_fixed_inner(mfcg_problem* P, const double* b, double* x_user, int maxi
 
 int solve_impl(mfcg_problem* P, const double* b, double* x_user, double rtol, int maxit, mfcg_solve_info* info) {
   int st;
-  if (P->opt.precision == MFCG_PREC_FP32_INNER)
+  if (inner_precision(P->opt.precision))
     st = rtol == 0.0 ? solve_fixed_inner(P, b, x_user, maxit, info) : solve_defect_correction(P, b, x_user, rtol, maxit, info);
   else
     st = solve_direct(P, b, x_user, rtol, maxit, info);
@@ -956,8 +972,8 @@ int setup_impl(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, con
     return MFCG_INVALID_ARG;
   if (o.preconditioner != MFCG_PRECOND_JACOBI && o.preconditioner != MFCG_PRECOND_NONE) return MFCG_INVALID_ARG;
   if (o.graph_iterations < 0 || (o.graph_iterations & 1)) return MFCG_INVALID_ARG;
-  if (o.precision < MFCG_PREC_FP64 || o.precision > MFCG_PREC_FP32_INNER) return MFCG_INVALID_ARG;
-  if (o.precision == MFCG_PREC_FP32_INNER && o.mode != MFCG_MODE_FUSED) return MFCG_INVALID_ARG;
+  if (o.precision < MFCG_PREC_FP64 || o.precision > MFCG_PREC_DOUBLE_FLOAT_INNER) return MFCG_INVALID_ARG;
+  if (inner_precision(o.precision) && o.mode != MFCG_MODE_FUSED) return MFCG_INVALID_ARG;
   if (!(o.inner_rtol >= 0.0 && o.inner_rtol < 1.0)) return MFCG_INVALID_ARG;
   if (o.x_update_every_iteration != 0 && o.x_update_every_iteration != 1) return MFCG_INVALID_ARG;
   if (o.true_residual != 0 && o.true_residual != 1) return MFCG_INVALID_ARG;
@@ -993,7 +1009,9 @@ int setup_impl(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, con
   // the defect correction forms its outer residual with the native FP64
   // operator: its true-residual floor is 2^5 lower than the double-float one
   P->op_prec = o.precision == MFCG_PREC_DOUBLE_FLOAT ? PREC_DD : PREC_F64;
-  P->cg_prec = o.precision == MFCG_PREC_FP64 ? PREC_F64 : (o.precision == MFCG_PREC_DOUBLE_FLOAT ? PREC_DD : PREC_F32);
+  P->cg_prec = o.precision == MFCG_PREC_FP64 ? PREC_F64
+               : (o.precision == MFCG_PREC_DOUBLE_FLOAT || o.precision == MFCG_PREC_DOUBLE_FLOAT_INNER ? PREC_DD
+                                                                                                   : PREC_F32);
   P->graph_iters = o.graph_iterations ? o.graph_iterations : 16;
   if (cudaStreamCreateWithFlags(&P->exec, cudaStreamNonBlocking) != cudaSuccess) return fail(MFCG_CUDA_ERROR);
   if (cudaEventCreateWithFlags(&P->ev_in, cudaEventDisableTiming) != cudaSuccess) return fail(MFCG_CUDA_ERROR);
@@ -1058,7 +1076,7 @@ int setup_impl(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, con
     }
     if (st == MFCG_OK) st = alloc_bytes(P, &P->xs, n8);
     if (st == MFCG_OK && !share) st = alloc_bytes(P, &P->dinv_s, n8);
-    if (st == MFCG_OK && o.precision == MFCG_PREC_FP32_INNER) st = alloc_bytes(P, &P->x, n8);
+    if (st == MFCG_OK && inner_precision(o.precision)) st = alloc_bytes(P, &P->x, n8);
   } else {
     if (st == MFCG_OK) st = alloc_bytes(P, &P->x, n8);
     if (st == MFCG_OK) st = alloc_bytes(P, &P->z, n8);

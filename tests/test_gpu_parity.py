@@ -124,8 +124,8 @@ CG_CASES = [
 
 SOLVER_VARIANTS = [("fused", "fp64"), ("unfused", "fp64"), ("fused", "double_float"), ("unfused", "double_float"),
                    ("fused", "fp32_inner"), ("semi_fused", "fp64"), ("semi_fused", "double_float"),
-                   ("loop_fused", "fp64"), ("loop_fused", "double_float")]
-FIXED_VARIANTS = [v for v in SOLVER_VARIANTS if v[1] != "fp32_inner"]
+                   ("loop_fused", "fp64"), ("loop_fused", "double_float"), ("fused", "double_float_inner")]
+FIXED_VARIANTS = [v for v in SOLVER_VARIANTS if not v[1].endswith("_inner")]
 
 
 @pytest.mark.parametrize("mode,precision", SOLVER_VARIANTS)
@@ -138,7 +138,7 @@ def test_cg_solution_matches_oracle(mfcg, mode, precision, p, cells, amp, coef):
     prob = _gpu_problem(mfcg, p, cells, amp, coef, mode=mode, precision=precision)
     x, info = prob.cg_solve(_to_dev(prob, b), rtol=1e-10, maxit=5000)
     assert info["converged"] == 1
-    if precision != "fp32_inner":
+    if not precision.endswith("_inner"):
         assert abs(info["iterations"] - ref.iterations) <= 1
     else:
         # defect correction: the true FP64 residual meets the tolerance
@@ -150,7 +150,7 @@ def test_cg_solution_matches_oracle(mfcg, mode, precision, p, cells, amp, coef):
 
 
 @pytest.mark.parametrize("mode,precision", [("fused", "fp64"), ("unfused", "fp64"), ("fused", "double_float"),
-                                            ("fused", "fp32_inner")])
+                                            ("fused", "fp32_inner"), ("fused", "double_float_inner")])
 @pytest.mark.parametrize("p,cells,amp,coef", [c for c in CG_CASES if c[2] != 0.0])
 def test_cg_with_final_tensor_geometry_matches_oracle(mfcg, mode, precision, p, cells, amp, coef):
     op = _oracle_problem(p, cells, amp, coef)
@@ -160,7 +160,7 @@ def test_cg_with_final_tensor_geometry_matches_oracle(mfcg, mode, precision, p, 
     prob = _gpu_problem(mfcg, p, cells, amp, coef, geometry="deformed_tensor", mode=mode, precision=precision)
     x, info = prob.cg_solve(_to_dev(prob, b), rtol=1e-10, maxit=5000)
     assert info["converged"] == 1
-    if precision != "fp32_inner":
+    if not precision.endswith("_inner"):
         assert abs(info["iterations"] - ref.iterations) <= 1
     assert _rel(_to_host(prob, x), ref.x) <= SOL_TOL
     prob.close()
@@ -356,7 +356,7 @@ def test_defect_correction_on_deformed_mesh(mfcg):
     ref.close()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32_inner", "double_float"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32_inner", "double_float", "double_float_inner"])
 def test_full_size_q4_128cube_solve(mfcg, precision):
     # the fused FP64 CG, the FP32-inner defect correction and the double-float
     # CG at 135M unknowns against the exact discrete solution by fast
@@ -367,6 +367,8 @@ def test_full_size_q4_128cube_solve(mfcg, precision):
     b = prob.rhs()
     x, info = prob.cg_solve(b, rtol=1e-10, maxit=20000)
     assert info["converged"]
+    if precision == "double_float_inner":
+        assert info["outer_cycles"] <= 2
     bh = _to_host(prob, b)
     xh = _to_host(prob, x)
     prob.close()
@@ -418,7 +420,7 @@ def test_full_size_q6_48cube_deformed_solve(mfcg):
     # the sampled rows of the residual stay within the norm bound
     assert np.abs(bh[rows] - ref).max() <= 1.5e-10 * np.linalg.norm(bh)
     prob.close()
-    for precision in ("double_float", "fp32_inner"):
+    for precision in ("double_float", "fp32_inner", "double_float_inner"):
         other = _gpu_problem(mfcg, w.degree, w.cells, w.amplitude, w.coefficient, precision=precision)
         xo, info_o = other.cg_solve(other.rhs(), rtol=1e-10, maxit=20000)
         assert info_o["converged"]
@@ -451,7 +453,7 @@ def test_random_rhs_solve_matches_algorithm1(mfcg, mode, precision, p, cells, am
     x, info = prob.cg_solve(_to_dev(prob, b), rtol=1e-10, maxit=5000)
     assert info["converged"] == 1
     xh = _to_host(prob, x)
-    if precision == "fp32_inner":
+    if precision.endswith("_inner"):
         assert np.linalg.norm(b - A @ xh) < 1e-10 * np.linalg.norm(b)
         assert _rel(xh, ref.x) <= SOL_TOL
     else:
@@ -562,7 +564,7 @@ def test_vector_valued_operator_and_solve(mfcg, p, cells, amp, coef, geometry, p
     ref = ocg.pcg_algorithm1(lambda v: A3 @ v, b, 1.0 / A3.diagonal(), 1e-10, 5000)
     x, info = prob.cg_solve(_to_dev(prob, b), rtol=1e-10, maxit=5000)
     assert info["converged"] == 1
-    if precision != "fp32_inner":
+    if not precision.endswith("_inner"):
         assert abs(info["iterations"] - ref.iterations) <= 1
     else:
         xh = _to_host(prob, x)
@@ -597,7 +599,7 @@ def test_mass_operator_matches_oracle(mfcg, p, cells, amp, coef, tile, precision
     ref = ocg.pcg_algorithm1(lambda v: A @ v, b, 1.0 / A.diagonal(), 1e-10, 5000)
     x, info = prob.cg_solve(_to_dev(prob, b), rtol=1e-10, maxit=5000)
     assert info["converged"] == 1
-    if precision != "fp32_inner":
+    if not precision.endswith("_inner"):
         assert abs(info["iterations"] - ref.iterations) <= 1
     assert _rel(_to_host(prob, x), ref.x) <= SOL_TOL
     prob.close()
@@ -694,10 +696,10 @@ def test_x_update_every_iteration(mfcg, mode, precision, maxit):
         ref = ocg.pcg_algorithm1(lambda v: A @ v, b, 1.0 / A.diagonal(), 1e-10, 5000)
         x, info = prob.cg_solve(_to_dev(prob, b), rtol=1e-10, maxit=5000)
         assert info["converged"] == 1
-        if precision != "fp32_inner":
+        if not precision.endswith("_inner"):
             assert abs(info["iterations"] - ref.iterations) <= 1
         assert _rel(_to_host(prob, x), ref.x) <= SOL_TOL
-    elif precision != "fp32_inner":
+    elif not precision.endswith("_inner"):
         ref = ocg.pcg_algorithm1(lambda v: A @ v, b, 1.0 / A.diagonal(), 0.0, maxit)
         x, info = prob.cg_solve(_to_dev(prob, b), rtol=0.0, maxit=maxit)
         assert info["iterations"] == maxit
@@ -864,7 +866,8 @@ def test_quadratic_geometry_mass_operator(mfcg, p, cells, amp, coef):
 
 
 @pytest.mark.parametrize("mode,precision", [("fused", "fp64"), ("unfused", "fp64"), ("loop_fused", "fp64"),
-                                            ("fused", "double_float"), ("fused", "fp32_inner")])
+                                            ("fused", "double_float"), ("fused", "fp32_inner"),
+                                            ("fused", "double_float_inner")])
 @pytest.mark.parametrize("p,cells,amp,coef", [(3, (4, 3, 5), 0.05, "sin_x"), (6, (2, 3, 2), 0.08, "sin_x")])
 def test_quadratic_geometry_solve_matches_oracle(mfcg, mode, precision, p, cells, amp, coef):
     op = _quad_oracle(p, cells, amp, coef)
@@ -875,7 +878,7 @@ def test_quadratic_geometry_solve_matches_oracle(mfcg, mode, precision, p, cells
     x, info = prob.cg_solve(_to_dev(prob, b), rtol=1e-10, maxit=5000)
     assert info["converged"] == 1
     xh = _to_host(prob, x)
-    if precision == "fp32_inner":
+    if precision.endswith("_inner"):
         assert np.linalg.norm(b - A @ xh) < 1e-10 * np.linalg.norm(b)
     else:
         assert abs(info["iterations"] - ref.iterations) <= 1
