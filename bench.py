@@ -676,6 +676,15 @@ def run_ours(args, world, rank, local):
             batched[key] = measure_batch(batch_specs(8, blk), bprec, 2, 1, iters, world, local)
             batched[key]["precision"] = bprec
 
+    # the stated target of the fused FP64 CG at p = 4 on >= 100M unknowns
+    met = bool(main_prec == "fp64" and value / world * kernel_bytes_per_dof / hbm >= 0.70
+               and (fused_over_unfused or 0.0) >= 2.0)
+    target = {"hbm_roofline_frac_min": 0.70, "fused_over_unfused_min": 2.0, "met": met,
+              "why_not": None if met else (
+                  "the fused FP64 kernel is bound by FP64 vector arithmetic (Algorithm 5: about 15 FP64 "
+                  "operations per unknown and iteration, twice Algorithm 1's, on a pipe of two FMAs per clock "
+                  "per SM) and by issue latency, not by HBM traffic")}
+
     dtype = {"fp64": "f64", "double_float": "f32x2 (double-float, ~48-bit; FP64 scalars and reductions)",
              "fp32_inner": "f32"}[main_prec]
     line = {
@@ -695,6 +704,8 @@ def run_ours(args, world, rank, local):
         "algorithmic_bytes_per_dof": round(kernel_bytes_per_dof, 2),
         "fused_over_unfused": fused_over_unfused,
         "fused_over_loop_fused": fused_over_loop_fused,
+        # the stated target of the fused FP64 CG at p = 4 on >= 100M unknowns
+        "target": target,
         "solve_rtol_1e-10": solve_main,
         "variants": variants,
         "defect_correction_fp32_inner": dc,
