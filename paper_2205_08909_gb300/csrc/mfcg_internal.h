@@ -400,6 +400,8 @@ struct TileArgs {
   int64_t shell_comp_stride;  // shell elements per component (= g.n_tiles * g.face_stride)
   int op_kind;           // OpKind
   int tail_ctas;
+  int stagger_lo, stagger_hi;  // fused tensor-core iterations: CTAs blockIdx in [lo, hi) -- those that
+  long long stagger_cycles;    // start beside another CTA on the same SM -- begin stagger_cycles later
   int prefetch_ahead;    // operator passes: during its cell phase, a CTA prefetches into L2 the
                          // owned input block (and geometry) of tile blockIdx + prefetch_ahead
                          // (the CTAs resident in one wave); 0 = off

@@ -1011,6 +1011,16 @@ __global__ void __launch_bounds__(kThreads, PREC == PREC_F32 ? 3 : (PREC == PREC
   if constexpr (MODE == MODE_CG) {
     const CGState* st = a_all.state;
     if (st->done) return;
+    // The CTAs that start beside another one on the same SM begin a fixed
+    // number of clocks later, so that the two CTAs of an SM run different
+    // phases (the FP64 vector work of "pre"/"post" against the integer and
+    // tensor-core work of the operator) instead of the same phase in step.
+    if constexpr (PREC == PREC_F64TC) {
+      if (blockIdx.x >= a_all.stagger_lo && blockIdx.x < a_all.stagger_hi) {
+        const long long t0 = clock64();
+        while (clock64() - t0 < a_all.stagger_cycles) __nanosleep(256);
+      }
+    }
     const int k = st->k;
     xupd = (k > 1) && ((k & 1) || st->x_every_iter);
     if constexpr (is_f64(PREC)) {
