@@ -1057,16 +1057,16 @@ int setup_impl(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, con
                                       tile_smem_bytes(degree, P->geom_kind, op_launch_prec, g, MODE_OPERATOR));
   // fused FP64 iterations on the tensor cores, two CTAs per SM: the first
   // wave's second CTA on each SM (blockIdx in [n_sm, 2 n_sm)) starts about
-  // two thirds of a tile later (90,000 clocks for the 17 x 17 x 13-node brick
-  // of degree 4, measured best among 0-110,000 on Q4 128^3: +6 %), scaled by
-  // the brick's node count for other tiles
+  // half a tile later (80,000 clocks for the 17 x 17 x 13-node brick of
+  // degree 4, the best of 0-110,000 measured on Q4 128^3: +8 %), scaled by the
+  // brick's node count for other tiles
   if (P->tc && P->cg_prec == PREC_F64 &&
       tile_occupancy(degree, MODE_CG, P->geom_kind, PREC_F64TC, P->ncomp,
                      tile_smem_bytes(degree, P->geom_kind, PREC_F64TC, g, MODE_CG)) == 2) {
     const double nodes = (double)(degree * g.T[0] + 1) * (degree * g.T[1] + 1) * (degree * g.T[2] + 1);
     P->stagger_lo = n_sm;
     P->stagger_hi = 2 * n_sm;
-    P->stagger_cycles = (long long)(90000.0 * nodes / (17.0 * 17.0 * 13.0));
+    P->stagger_cycles = (long long)(80000.0 * nodes / (17.0 * 17.0 * 13.0));
   }
   P->tail_nodes = P->fam[0] + P->fam[1] + P->fam[2];
   // about four shared-face nodes per tail thread (two iterations of two)

@@ -1529,13 +1529,15 @@ __global__ void __launch_bounds__(kThreads, 3) tail_kernel(const TileArgs a) {
   }
   // Two nodes per thread and iteration, each summing its (up to eight) shell
   // partials through a fixed 2x2x2 loop of predicated loads, so that all loads
-  // of both nodes are in flight together; the sum order is the fixed (z, y, x)
-  // order of the contributing tiles.
+  // of both nodes -- with r_k, p_k and D^-1 in CG mode -- are in flight
+  // together; the sum order is the fixed (z, y, x) order of the contributing
+  // tiles.
   const int64_t gstride = (int64_t)gridDim.x * kThreads;
   for (int64_t t0 = (int64_t)blockIdx.x * kThreads + threadIdx.x; t0 < a.tail_nodes; t0 += 2 * gstride) {
     T v[2];
     int64_t gi[2];
     bool ok[2];
+    T rk[2], pk[2], dv[2];  // CG: r_k, p_k and D^-1 of the node, loaded with its shell partials
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int64_t t = t0 + h * gstride;
@@ -1545,6 +1547,12 @@ __global__ void __launch_bounds__(kThreads, 3) tail_kernel(const TileArgs a) {
       if (!ok[h]) continue;
       int i, j, k;
       decode_tail_node(g, a.fam, a.tdiv, t, i, j, k);
+      gi[h] = node_index(g, i, j, k);
+      if constexpr (MODE == MODE_CG) {
+        rk[h] = r_k[gi[h]];
+        pk[h] = p_k[gi[h]];
+        dv[h] = static_cast<const T*>(a.diag_inv)[gi[h]];
+      }
       int txs[2], lis[2], tys[2], ljs[2], tzs[2], lks[2];
       const int nx = contributors(g, 0, i, txs, lis);
       const int ny = contributors(g, 1, j, tys, ljs);
@@ -1566,17 +1574,8 @@ __global__ void __launch_bounds__(kThreads, 3) tail_kernel(const TileArgs a) {
         const int cx = m & 1, cy = (m >> 1) & 1, cz = m >> 2;
         if (cx < nx && cy < ny && cz < nz) v[h] = m == 0 ? part[m] : t_add<PREC>(v[h], part[m]);
       }
-      gi[h] = node_index(g, i, j, k);
     }
     if constexpr (MODE == MODE_CG) {
-      T rk[2], pk[2], dv[2];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        if (!ok[h]) continue;
-        rk[h] = r_k[gi[h]];
-        pk[h] = p_k[gi[h]];
-        dv[h] = static_cast<const T*>(a.diag_inv)[gi[h]];
-      }
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         if (!ok[h]) continue;
