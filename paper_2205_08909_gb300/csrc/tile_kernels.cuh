@@ -1664,8 +1664,10 @@ TileFn<P> tile_fn_gn(int mode, int prec) {
 template <int P, int GEOM>
 TileFn<P> tile_fn_g(int mode, int prec, int ncomp) {
   // the tri-quadratic geometry has the scalar operator only
-  if constexpr (GEOM == GEOM_QUAD) return ncomp == 1 ? tile_fn_gn<P, GEOM, 1>(mode, prec) : nullptr;
-  return ncomp == 3 ? tile_fn_gn<P, GEOM, 3>(mode, prec) : tile_fn_gn<P, GEOM, 1>(mode, prec);
+  if constexpr (GEOM == GEOM_QUAD)
+    return ncomp == 1 ? tile_fn_gn<P, GEOM, 1>(mode, prec) : nullptr;
+  else
+    return ncomp == 3 ? tile_fn_gn<P, GEOM, 3>(mode, prec) : tile_fn_gn<P, GEOM, 1>(mode, prec);
 }
 
 template <int P>
