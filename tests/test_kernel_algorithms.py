@@ -7,7 +7,11 @@ it against the plain definition it replaces:
   * the even-odd halves of centrosymmetric and anti-centrosymmetric 1D
     matrices reproduce the plain matrix-vector product;
   * the batched cell schedule of deformed tiles with its node gather adds every
-    (cell, local node) contribution exactly once and stays inside the brick.
+    (cell, local node) contribution exactly once and stays inside the brick;
+  * the tri-quadratic metric -- per-line partial sums of the 27 support points,
+    one more sum per point, cyclic cofactors and the flux (w a / det J) C^T (C g)
+    -- equals J^{-1} (w det J a) J^{-T} g with J from the plain tensor-product
+    interpolation.
 """
 import itertools
 
@@ -147,3 +151,64 @@ def test_deformed_batch_gather_covers_every_contribution_once(P):
                             key = (cx, cy, cz, a, b, c)
                             count[key] = count.get(key, 0) + 1
                 assert len(count) == ncell * (P + 1) ** 3 and set(count.values()) == {1}
+
+
+def _quadratic_tables(g):
+    """Values and derivatives of the quadratic Lagrange polynomials through
+    0, 1/2, 1 at the points g: [q][a]."""
+    v = np.stack([2 * (g - 0.5) * (g - 1), -4 * g * (g - 1), 2 * g * (g - 0.5)], axis=1)
+    d = np.stack([4 * g - 3, -8 * g + 4, 4 * g - 1], axis=1)
+    return v, d
+
+
+@pytest.mark.parametrize("P", [1, 3, 6])
+def test_quadratic_metric_scheme(P):
+    rng = np.random.default_rng(40 + P)
+    N1 = P + 1
+    x, w = np.polynomial.legendre.leggauss(N1)
+    g, w = 0.5 * (x + 1), 0.5 * w
+    v, dv = _quadratic_tables(g)
+    s3 = np.array([0.0, 0.5, 1.0])
+    # support points X[d][a + 3 (b + 3 c)]: a scaled cube, perturbed
+    ref_pts = np.stack(np.meshgrid(s3, s3, s3, indexing="ij"), axis=-1)  # [a][b][c][d]
+    pts = 0.3 * ref_pts + 0.01 * rng.standard_normal(ref_pts.shape)
+    X = np.array([[pts[m % 3, (m // 3) % 3, m // 9, d] for m in range(27)] for d in range(3)])
+    coef = lambda x0: 1.0 + 0.5 * np.sin(np.pi * x0)
+    # kernel scheme: line sums G[d][a][k][qb][qc]
+    G = np.zeros((3, 3, 3, N1, N1))
+    for d, a, qb, qc in itertools.product(range(3), range(3), range(N1), range(N1)):
+        s0 = s1 = s2 = 0.0
+        for b in range(3):
+            col = [X[d][a + 3 * b + 9 * c] for c in range(3)]
+            e0 = sum(col[c] * v[qc, c] for c in range(3))
+            e1 = sum(col[c] * dv[qc, c] for c in range(3))
+            s0 += v[qb, b] * e0
+            s1 += dv[qb, b] * e0
+            s2 += v[qb, b] * e1
+        G[d, a, :, qb, qc] = (s0, s1, s2)
+    for qa, qb, qc in itertools.product(range(N1), repeat=3):
+        J = np.zeros((3, 3))
+        for d in range(3):
+            J[d, 0] = sum(dv[qa, a] * G[d, a, 0, qb, qc] for a in range(3))
+            J[d, 1] = sum(v[qa, a] * G[d, a, 1, qb, qc] for a in range(3))
+            J[d, 2] = sum(v[qa, a] * G[d, a, 2, qb, qc] for a in range(3))
+        x0 = sum(v[qa, a] * G[0, a, 0, qb, qc] for a in range(3))
+        C = np.zeros((3, 3))
+        for i, j in itertools.product(range(3), repeat=2):
+            i1, i2, j1, j2 = (i + 1) % 3, (i + 2) % 3, (j + 1) % 3, (j + 2) % 3
+            C[i, j] = J[i1, j1] * J[i2, j2] - J[i1, j2] * J[i2, j1]
+        det = J[0] @ C[0]
+        wq = w[qa] * w[qb] * w[qc]
+        grad = rng.standard_normal(3)
+        flux = (wq * coef(x0) / det) * (C.T @ (C @ grad))
+        # plain definition: J from the tensor-product interpolation of the map
+        phi = np.einsum("a,b,c->abc", v[qa], v[qb], v[qc])
+        Jd = np.stack([np.einsum("abcd,a,b,c->d", pts, dv[qa], v[qb], v[qc]),
+                       np.einsum("abcd,a,b,c->d", pts, v[qa], dv[qb], v[qc]),
+                       np.einsum("abcd,a,b,c->d", pts, v[qa], v[qb], dv[qc])], axis=1)
+        xd = np.einsum("abcd,abc->d", pts, phi)
+        np.testing.assert_allclose(J, Jd, atol=1e-14)
+        assert abs(x0 - xd[0]) < 1e-14
+        Ji = np.linalg.inv(Jd)
+        ref = Ji @ ((wq * np.linalg.det(Jd) * coef(xd[0])) * (Ji.T @ grad))
+        np.testing.assert_allclose(flux, ref, rtol=1e-12, atol=1e-14 * np.abs(ref).max())
