@@ -1059,8 +1059,9 @@ int setup_impl(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, con
   // wave's second CTA on each SM (blockIdx in [n_sm, 2 n_sm)) starts about
   // half a tile later (80,000 clocks for the 17 x 17 x 13-node brick of
   // degree 4, the best of 0-110,000 measured on Q4 128^3: +8 %), scaled by the
-  // brick's node count for other tiles
-  if (P->tc && P->cg_prec == PREC_F64 &&
+  // brick's node count for other tiles.  The delay costs about half a tile
+  // once per launch, so it is applied only to launches of at least eight waves.
+  if (P->tc && P->cg_prec == PREC_F64 && g.n_tiles >= 16LL * n_sm &&
       tile_occupancy(degree, MODE_CG, P->geom_kind, PREC_F64TC, P->ncomp,
                      tile_smem_bytes(degree, P->geom_kind, PREC_F64TC, g, MODE_CG)) == 2) {
     const double nodes = (double)(degree * g.T[0] + 1) * (degree * g.T[1] + 1) * (degree * g.T[2] + 1);
