@@ -513,6 +513,18 @@ def test_mass_matrix_total_is_domain_volume(p, amp, tol):
     assert abs(one @ (A @ one) - 1.0) < tol
 
 
+@pytest.mark.parametrize("p", [1, 3, 5])
+def test_quadratic_geometry_volume_is_exact(p):
+    # the tri-quadratic cells tile the unit cube exactly, and since the map adds
+    # the same interpolated scalar s_h to every coordinate, det J = h_x h_y h_z
+    # (1 + A sum_i (d s_h / d xhat_i) / h_i) has degree <= 2 in each reference
+    # coordinate: every Gauss rule here integrates it exactly, so 1^T M 1 = 1 to
+    # rounding however large the deformation
+    A = fem.assemble(fem.Problem(p, (3, 2, 3), 0.09, op=fem.OP_MASS, geometry_degree=2), dirichlet=False)
+    one = np.ones(A.shape[0])
+    assert abs(one @ (A @ one) - 1.0) < 1e-13
+
+
 def test_mass_projection_reproduces_polynomial():
     # u = x(1-x) y(1-y) z(1-z) lies in Q_2 and vanishes on the boundary: the
     # discrete L2 projection (mass matrix, right-hand side by the same Gauss rule,
