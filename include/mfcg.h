@@ -196,10 +196,11 @@ typedef struct mfcg_problem mfcg_problem;
  * With tile = {-1,-1,-1} the call sets up and times a few candidate tiles first
  * (short fixed-iteration solves) and keeps the fastest.
  * Errors: INVALID_ARG (cells < 1, |amplitude| >= 0.1, affine kind with A != 0 or
- * a != 1, bad enums, FP32_INNER without FUSED, SEMI_FUSED with FP32_INNER,
- * components other than 0, 1, 3 or components 3 without FUSED, MFCG_OP_MASS with
- * MFCG_GEOM_DEFORMED_TENSOR, MFCG_GEOM_USER without user_data), UNSUPPORTED_DEGREE,
- * OUT_OF_MEMORY, CUDA_ERROR. */
+ * a != 1, bad enums, FP32_INNER or DOUBLE_FLOAT_INNER without FUSED, components
+ * other than 0, 1, 3 or components 3 without FUSED or with
+ * MFCG_GEOM_DEFORMED_QUADRATIC, MFCG_OP_MASS with MFCG_GEOM_DEFORMED_TENSOR,
+ * MFCG_GEOM_USER without user_data), UNSUPPORTED_DEGREE, OUT_OF_MEMORY,
+ * CUDA_ERROR. */
 int mfcg_setup(const mfcg_mesh* mesh, int degree, const mfcg_geometry* geom, const mfcg_options* opt,
                void* cuda_stream, mfcg_problem** out);
 
